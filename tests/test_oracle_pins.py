@@ -1,0 +1,406 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: they use hand-worked
+values, closed forms, invariants, brute force on tiny inputs, and Monte-Carlo
+expectations that the paper states (unbiasedness of r_0 and tau, Sec. 2) or
+that Stein's lemma fixes.  The last test plants plausible mistakes in the
+oracle and checks that one of these pins catches each of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import vdamp_oracle as O
+from paper_1911_01234_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _crand(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# --------------------------------------------------------------------- FFT ---
+
+def _naive_dft2(x):
+    ny, nx = x.shape
+    wy = np.exp(-2j * np.pi * np.outer(np.arange(ny), np.arange(ny)) / ny) / math.sqrt(ny)
+    wx = np.exp(-2j * np.pi * np.outer(np.arange(nx), np.arange(nx)) / nx) / math.sqrt(nx)
+    out = np.zeros_like(x, dtype=np.complex128)
+    for ky in range(ny):           # explicit O(N^2) double sum, row by row
+        for kx in range(nx):
+            out[ky, kx] = np.sum(wy[ky][:, None] * wx[kx][None, :] * x)
+    return out
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (12, 20)])
+def test_fft_matches_naive_dft(shape):
+    x = _crand(np.random.default_rng(1), *shape)
+    ref = _naive_dft2(x)
+    got = O.fft2u(x)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_fft_parseval_and_inverse():
+    x = _crand(np.random.default_rng(2), 24, 40)
+    k = O.fft2u(x)
+    assert abs(np.linalg.norm(k) - np.linalg.norm(x)) < 1e-12 * np.linalg.norm(x)
+    assert np.abs(O.ifft2u(k) - x).max() < 1e-13
+
+
+# --------------------------------------------------------------------- DWT ---
+
+def test_haar_2x2_by_hand():
+    gold = json.load(open(os.path.join(GOLD, "haar_2x2.json")))
+    h, g = O.wavelet_filters("haar")
+    w = O.dwt2(np.array(gold["x"]), h, g, 1)
+    assert np.allclose(w, gold["packed"], atol=1e-14)
+
+
+def test_db2_matches_closed_form():
+    gold = json.load(open(os.path.join(GOLD, "db2_closed_form.json")))
+    want = np.array([eval(e, {"sqrt": math.sqrt}) for e in gold["expr"]])
+    assert np.abs(O.daubechies_lowpass(2) - want).max() < 1e-14
+
+
+@pytest.mark.parametrize("name", ["haar", "db4"])
+def test_filter_identities(name):
+    h, g = O.wavelet_filters(name)
+    L = len(h)
+    assert L == {"haar": 2, "db4": 8}[name]
+    assert abs(h.sum() - math.sqrt(2)) < 1e-14
+    for m in range(0, L // 2):
+        want = 1.0 if m == 0 else 0.0
+        assert abs(np.dot(h[:L - 2 * m], h[2 * m:]) - want) < 1e-14
+        assert abs(np.dot(g[:L - 2 * m], g[2 * m:]) - want) < 1e-14
+        assert abs(np.dot(h[:L - 2 * m], g[2 * m:])) < 1e-14
+        assert abs(np.dot(g[:L - 2 * m], h[2 * m:])) < 1e-14
+    k = np.arange(L, dtype=np.float64)
+    for q in range(L // 2):          # vanishing moments of the wavelet
+        assert abs(np.sum(k ** q * g)) < 1e-10 * max(1.0, np.sum(np.abs(k ** q * g)))
+    if name == "db4":
+        # minimum phase: the zeros of H(z) other than z = -1 lie inside the unit circle
+        roots = np.roots(h)
+        inner = roots[np.abs(roots + 1.0) > 1e-2]
+        assert np.all(np.abs(inner) < 1.0)
+
+
+@pytest.mark.parametrize("name,shape,s", [("haar", (64, 64), 3), ("db4", (32, 48), 3),
+                                          ("db4", (64, 64), 4), ("db4", (24, 40), 2)])
+def test_dwt_perfect_reconstruction_and_parseval(name, shape, s):
+    h, g = O.wavelet_filters(name)
+    x = _crand(np.random.default_rng(3), *shape)
+    w = O.dwt2(x, h, g, s)
+    assert abs(np.linalg.norm(w) - np.linalg.norm(x)) < 1e-12 * np.linalg.norm(x)
+    assert np.abs(O.idwt2(w, h, g, s, *shape) - x).max() < 1e-12
+
+
+def test_dwt_layout_and_constant_image():
+    # a constant image lives entirely in the approximation band A_s
+    h, g = O.wavelet_filters("db4")
+    x = np.full((32, 32), 3.0 + 1.0j)
+    w = O.dwt2(x, h, g, 3)
+    sbs = O.subbands(32, 32, 3)
+    a = sbs[0]
+    assert a.name == "A3" and a.shape == (4, 4)
+    assert np.allclose(w[a.offset:a.offset + a.size], (3.0 + 1.0j) * 2 ** 3)
+    assert np.abs(w[a.size:]).max() < 1e-12
+    assert [sb.name for sb in sbs] == ["A3", "H3", "V3", "D3", "H2", "V2", "D2", "H1", "V1", "D1"]
+
+
+def test_dwt_orientation():
+    # an image varying only along x has energy only in bands that are high-pass along x
+    h, g = O.wavelet_filters("haar")
+    x = np.tile(np.array([1.0, -1.0] * 8), (16, 1))
+    w = O.dwt2(x, h, g, 1)
+    sbs = O.subbands(16, 16, 1)
+    energy = {sb.kind: float(np.sum(np.abs(w[sb.offset:sb.offset + sb.size]) ** 2)) for sb in sbs}
+    assert energy["H"] > 0 and energy["A"] < 1e-20 and energy["V"] < 1e-20 and energy["D"] < 1e-20
+
+
+# ----------------------------------------------------------------------- S ---
+
+@pytest.mark.parametrize("name,ny,nx,s", [("haar", 32, 32, 3), ("db4", 32, 48, 3)])
+def test_s_columns_invariants(name, ny, nx, s):
+    h, g = O.wavelet_filters(name)
+    S = O.s_columns(ny, nx, h, g, s)
+    sbs = O.subbands(ny, nx, s)
+    assert S.shape == (1 + 3 * s, ny, nx)
+    # each column is |F psi|^2 of a unit-norm atom: sums to 1 (Parseval)
+    assert np.abs(S.reshape(len(sbs), -1).sum(axis=1) - 1.0).max() < 1e-12
+    # the atoms form an orthonormal basis: sum_b N_b S[i, b] = 1 at every frequency
+    tot = sum(sb.size * S[sb.index] for sb in sbs)
+    assert np.abs(tot - 1.0).max() < 1e-12
+    # 1 + 3s unique columns (Sec. 2): another position in the subband gives the same column
+    pos = [sb.size - 1 if sb.size > 1 else 0 for sb in sbs]
+    S2 = O.s_columns(ny, nx, h, g, s, position=pos)
+    assert np.abs(S2 - S).max() < 1e-14
+
+
+def test_s_haar_single_level_closed_form():
+    n = 16
+    h, g = O.wavelet_filters("haar")
+    S = O.s_columns(n, n, h, g, 1)
+    k = np.arange(n)
+    lo = (2.0 / n) * np.cos(np.pi * k / n) ** 2
+    hi = (2.0 / n) * np.sin(np.pi * k / n) ** 2
+    want = {"A": np.outer(lo, lo), "H": np.outer(lo, hi), "V": np.outer(hi, lo),
+            "D": np.outer(hi, hi)}
+    for sb in O.subbands(n, n, 1):
+        assert np.abs(S[sb.index] - want[sb.kind]).max() < 1e-14
+
+
+# --------------------------------------------------------------------- tau ---
+
+def test_tau_full_sampling_closed_form():
+    # p = 1 everywhere: tau_b = sigma^2 for every subband, whatever z is
+    ny = nx = 32
+    mask = np.ones((ny, nx), dtype=bool)
+    ops = O.make_operators(mask, np.ones((ny, nx)), "db4", 3)
+    z = _crand(np.random.default_rng(4), ny, nx)
+    tau = O.tau_estimate(z, ops, 0.37)
+    assert np.abs(tau - 0.37).max() < 1e-12
+
+
+def _mc_setup(ny=32, nx=32, s=3, name="db4"):
+    rng = np.random.default_rng(5)
+    wl = synth.Workload("mc", 99, ny, nx, 6, False, name, s, 3.0, 3.0, 4, 20.0, 20.0, 1, 1)
+    x0 = synth.phantom(ny, nx, 6, False, rng)
+    p = synth.poly_density(ny, nx, 3.0, 4)
+    p = np.maximum(p, 0.05)             # keep the Monte-Carlo variance bounded
+    h, g = O.wavelet_filters(name)
+    r_tilde = O.dwt2(x0, h, g, s) + 0.05 * _crand(rng, ny * nx)
+    sigma = 0.03
+    return wl, rng, x0, p, r_tilde, sigma
+
+
+def test_r0_and_tau_unbiased_monte_carlo():
+    """E r_k = w0 for r~ = 0 and E tau_k = E|w0 - r_k|^2 per subband for a fixed r~ (Sec. 2)."""
+    wl, rng, x0, p, r_tilde, sigma = _mc_setup()
+    ny, nx, s = wl.ny, wl.nx, wl.levels
+    ops = O.make_operators(np.ones((ny, nx), bool), p, wl.wavelet, s)
+    w0 = ops.psi(x0)
+    k0 = O.fft2u(x0)
+    draws = 1500
+    tau_d = np.zeros((draws, len(ops.sbs)))
+    err_d = np.zeros((draws, len(ops.sbs)))
+    r0_sum = np.zeros(ny * nx, dtype=np.complex128)
+    r0_sq = np.zeros(ny * nx)
+    for d in range(draws):
+        mask = rng.random((ny, nx)) < p
+        eps = (sigma / math.sqrt(2)) * _crand(rng, ny, nx)
+        y = np.where(mask, k0 + eps, 0.0)
+        ops.mask = mask
+        rec = O.iterate(r_tilde, y, ops, sigma ** 2)
+        tau_d[d] = rec.tau
+        for sb in ops.sbs:
+            e = rec.r[sb.offset:sb.offset + sb.size] - w0[sb.offset:sb.offset + sb.size]
+            err_d[d, sb.index] = np.mean(np.abs(e) ** 2)
+        rec0 = O.iterate(np.zeros_like(r_tilde), y, ops, sigma ** 2)
+        r0_sum += rec0.r
+        r0_sq += np.abs(rec0.r - w0) ** 2
+    # tau: difference of means within 3 standard errors, per subband
+    diff = tau_d - err_d
+    se = diff.std(axis=0, ddof=1) / math.sqrt(draws)
+    assert np.all(np.abs(diff.mean(axis=0)) < 3.5 * se + 1e-12), (diff.mean(axis=0), se)
+    # and both agree with the analytic expectation sum_i S((1-p)/p |E_i|^2 + sigma^2/p)
+    e_k = O.fft2u(x0 - ops.psi_h(r_tilde))
+    expect = ops.S.reshape(len(ops.sbs), -1) @ (((1 - p) / p * np.abs(e_k) ** 2
+                                                  + sigma ** 2 / p).ravel())
+    se_t = tau_d.std(axis=0, ddof=1) / math.sqrt(draws)
+    assert np.all(np.abs(tau_d.mean(axis=0) - expect) < 3.5 * se_t)
+    # r_0 unbiased: the mean error, normalised by its standard error, is O(1)
+    mean_err = r0_sum / draws - w0
+    se_r = np.sqrt(r0_sq / draws / draws)
+    z = np.abs(mean_err) / se_r
+    assert np.mean(z ** 2) < 1.5          # ~1 (chi^2 / 2 per complex coefficient) if unbiased
+
+
+# ----------------------------------------------------- denoiser and SURE ---
+
+def test_soft_threshold_closed_form():
+    r = np.array([0.0, 0.5 + 0.0j, -0.3 + 0.4j, 3.0 - 4.0j, 1.0j])
+    got = O.soft(r, 0.5)
+    want = np.array([0.0, 0.0, 0.0, (3.0 - 4.0j) * (4.5 / 5.0), 0.5j])
+    assert np.abs(got - want).max() < 1e-15
+
+
+def test_alpha_matches_finite_difference_half_divergence():
+    rng = np.random.default_rng(6)
+    r = _crand(rng, 400)
+    theta = 0.8
+    eps = 1e-6
+    div = np.zeros(r.size)
+    for d in (1.0, 1.0j):
+        gp = O.soft(r + eps * d, theta)
+        gm = O.soft(r - eps * d, theta)
+        comp = (gp - gm) / (2 * eps)
+        div += comp.real if d == 1.0 else comp.imag
+    fd = float(np.mean(div / 2.0))
+    assert abs(O.soft_divergence_mean(np.abs(r), theta) - fd) < 1e-6 * abs(fd)
+
+
+def test_sure_is_unbiased_stein():
+    rng = np.random.default_rng(7)
+    w = np.concatenate([np.zeros(60), 3.0 * _crand(rng, 20)])
+    tau = 0.5
+    theta = 0.9
+    draws = 10000
+    sure = np.empty(draws)
+    mse = np.empty(draws)
+    for d in range(draws):
+        r = w + math.sqrt(tau / 2) * _crand(rng, w.size)
+        sure[d] = O.sure_value(np.abs(r), theta, tau)
+        mse[d] = np.sum(np.abs(O.soft(r, theta) - w) ** 2)
+    diff = sure - mse
+    assert abs(diff.mean()) < 3.5 * diff.std(ddof=1) / math.sqrt(draws)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_sure_exact_minimiser_vs_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 17))
+    a = np.abs(_crand(rng, n)) * rng.uniform(0.2, 3.0)
+    if seed == 3:
+        a[0] = 0.0                    # a zero coefficient is always "below"
+    tau = float(rng.uniform(0.05, 2.0))
+    th, val = O.sure_threshold(a, tau)
+    assert abs(val - O.sure_value(a, th, tau)) < 1e-12 * max(1.0, abs(val))
+    bt, bv = O.sure_threshold_bruteforce(a, tau, grid=200_000)
+    assert val <= bv + 1e-12 * max(1.0, abs(bv))
+    assert bv - val < 1e-6 * max(1.0, abs(bv))
+
+
+def test_sure_threshold_never_zero_when_noisy():
+    a = np.abs(_crand(np.random.default_rng(8), 300))
+    th, _ = O.sure_threshold(a, 0.2)
+    assert th > 0.0
+
+
+# ------------------------------------------------------- line 8, line 10 ---
+
+def test_onsager_linear_denoiser_and_identity():
+    sbs = O.subbands(16, 16, 2)
+    r = _crand(np.random.default_rng(9), 256)
+    c = np.linspace(0.1, 0.7, len(sbs))
+    w_hat = O.expand(c, sbs) * r
+    assert np.abs(O.onsager(w_hat, r, c, sbs)).max() < 1e-15
+    assert np.array_equal(O.onsager(r, r, np.zeros(len(sbs)), sbs), r)
+
+
+def test_return_line_is_data_consistent():
+    pr = synth.make_problem(synth.PLAIN_64_HAAR3)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, 3)
+    k = O.fft2u(res.x_hat)
+    m = pr.mask == 1
+    assert np.abs(k[m] - pr.y[m]).max() < 1e-12
+
+
+# ----------------------------------------------------- the whole iteration ---
+
+def test_converges_on_sparse_signal():
+    """OAMP-type iteration with uniform density reaches the noise floor on a sparse image."""
+    rng = np.random.default_rng(10)
+    ny = nx = 64
+    h, g = O.wavelet_filters("haar")
+    w0 = np.where(rng.random(ny * nx) < 0.05, _crand(rng, ny * nx), 0.0)
+    x0 = O.idwt2(w0, h, g, 3, ny, nx)
+    p = np.full((ny, nx), 0.5)
+    mask = rng.random((ny, nx)) < p
+    sigma = 1e-3
+    y = np.where(mask, O.fft2u(x0) + sigma / math.sqrt(2) * _crand(rng, ny, nx), 0.0)
+    res = O.vdamp(y, mask, p, sigma, "haar", 3, 20)
+    assert O.nmse_db(res.x_hat, x0) < -45.0
+
+
+def test_state_evolution_plain_256():
+    """Colored state evolution (Eq. 5, Fig. 4-5): per subband, r_k - w0 is Gaussian with
+    the variance tau_k predicts.  (Within a subband it is not white under this steep
+    density: neighbouring coefficients correlate, so whiteness is not asserted.)"""
+    from scipy import stats
+    pr = synth.make_problem(synth.PLAIN_256_DB4_4)
+    ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, 8,
+                  want_x=True, ops=ops)
+    w0 = ops.psi(pr.x0)
+    for rec in res.records:
+        for sb in ops.sbs:
+            if sb.size < 1024:
+                continue
+            e = (rec.r - w0)[sb.offset:sb.offset + sb.size]
+            ratio = np.mean(np.abs(e) ** 2) / rec.tau[sb.index]
+            assert 0.85 <= ratio <= 1.15, (sb.name, ratio)
+            if sb.size < 4096:
+                continue              # sample kurtosis s.e. sqrt(24/n) is ~0.08 from here
+            for part in (e.real, e.imag):
+                assert abs(stats.kurtosis(part)) < 0.3, sb.name
+                assert abs(stats.skew(part)) < 0.2, sb.name
+    nm = [O.nmse_db(r.x_hat, pr.x0) for r in res.records]
+    assert nm[2] < nm[0]
+
+
+# ------------------------------------------ the pins catch planted mistakes ---
+
+def _bad_tau_no_outer_pinv(z, ops, sigma2):
+    om = ops.mask
+    pinv = 1.0 / ops.p[om]
+    return ops.S[:, om] @ ((pinv - 1.0) * np.abs(z[om]) ** 2 + sigma2)
+
+
+def _bad_tau_no_noise(z, ops, sigma2):
+    om = ops.mask
+    pinv = 1.0 / ops.p[om]
+    return ops.S[:, om] @ (pinv * (pinv - 1.0) * np.abs(z[om]) ** 2)
+
+
+def _bad_alpha_full_divergence(a, theta):
+    above = a > theta
+    return float(np.sum(np.where(above, 1.0 - theta / np.where(above, a, 1.0), 0.0)) / a.size)
+
+
+def _bad_sure_sign(a, theta, tau):
+    below = a <= theta
+    above_val = theta * theta + tau * (1.0 + theta / np.where(below, 1.0, a))
+    return float(np.sum(np.where(below, a * a - tau, above_val)))
+
+
+def _bad_synthesis_index(c, f, axis):
+    half = c.shape[axis]
+    n = 2 * half
+    cm = np.moveaxis(c, axis, 0)
+    out = np.zeros((n,) + cm.shape[1:], dtype=np.result_type(c, np.float64))
+    for k, fk in enumerate(f):
+        out[(2 * np.arange(half) - k) % n] += fk * cm
+    return np.moveaxis(out, 0, axis)
+
+
+def _bad_iterate_no_density_compensation(r_tilde, y, ops, sigma2, want_x=False):
+    z = np.where(ops.mask, y - ops.phi(ops.psi_h(r_tilde)), 0.0)
+    r = r_tilde + ops.psi(ops.phi_h(z))
+    tau = O.tau_estimate(z, ops, sigma2)
+    w_hat, theta, alpha = O.denoise(r, tau, ops.sbs)
+    return O.Record(r_tilde=r_tilde, z=z, r=r, tau=tau, theta=theta, alpha=alpha, w_hat=w_hat)
+
+
+@pytest.mark.parametrize("target,bad,pins", [
+    ("tau_estimate", _bad_tau_no_outer_pinv, ["test_r0_and_tau_unbiased_monte_carlo"]),
+    ("tau_estimate", _bad_tau_no_noise, ["test_tau_full_sampling_closed_form"]),
+    ("soft_divergence_mean", _bad_alpha_full_divergence,
+     ["test_alpha_matches_finite_difference_half_divergence"]),
+    ("sure_value", _bad_sure_sign, ["test_sure_is_unbiased_stein"]),
+    ("_synthesis_axis", _bad_synthesis_index, ["test_dwt_perfect_reconstruction_and_parseval"]),
+    ("iterate", _bad_iterate_no_density_compensation, ["test_r0_and_tau_unbiased_monte_carlo"]),
+])
+def test_pins_catch_planted_mistakes(monkeypatch, target, bad, pins):
+    monkeypatch.setattr(O, target, bad)
+    g = globals()
+    for name in pins:
+        fn = g[name]
+        with pytest.raises(AssertionError):
+            if name == "test_dwt_perfect_reconstruction_and_parseval":
+                fn("db4", (32, 48), 3)
+            else:
+                fn()
