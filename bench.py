@@ -1,0 +1,374 @@
+"""Benchmark: plain VDAMP (Algorithm 1) on one 256x256 slice, db4 s=4, 30 iterations.
+
+One step = one vdamp_solve of the whole hot path (30 iterations of lines 3-8
+plus the return line) on one synthetic slice whose inputs are resident in
+HBM.  Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on
+the host cores instead.  Under torchrun each rank solves its own slice
+(independent replicas, weak scaling, no collective on the data path).
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")   # the oracle baseline runs on one core
+
+import argparse
+import json
+import math
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1911_01234_gb300 import synth  # noqa: E402
+
+WL = synth.PLAIN_256_DB4_4
+METRIC = "slice-iterations/s at 256x256 (plain VDAMP, db4 s=4, 30 iterations)"
+UNIT = "slice-iterations/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def config_block(slices_per_gpu, world):
+    return {"workload": WL.name, "ny": WL.ny, "nx": WL.nx, "wavelet": WL.wavelet,
+            "levels": WL.levels, "iters": WL.iters, "rate": WL.rate, "snr_db": WL.snr_db,
+            "slices_per_gpu": slices_per_gpu, "global_batch": slices_per_gpu * world,
+            "parallelism": f"replicas x{world} (independent slices, no collective)",
+            "l2": "flushed between steps (256 MiB write outside the step events)"}
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+class OracleRunner:
+    """The FP64 oracle iterating the same workload; operators (S) built once."""
+
+    def __init__(self):
+        from oracle import vdamp_oracle as O
+        self.O = O
+        self.pr = synth.make_problem(WL)
+        self.ops = O.make_operators(self.pr.mask, self.pr.density, self.pr.wavelet,
+                                    self.pr.levels)
+        self.y = np.where(self.pr.mask == 1, self.pr.y.astype(np.complex128), 0.0)
+        self.s2 = float(self.pr.sigma) ** 2
+        self.k = 0
+        self.rt = np.zeros(WL.ny * WL.nx, dtype=np.complex128)
+
+    def run(self, budget_s):
+        """Iterate (lines 3-8; the return line after every 30th) for ~budget_s seconds."""
+        O = self.O
+        done = 0
+        t0 = time.perf_counter()
+        while True:
+            rec = O.iterate(self.rt, self.y, self.ops, self.s2)
+            self.rt = O.next_r_tilde(rec, self.ops)
+            self.k += 1
+            done += 1
+            if self.k == WL.iters:
+                O.final_estimate(rec.w_hat, self.y, self.ops)
+                self.k = 0
+                self.rt = np.zeros_like(self.rt)
+            el = time.perf_counter() - t0
+            if el >= budget_s:
+                return done, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    runner = OracleRunner()
+    budget = max(0.2, min(args.ref_step_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        runner.run(budget)
+    total_it, total_s = 0, 0.0
+    for _ in range(args.steps):
+        it, el = runner.run(budget)
+        total_it += it
+        total_s += el
+    value = total_it / total_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(1, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of ~{budget:.2f} s of FP64 numpy "
+                                       f"oracle iterations on the 256x256 slice "
+                                       f"({total_it} iterations)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm ---
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return []
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = []
+        for ln in out.strip().splitlines():
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        return rows
+
+    @staticmethod
+    def summarize(rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# Algorithmic bytes per launch of each kernel kind, per slice, for this
+# workload (N = ny nx pixels, n = sampled frequencies).
+def algorithmic_bytes(kind, N, n, levels):
+    lv = [N / 4 ** (j - 1) for j in range(1, levels + 1)]   # pixels entering scale j
+    if kind == "col_pass":     # k-space in + out, y and p on Omega, mask bits
+        return 16 * N + 12 * n + N / 8
+    if kind == "fft_rows":     # rows in + out
+        return 16 * N
+    if kind == "idwt":         # four bands in, one image out, mean over scales
+        return statistics.mean(16 * v for v in lv)
+    if kind == "dwt":          # image in, four bands out, r_{k-1} in for r~
+        return statistics.mean(16 * v + 8 * v * (1.0 if j == levels else 0.75)
+                               for j, v in enumerate(lv, start=1))
+    if kind == "sure":         # r_k once
+        return 8 * N
+    return 0.0
+
+
+# Measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum per launch)
+# on the kernel build named by its source hash; None when the source changed.
+MEASURED_TRAFFIC = {}
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1911_01234_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1911_01234_gb300 import binding as vb
+    from paper_1911_01234_gb300 import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    vb.load()
+
+    pr = synth.make_problem(WL, slice_idx=rank)
+    N = WL.ny * WL.nx
+    n_samp = int(pr.mask.sum())
+    y = torch.from_numpy(pr.y[None].copy()).cuda()
+    m = torch.from_numpy(pr.mask[None].copy()).cuda()
+    p = torch.from_numpy(pr.density[None].copy()).cuda()
+    plan = vb.Plan(WL.ny, WL.nx, WL.wavelet, WL.levels)
+    K = WL.iters
+    x_hat = torch.empty((1, WL.ny, WL.nx), dtype=torch.complex64, device="cuda")
+    tau = torch.empty((1, K, plan.B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        vb.vdamp_solve(plan.handle, 1, y, m, p, [pr.sigma], K, None, x_hat, tau, thr, alpha,
+                       stream=stream.cuda_stream)
+
+    for i in range(max(args.warmup, 3)):
+        flush_buf.fill_(float(i))
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = vb.vdamp_last_launch_count(plan.handle)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush_buf.fill_(float(i))
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    rows = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    st, _ = vb.vdamp_device_status(plan.handle)
+    if st != vb.VDAMP_OK:
+        raise RuntimeError("solve reported a non-finite tau or alpha")
+    t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * args.steps * K / (max_ms / 1e3)
+
+    # ---- dominant kernel, timed live with CUDA events on the launching stream
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 1)
+    vb.vdamp_kernel_times(plan.handle)
+    reps = 5
+    for i in range(reps):
+        flush_buf.fill_(float(i))
+        step()
+    kt = vb.vdamp_kernel_times(plan.handle)
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 0)
+    dom = max((k for k in kt if kt[k][1] > 0 and k != "other"), key=lambda k: kt[k][0])
+    dom_ms, dom_cnt = kt[dom]
+    avg_s = dom_ms / dom_cnt / 1e3
+    byt = algorithmic_bytes(dom, N, n_samp, WL.levels)
+    hbm, src = peaks()
+    achieved = byt / avg_s / 1e9
+    meas = MEASURED_TRAFFIC.get(dom)
+    traffic = meas["bytes_per_launch"] if meas and meas.get("source") == source_hash() else None
+    shares = {k: round(v[0] / sum(x[0] for x in kt.values()), 4) for k, v in kt.items()}
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                "algorithmic_bytes_per_launch": byt, "avg_launch_us": avg_s * 1e6,
+                "launches_per_step": {k: v[1] // reps for k, v in kt.items()},
+                "time_share": shares}
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    hy = torch.from_numpy(pr.y[None].copy()).pin_memory()
+    hm = torch.from_numpy(pr.mask[None].copy()).pin_memory()
+    hp = torch.from_numpy(pr.density[None].copy()).pin_memory()
+    hx = torch.empty((1, WL.ny, WL.nx), dtype=torch.complex64).pin_memory()
+    ht = torch.empty((1, K, plan.B), dtype=torch.float64).pin_memory()
+    hth, hal = torch.empty_like(ht).pin_memory(), torch.empty_like(ht).pin_memory()
+    lib = vb.load()
+    sig = vb._sigma_array([pr.sigma], 1)
+
+    def e2e_step():
+        vb.check(lib.vdamp_solve_host(plan.handle, 1, hy.data_ptr(), hm.data_ptr(),
+                                      hp.data_ptr(), sig, K, None, hx.data_ptr(), ht.data_ptr(),
+                                      hth.data_ptr(), hal.data_ptr(), stream.cuda_stream),
+                 "vdamp_solve_host")
+    for i in range(3):
+        e2e_step()
+    e2e_steps = max(10, min(args.steps, 200))
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        flush_buf.fill_(float(i))
+        torch.cuda.synchronize()
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * e2e_steps * K / e2e_s
+    h2d = 8 * N + N + 4 * N
+    d2h = 8 * N + 3 * 8 * K * plan.B
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded ellipse phantom, polynomial VD mask)",
+                "config": config_block(1, world),
+                "clocks": ClockSampler.summarize(rows),
+                "gpu_launches": launches_per_step * args.steps,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "roofline": roofline,
+                "wall_s_timed": wall}
+        if not args.no_cpu_baseline:
+            it, el = OracleRunner().run(args.cpu_seconds)
+            line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"{it} FP64 numpy oracle iterations of the same "
+                                              f"256x256 slice in {el:.1f} s (one core)"}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

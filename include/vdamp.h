@@ -1,0 +1,212 @@
+/*
+ * vdamp.h -- C ABI of the GB300 VDAMP library.
+ *
+ * VDAMP (variable-density approximate message passing, Algorithm 1 of
+ * Millard, Hess, Mailhe and Tanner, "An approximate message passing algorithm
+ * for rapid parameter-free compressed sensing MRI") reconstructs an image x0
+ * from y = Phi x0 + eps (Eq. 1) with Phi = M_Omega F (Sec. 1): F the unitary
+ * 2D DFT, M_Omega a Bernoulli variable-density row selection.  Every step of
+ * the iteration runs in this library's CUDA kernels (sm_103a); there is no
+ * CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex arrays are interleaved float32 (re, im) pairs, i.e. complex64.
+ * - Image and k-space arrays are [batch][ny][nx] row-major; k-space is
+ *   unshifted (DC at index 0, signed frequency i for i < n/2, else i - n).
+ *   F and F^H are unitary (1/sqrt(ny nx) each way).
+ * - Psi is an orthonormal periodic 2D wavelet transform with `levels` = s
+ *   scales: a[n] = sum_k h[k] x[(2n+k) mod L], d[n] = sum_k g[k] x[(2n+k) mod L],
+ *   g[k] = (-1)^k h[len-1-k], h the minimum-phase Daubechies filter
+ *   (Haar: 2 taps, DB4: 8 taps, 4 vanishing moments).
+ * - Wavelet coefficients are "packed": [batch][ny*nx] complex, the 1 + 3s
+ *   subbands of Eq. 6 stored one after another in the order
+ *   A_s, H_s, V_s, D_s, H_{s-1}, V_{s-1}, D_{s-1}, ..., H_1, V_1, D_1
+ *   (H high-pass along x, V along y, D along both), each row-major with
+ *   (ny >> j) x (nx >> j) entries at level j.  B = 1 + 3s.
+ * - Per-iteration outputs tau, thr, alpha are double [batch][iters][B]:
+ *   tau is the colored noise estimate of Algorithm 1 line 5, thr the
+ *   absolute soft threshold theta_b = lambda_b tau_b (same units as |r|) of
+ *   the SURE-tuned denoiser (Sec. 3), alpha the subband-mean derivative of
+ *   line 7.
+ * - "device" pointers must be CUDA device (or managed) memory of the current
+ *   device; "host" pointers ordinary CPU memory.  The caller owns every
+ *   buffer it passes; the plan owns its own workspace.
+ * - Calls that take a stream are asynchronous on it (NULL = legacy default
+ *   stream); they return VDAMP_EINVAL without launching anything when an
+ *   argument is invalid.  Errors met inside kernels (a non-finite tau or
+ *   alpha) are recorded in the plan and read with vdamp_device_status().
+ * - A plan may be used by one host thread at a time.
+ */
+#ifndef VDAMP_H
+#define VDAMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VDAMP_OK = 0,
+    VDAMP_EINVAL = 1,    /* invalid argument; nothing was launched          */
+    VDAMP_ENOMEM = 2,    /* a device or host allocation failed              */
+    VDAMP_ECUDA = 3,     /* a CUDA runtime call failed (see last_error)     */
+    VDAMP_ENUMERIC = 4,  /* tau or alpha became non-finite during a solve   */
+    VDAMP_ETIMEOUT = 5   /* a bounded device wait ran out                   */
+} vdamp_status;
+
+typedef enum { VDAMP_HAAR = 1, VDAMP_DB4 = 4 } vdamp_wavelet;
+
+typedef struct vdamp_plan vdamp_plan;
+
+/* Thread-local text of the last error raised by any call on this thread. */
+const char* vdamp_last_error(void);
+
+/*
+ * Create a plan for ny x nx slices with wavelet `wavelet` at `levels` scales
+ * (Algorithm 1 "Require": Psi; line 1: S = |Phi Psi^H|^2 is tabulated here
+ * from its 1 + 3s unique columns, Sec. 2).  Sizes: ny and nx divisible by
+ * 2^levels, of the form 2^a 3^b 5^c, 8 <= n <= 1024; 1 <= levels <= 6;
+ * 1 <= max_batch.  Allocates all device workspace for up to max_batch slices
+ * on the current device.  On success *out holds the plan; on failure *out is
+ * NULL and the status says why.
+ */
+vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int wavelet, int levels,
+                               int max_batch);
+
+/* Release the plan and its device memory (waits for its work to finish). */
+vdamp_status vdamp_plan_destroy(vdamp_plan* plan);
+
+/* Number of subbands B = 1 + 3 levels, or -1 for a NULL plan. */
+int vdamp_num_subbands(const vdamp_plan* plan);
+
+/* Bytes of device workspace the plan holds. */
+size_t vdamp_workspace_bytes(const vdamp_plan* plan);
+
+/* Option switches.
+ *   VDAMP_OPT_GRAPH (default 1): replay solves from a cached CUDA graph;
+ *     0 launches every kernel directly.
+ *   VDAMP_OPT_KERNEL_TIMING (default 0): launch directly and bracket every
+ *     kernel with CUDA events on its stream; read with vdamp_kernel_times(). */
+enum { VDAMP_OPT_GRAPH = 1, VDAMP_OPT_KERNEL_TIMING = 2 };
+vdamp_status vdamp_plan_set_option(vdamp_plan* plan, int option, int value);
+
+/* Kernel kinds reported by vdamp_kernel_times. */
+enum {
+    VDAMP_KERNEL_IDWT = 0,      /* one synthesis scale of Psi^H (+ line 8 / line 6 prologue) */
+    VDAMP_KERNEL_FFT_ROWS = 1,  /* row pass of F or F^H */
+    VDAMP_KERNEL_COL_PASS = 2,  /* column pass of F and F^H with lines 3-5 fused */
+    VDAMP_KERNEL_DWT = 3,       /* one analysis scale of Psi (+ r~ of line 4) */
+    VDAMP_KERNEL_SURE = 4,      /* SURE threshold, alpha, tau (lines 5-7) */
+    VDAMP_KERNEL_OTHER = 5,     /* line-8 write-out, sigma upload */
+    VDAMP_KERNEL_KINDS = 6
+};
+
+/* With VDAMP_OPT_KERNEL_TIMING on: wait for the timed launches, then add up
+ * their event-measured durations per kind since the last call.  ms and
+ * counts hold VDAMP_KERNEL_KINDS entries each (milliseconds, launches). */
+vdamp_status vdamp_kernel_times(vdamp_plan* plan, double* ms, int* counts);
+
+/* Number of kernel launches (graph kernel nodes included) made by the last
+ * solve/iterate/transform call on this plan. */
+int vdamp_last_launch_count(const vdamp_plan* plan);
+
+/*
+ * VDAMP solve, Algorithm 1 lines 1-10 with the SURE soft threshold of Sec. 3,
+ * on `batch` independent slices (1 <= batch <= max_batch).
+ *   y         device  [batch][ny][nx] complex64  measurements (ignored off the mask)
+ *   mask      device  [batch][ny][nx] uint8      1 where the frequency is sampled
+ *   density   device  [batch][ny][nx] float32    sampling probability p; 0 < p <= 1
+ *                                                wherever mask = 1 (P of Algorithm 1)
+ *   sigma     host    [batch] float32            noise level sigma_eps (Eq. 1), >= 0
+ *   iters     number of iterations K_it >= 1
+ *   r_tilde0  device  [batch][ny*nx] complex64 packed, or NULL: starting r~_0
+ *                     (NULL = 0 as in line 1; non-NULL resumes a stopped run)
+ *   x_hat     device  [batch][ny][nx] complex64 out: the return line applied to
+ *                     the last denoiser output
+ *   tau, thr, alpha  device  [batch][iters][B] double out (see conventions)
+ *   r_tilde_out      device  [batch][ny*nx] complex64 out or NULL: r~ after the
+ *                     last iteration (line 8), the state to resume from
+ *   x_hat_iters      device  [batch][iters][ny][nx] complex64 out or NULL: the
+ *                     return line applied to every w_hat_k (NMSE curves)
+ * Asynchronous on `stream` (a cudaStream_t).  A solve that hits a non-finite
+ * tau or alpha finishes its launches and records VDAMP_ENUMERIC for
+ * vdamp_device_status().
+ */
+vdamp_status vdamp_solve(vdamp_plan* plan, int batch, const float* y, const uint8_t* mask,
+                         const float* density, const float* sigma, int iters,
+                         const float* r_tilde0, float* x_hat, double* tau, double* thr,
+                         double* alpha, float* r_tilde_out, float* x_hat_iters, void* stream);
+
+/*
+ * The same solve on HOST buffers (same shapes as vdamp_solve; r_tilde0 may be
+ * NULL).  Copies inputs to the plan's device staging, solves on `stream`,
+ * copies x_hat, tau, thr and alpha back and waits.  Returns VDAMP_ENUMERIC
+ * if the solve met a non-finite tau or alpha.
+ */
+vdamp_status vdamp_solve_host(vdamp_plan* plan, int batch, const float* y, const uint8_t* mask,
+                              const float* density, const float* sigma, int iters,
+                              const float* r_tilde0, float* x_hat, double* tau, double* thr,
+                              double* alpha, void* stream);
+
+/*
+ * One pass of Algorithm 1 lines 3-8 from an explicit r~_k (device buffers as
+ * in vdamp_solve):
+ *   z_k = y - Phi Psi^H r~_k;  r_k = r~_k + Psi Phi^H P^{-1} z_k;
+ *   tau_k (line 5); w_hat_k, theta_k (line 6, Sec. 3); alpha_k (line 7);
+ *   r~_{k+1} = (w_hat_k - alpha_k r_k) / (1 - alpha_k) (line 8).
+ * Outputs: r (packed r_k), tau/thr/alpha [batch][B], r_tilde_next (packed).
+ */
+vdamp_status vdamp_iterate(vdamp_plan* plan, int batch, const float* r_tilde, const float* y,
+                           const uint8_t* mask, const float* density, const float* sigma,
+                           float* r, double* tau, double* thr, double* alpha,
+                           float* r_tilde_next, void* stream);
+
+/*
+ * Return line of Algorithm 1 for packed coefficients w (device):
+ *   x_hat = Psi^H w + Phi^H (y - Phi Psi^H w).
+ */
+vdamp_status vdamp_final_estimate(vdamp_plan* plan, int batch, const float* w, const float* y,
+                                  const uint8_t* mask, float* x_hat, void* stream);
+
+/* Transforms on their own (device buffers, [batch] slices):
+ *   vdamp_psi:    packed w = Psi x        (x image, [batch][ny][nx])
+ *   vdamp_psi_h:  image  x = Psi^H w
+ *   vdamp_fft2:   out = F in (inverse = 0) or F^H in (inverse = 1), unitary.
+ * in and out must not overlap. */
+vdamp_status vdamp_psi(vdamp_plan* plan, int batch, const float* x, float* w, void* stream);
+vdamp_status vdamp_psi_h(vdamp_plan* plan, int batch, const float* w, float* x, void* stream);
+vdamp_status vdamp_fft2(vdamp_plan* plan, int batch, const float* in, float* out, int inverse,
+                        void* stream);
+
+/*
+ * Wait for the plan's last call on `stream` and report what its kernels
+ * recorded: VDAMP_OK, or VDAMP_ENUMERIC with *iter (may be NULL) set to the
+ * first iteration whose tau or alpha was non-finite.  Clears the record.
+ */
+vdamp_status vdamp_device_status(vdamp_plan* plan, int* iter, void* stream);
+
+/* ---- host-only helpers (no GPU needed) ----------------------------------- */
+
+/* The plan's analysis low-pass filter h for `wavelet`, derived in double by
+ * Daubechies' spectral factorisation.  h must hold 8 doubles; *len gets the
+ * tap count (2 or 8). */
+vdamp_status vdamp_wavelet_filter(int wavelet, double* h, int* len);
+
+/*
+ * The 1D factors of S = |Phi Psi^H|^2 (Algorithm 1 line 1) along an axis of
+ * length n: out[(2(j-1) + t) * n + k], j = 1..levels, t = 0 for the level-j
+ * scaling atom and t = 1 for the level-j wavelet atom, is |F_n psi|^2 at
+ * frequency k.  Column b of S is the outer product of the y and x factors of
+ * its subband (A_s: scaling/scaling; H_j: scaling along y, wavelet along x;
+ * V_j: wavelet/scaling; D_j: wavelet/wavelet).  out holds 2*levels*n doubles.
+ */
+vdamp_status vdamp_subband_spectra(int wavelet, int levels, int n, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VDAMP_H */

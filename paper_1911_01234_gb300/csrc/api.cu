@@ -1,0 +1,963 @@
+// C ABI of the VDAMP library: plans, table setup and the launch sequence of
+// Algorithm 1.  See include/vdamp.h for the contract of every entry point.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/vdamp.h"
+#include "vdamp_internal.cuh"
+
+using vdamp::FftAxis;
+using vdamp::Filt;
+using vdamp::SrcSpec;
+
+// ------------------------------------------------------------- errors ---
+static thread_local std::string g_last_error;
+
+static vdamp_status fail(vdamp_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t _e = (expr);                                                          \
+        if (_e != cudaSuccess)                                                            \
+            return fail(VDAMP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// ------------------------------------------- filters (Daubechies 1988) ---
+using cd = std::complex<double>;
+
+static std::vector<cd> conv(const std::vector<cd>& a, const std::vector<cd>& b) {
+    std::vector<cd> o(a.size() + b.size() - 1, cd(0.0, 0.0));
+    for (size_t i = 0; i < a.size(); ++i)
+        for (size_t j = 0; j < b.size(); ++j) o[i + j] += a[i] * b[j];
+    return o;
+}
+
+// Minimum-phase Daubechies low-pass filter with p vanishing moments (2p taps):
+// |H(w)|^2 = 2 cos^{2p}(w/2) P(sin^2(w/2)), P(y) = sum_{k<p} C(p-1+k, k) y^k.
+// The roots of P are found by Durand-Kerner iteration; each root y_r gives
+// z^2 - (2 - 4 y_r) z + 1 = 0 whose root inside the unit circle is kept.
+static void daubechies(int p, double* h) {
+    std::vector<cd> poly{cd(1.0, 0.0)};
+    for (int i = 0; i < p; ++i) poly = conv(poly, {cd(0.5, 0.0), cd(0.5, 0.0)});
+    if (p > 1) {
+        const int d = p - 1;
+        std::vector<double> c(p);
+        for (int k = 0; k < p; ++k) {
+            double b = 1.0;  // C(p-1+k, k)
+            for (int i = 1; i <= k; ++i) b = b * (p - 1 + i) / i;
+            c[k] = b;
+        }
+        auto eval = [&](cd y) {
+            cd acc(0.0, 0.0);
+            for (int k = d; k >= 0; --k) acc = acc * y + c[k];
+            return acc / c[d];
+        };
+        std::vector<cd> z(d);
+        const cd seed(0.4, 0.9);
+        cd pw(1.0, 0.0);
+        for (int i = 0; i < d; ++i) {
+            z[i] = pw;
+            pw *= seed;
+        }
+        for (int it = 0; it < 1000; ++it) {
+            double delta = 0.0;
+            for (int i = 0; i < d; ++i) {
+                cd den(1.0, 0.0);
+                for (int j = 0; j < d; ++j)
+                    if (j != i) den *= (z[i] - z[j]);
+                cd step = eval(z[i]) / den;
+                z[i] -= step;
+                delta = std::max(delta, std::abs(step));
+            }
+            if (delta < 1e-16) break;
+        }
+        for (int i = 0; i < d; ++i) {
+            cd b = 2.0 - 4.0 * z[i];
+            cd disc = std::sqrt(b * b - 4.0);
+            cd z1 = (b + disc) / 2.0, z2 = (b - disc) / 2.0;
+            cd zr = std::abs(z1) < 1.0 ? z1 : z2;
+            poly = conv(poly, {cd(1.0, 0.0), -zr});
+            for (auto& q : poly) q /= (1.0 - zr);
+        }
+    }
+    for (int k = 0; k < 2 * p; ++k) h[k] = std::sqrt(2.0) * poly[k].real();
+}
+
+static int wavelet_taps(int wavelet) {
+    if (wavelet == VDAMP_HAAR) return 2;
+    if (wavelet == VDAMP_DB4) return 8;
+    return 0;
+}
+
+static double resp2(const double* f, int L, double w) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < L; ++k) {
+        re += f[k] * std::cos(w * k);
+        im -= f[k] * std::sin(w * k);
+    }
+    return re * re + im * im;
+}
+
+// 1D factors of S = |Phi Psi^H|^2 (Algorithm 1 line 1).  The level-j atoms
+// have DTFT prod_{l<j} H(2^l w) (scaling) and G(2^{j-1} w) prod_{l<j-1} H(2^l w)
+// (wavelet); the unitary DFT of the periodised atom samples it at 2 pi k / n.
+static void spectra(const double* h, int L, int levels, int n, double* out) {
+    double g[VDAMP_MAX_TAPS];
+    for (int k = 0; k < L; ++k) g[k] = ((k & 1) ? -1.0 : 1.0) * h[L - 1 - k];
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    for (int k = 0; k < n; ++k) {
+        double low = 1.0;  // prod_{l < j-1} |H(2^l w)|^2
+        long long m = k;
+        for (int j = 1; j <= levels; ++j) {
+            const double w = two_pi * (double)(m % n) / n;
+            out[(2 * (j - 1) + 1) * n + k] = low * resp2(g, L, w) / n;
+            low *= resp2(h, L, w);
+            out[(2 * (j - 1)) * n + k] = low / n;
+            m = (2 * m) % n;
+        }
+    }
+}
+
+// ----------------------------------------------------------- fft plan ---
+static bool fft_radices(int n, int* radix, int* nst) {
+    int m = n, a = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    int s = 0;
+    int e8 = a / 3, rem = a % 3;
+    if (rem == 1 && e8 > 0) { --e8; rem = 4; }
+    for (int i = 0; i < e8; ++i) radix[s++] = 8;
+    if (rem == 4) { radix[s++] = 4; radix[s++] = 4; }
+    else if (rem == 2) radix[s++] = 4;
+    else if (rem == 1) radix[s++] = 2;
+    while (m % 3 == 0) { radix[s++] = 3; m /= 3; }
+    while (m % 5 == 0) { radix[s++] = 5; m /= 5; }
+    *nst = s;
+    return m == 1 && s <= VDAMP_MAX_STAGES;
+}
+
+// -------------------------------------------------------------- plan ---
+namespace {
+struct GraphKey {
+    int kind, batch, iters;
+    const void* p[12];
+    bool operator==(const GraphKey& o) const {
+        if (kind != o.kind || batch != o.batch || iters != o.iters) return false;
+        for (int i = 0; i < 12; ++i)
+            if (p[i] != o.p[i]) return false;
+        return true;
+    }
+};
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec;
+    int launches;
+};
+struct SigmaBlock {
+    int n;
+    float v[512];
+};
+__global__ void set_sigma_kernel(float* dst, SigmaBlock b) {
+    if ((int)threadIdx.x < b.n) dst[threadIdx.x] = b.v[threadIdx.x];
+}
+}  // namespace
+
+struct vdamp_plan {
+    int ny, nx, levels, wavelet, B, max_batch;
+    size_t N;
+    Filt filt;
+    FftAxis axy, axx;
+    int off[VDAMP_MAX_BANDS + 1];
+    int ty[VDAMP_MAX_BANDS], tx[VDAMP_MAX_BANDS];
+    int cb, nparts, rpc;
+    float* ey = nullptr;
+    float* ex = nullptr;
+    float2* tw_y = nullptr;
+    float2* tw_x = nullptr;
+    float2* u = nullptr;
+    float2* kbuf = nullptr;
+    float2* ll0 = nullptr;
+    float2* ll1 = nullptr;
+    float2* rA = nullptr;
+    float2* rB = nullptr;
+    double* tau_part = nullptr;
+    float4* coef = nullptr;
+    float* sigma_d = nullptr;
+    int* status = nullptr;
+    // staging for the host-buffer entry point
+    float2* st_y = nullptr;
+    uint8_t* st_mask = nullptr;
+    float* st_p = nullptr;
+    float2* st_x = nullptr;
+    float2* st_r0 = nullptr;
+    double* st_out = nullptr;
+    size_t st_out_cap = 0;
+    size_t ws_bytes = 0;
+    int use_graph = 1;
+    int timing = 0;
+    int last_launches = 0;
+    std::vector<cudaEvent_t> ev_pool;       // timing events, reused
+    std::vector<std::pair<int, int>> ev_used;  // (kind, index of start event)
+    int ev_next = 0;
+    cudaStream_t cap = nullptr;
+    std::vector<GraphEntry> graphs;
+};
+
+static void plan_free(vdamp_plan* p) {
+    if (!p) return;
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& e : p->ev_pool) cudaEventDestroy(e);
+    void* bufs[] = {p->ey, p->ex, p->tw_y, p->tw_x, p->u, p->kbuf, p->ll0, p->ll1, p->rA,
+                    p->rB, p->tau_part, p->coef, p->sigma_d, p->status, p->st_y, p->st_mask,
+                    p->st_p, p->st_x, p->st_r0, p->st_out};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    delete p;
+}
+
+static bool fft_size_ok(int n) {
+    if (n < 8 || n > 1024) return false;
+    int m = n;
+    for (int f : {2, 3, 5})
+        while (m % f == 0) m /= f;
+    return m == 1;
+}
+
+extern "C" const char* vdamp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" vdamp_status vdamp_wavelet_filter(int wavelet, double* h, int* len) {
+    const int L = wavelet_taps(wavelet);
+    if (!L || !h || !len) return fail(VDAMP_EINVAL, "vdamp_wavelet_filter: bad wavelet or NULL");
+    daubechies(L / 2, h);
+    *len = L;
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_subband_spectra(int wavelet, int levels, int n, double* out) {
+    const int L = wavelet_taps(wavelet);
+    if (!L || levels < 1 || levels > VDAMP_MAX_LEVELS || n < 2 || !out)
+        return fail(VDAMP_EINVAL, "vdamp_subband_spectra: bad argument");
+    double h[VDAMP_MAX_TAPS];
+    daubechies(L / 2, h);
+    spectra(h, L, levels, n, out);
+    return VDAMP_OK;
+}
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t count, size_t* acc) {
+    *acc += count * sizeof(T);
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int wavelet,
+                                          int levels, int max_batch) {
+    if (!out) return fail(VDAMP_EINVAL, "vdamp_plan_create: out is NULL");
+    *out = nullptr;
+    const int L = wavelet_taps(wavelet);
+    if (!L) return fail(VDAMP_EINVAL, "vdamp_plan_create: wavelet must be VDAMP_HAAR or VDAMP_DB4");
+    if (levels < 1 || levels > VDAMP_MAX_LEVELS)
+        return fail(VDAMP_EINVAL, "vdamp_plan_create: levels must be in [1, 6]");
+    if (!fft_size_ok(ny) || !fft_size_ok(nx))
+        return fail(VDAMP_EINVAL, "vdamp_plan_create: ny, nx must be 2^a 3^b 5^c in [8, 1024]");
+    if ((ny % (1 << levels)) || (nx % (1 << levels)))
+        return fail(VDAMP_EINVAL, "vdamp_plan_create: ny and nx must be divisible by 2^levels");
+    if (max_batch < 1) return fail(VDAMP_EINVAL, "vdamp_plan_create: max_batch must be >= 1");
+    const size_t N = (size_t)ny * nx;
+    const int max_band = (int)(N / 4);
+    if (vdamp::sure_smem(max_band) > 227 * 1024)
+        return fail(VDAMP_EINVAL, "vdamp_plan_create: finest subband exceeds 32768 coefficients");
+
+    vdamp_plan* p = new vdamp_plan();
+    p->ny = ny;
+    p->nx = nx;
+    p->levels = levels;
+    p->wavelet = wavelet;
+    p->B = 1 + 3 * levels;
+    p->max_batch = max_batch;
+    p->N = N;
+
+    double h[VDAMP_MAX_TAPS];
+    daubechies(L / 2, h);
+    p->filt.L = L;
+    for (int k = 0; k < VDAMP_MAX_TAPS; ++k) {
+        p->filt.h[k] = k < L ? (float)h[k] : 0.f;
+        p->filt.g[k] = k < L ? (float)(((k & 1) ? -1.0 : 1.0) * h[L - 1 - k]) : 0.f;
+    }
+    // packed subband offsets and the spectra each subband takes along y and x
+    p->off[0] = 0;
+    p->ty[0] = p->tx[0] = 2 * (levels - 1);
+    int o = (ny >> levels) * (nx >> levels);
+    int b = 1;
+    for (int j = levels; j >= 1; --j) {
+        const int sz = (ny >> j) * (nx >> j);
+        const int lo = 2 * (j - 1), hi = 2 * (j - 1) + 1;
+        const int tys[3] = {lo, hi, hi}, txs[3] = {hi, lo, hi};  // H, V, D
+        for (int q = 0; q < 3; ++q) {
+            p->off[b] = o;
+            p->ty[b] = tys[q];
+            p->tx[b] = txs[q];
+            o += sz;
+            ++b;
+        }
+    }
+    p->off[p->B] = o;
+
+    int cb = 8;
+    while (nx % cb) cb >>= 1;
+    p->cb = cb;
+    p->nparts = nx / cb;
+    p->rpc = std::max(1, 512 / nx);
+
+    p->axy.n = ny;
+    p->axx.n = nx;
+    if (!fft_radices(ny, p->axy.radix, &p->axy.nstages) ||
+        !fft_radices(nx, p->axx.radix, &p->axx.nstages)) {
+        plan_free(p);
+        return fail(VDAMP_EINVAL, "vdamp_plan_create: no radix plan");
+    }
+
+    size_t acc = 0;
+    cudaError_t e = cudaSuccess;
+    const size_t MB = (size_t)max_batch;
+    const int nt = 2 * levels;
+    auto A = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    A(dalloc(&p->ey, (size_t)nt * ny, &acc));
+    A(dalloc(&p->ex, (size_t)nt * nx, &acc));
+    A(dalloc(&p->tw_y, (size_t)ny, &acc));
+    A(dalloc(&p->tw_x, (size_t)nx, &acc));
+    A(dalloc(&p->u, MB * N, &acc));
+    A(dalloc(&p->kbuf, MB * N, &acc));
+    A(dalloc(&p->ll0, MB * N / 4, &acc));
+    A(dalloc(&p->ll1, MB * N / 4, &acc));
+    A(dalloc(&p->rA, MB * N, &acc));
+    A(dalloc(&p->rB, MB * N, &acc));
+    A(dalloc(&p->tau_part, MB * p->nparts * p->B, &acc));
+    A(dalloc(&p->coef, MB * p->B, &acc));
+    A(dalloc(&p->sigma_d, MB, &acc));
+    A(dalloc(&p->status, (size_t)2, &acc));
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return fail(e == cudaErrorMemoryAllocation ? VDAMP_ENOMEM : VDAMP_ECUDA,
+                    std::string("vdamp_plan_create: ") + cudaGetErrorString(e));
+    }
+    p->ws_bytes = acc;
+
+    // tables
+    std::vector<double> sy((size_t)nt * ny), sx((size_t)nt * nx);
+    spectra(h, L, levels, ny, sy.data());
+    spectra(h, L, levels, nx, sx.data());
+    std::vector<float> fy(sy.begin(), sy.end()), fx(sx.begin(), sx.end());
+    std::vector<float2> twy(ny), twx(nx);
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    for (int k = 0; k < ny; ++k)
+        twy[k] = make_float2((float)std::cos(two_pi * k / ny), (float)-std::sin(two_pi * k / ny));
+    for (int k = 0; k < nx; ++k)
+        twx[k] = make_float2((float)std::cos(two_pi * k / nx), (float)-std::sin(two_pi * k / nx));
+    A(cudaMemcpy(p->ey, fy.data(), fy.size() * sizeof(float), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(p->ex, fx.data(), fx.size() * sizeof(float), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(p->tw_y, twy.data(), ny * sizeof(float2), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(p->tw_x, twx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice));
+    A(cudaMemset(p->status, 0, 2 * sizeof(int)));
+    A(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    A(vdamp::configure_col_pass(vdamp::col_pass_smem(ny, cb, nt)));
+    A(vdamp::configure_fft_rows(2 * (size_t)p->rpc * nx * sizeof(float2)));
+    A(vdamp::configure_sure(vdamp::sure_smem(max_band)));
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return fail(VDAMP_ECUDA, std::string("vdamp_plan_create: ") + cudaGetErrorString(e));
+    }
+    p->axy.tw = p->tw_y;
+    p->axx.tw = p->tw_x;
+    *out = p;
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_plan_destroy(vdamp_plan* p) {
+    if (!p) return fail(VDAMP_EINVAL, "vdamp_plan_destroy: NULL plan");
+    cudaDeviceSynchronize();
+    plan_free(p);
+    return VDAMP_OK;
+}
+
+extern "C" int vdamp_num_subbands(const vdamp_plan* p) { return p ? p->B : -1; }
+extern "C" size_t vdamp_workspace_bytes(const vdamp_plan* p) { return p ? p->ws_bytes : 0; }
+extern "C" int vdamp_last_launch_count(const vdamp_plan* p) { return p ? p->last_launches : -1; }
+
+extern "C" vdamp_status vdamp_plan_set_option(vdamp_plan* p, int option, int value) {
+    if (!p) return fail(VDAMP_EINVAL, "vdamp_plan_set_option: NULL plan");
+    if (option == VDAMP_OPT_GRAPH) {
+        p->use_graph = value ? 1 : 0;
+        return VDAMP_OK;
+    }
+    if (option == VDAMP_OPT_KERNEL_TIMING) {
+        p->timing = value ? 1 : 0;
+        return VDAMP_OK;
+    }
+    return fail(VDAMP_EINVAL, "vdamp_plan_set_option: unknown option");
+}
+
+// ------------------------------------------------------ launch helpers ---
+namespace {
+
+struct Ctx {
+    vdamp_plan* p;
+    int batch;
+    cudaStream_t st;
+    int launches = 0;
+    cudaError_t err = cudaSuccess;
+    bool timed = false;
+    int ev_start = -1;
+    cudaEvent_t ev(int i) {
+        while ((int)p->ev_pool.size() <= i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            p->ev_pool.push_back(e);
+        }
+        return p->ev_pool[i];
+    }
+    // call before a launch
+    void pre() {
+        if (!timed) return;
+        ev_start = p->ev_next;
+        p->ev_next += 2;
+        cudaEvent_t e = ev(ev_start);
+        if (e) cudaEventRecord(e, st);
+    }
+    // call after a launch with its status and kind
+    void chk(cudaError_t e, int kind) {
+        ++launches;
+        if (err == cudaSuccess) err = e;
+        if (timed && ev_start >= 0) {
+            cudaEvent_t f = ev(ev_start + 1);
+            if (f) {
+                cudaEventRecord(f, st);
+                p->ev_used.push_back({kind, ev_start});
+            }
+            ev_start = -1;
+        }
+    }
+};
+
+SrcSpec make_src(const vdamp_plan* p, int mode, const float2* r) {
+    SrcSpec s;
+    s.mode = mode;
+    s.r = r;
+    s.coef = p->coef;
+    s.B = p->B;
+    return s;
+}
+
+// x = Psi^H (src), levels s .. 1
+void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
+    vdamp_plan* p = c.p;
+    const int s = p->levels;
+    const float2* ll_in = nullptr;
+    for (int j = s; j >= 1; --j) {
+        vdamp::IdwtArgs a;
+        a.ll_in = ll_in;
+        a.ll_stride = p->N / 4;
+        a.h = p->ny >> j;
+        a.w = p->nx >> j;
+        a.first = (j == s);
+        a.out = (j == 1) ? img : (((s - j) & 1) ? p->ll1 : p->ll0);
+        a.out_stride = (j == 1) ? p->N : p->N / 4;
+        a.N = p->N;
+        const int bh = 1 + 3 * (s - j);
+        a.off[0] = p->off[0];
+        a.off[1] = p->off[bh];
+        a.off[2] = p->off[bh + 1];
+        a.off[3] = p->off[bh + 2];
+        a.band[0] = 0;
+        a.band[1] = bh;
+        a.band[2] = bh + 1;
+        a.band[3] = bh + 2;
+        a.src = src;
+        a.f = p->filt;
+        c.pre();
+        c.chk(vdamp::launch_idwt_level(a, c.batch, c.st), VDAMP_KERNEL_IDWT);
+        ll_in = a.out;
+    }
+}
+
+// packed = Psi img + src (levels 1 .. s)
+void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
+    vdamp_plan* p = c.p;
+    const int s = p->levels;
+    const float2* in = img;
+    size_t in_stride = p->N;
+    for (int j = 1; j <= s; ++j) {
+        vdamp::DwtArgs a;
+        a.in = in;
+        a.in_stride = in_stride;
+        a.H = p->ny >> (j - 1);
+        a.W = p->nx >> (j - 1);
+        a.last = (j == s);
+        a.ll_out = (j & 1) ? p->ll0 : p->ll1;
+        a.ll_stride = p->N / 4;
+        a.packed = packed;
+        a.N = p->N;
+        const int bh = 1 + 3 * (s - j);
+        a.off[0] = p->off[0];
+        a.off[1] = p->off[bh];
+        a.off[2] = p->off[bh + 1];
+        a.off[3] = p->off[bh + 2];
+        a.band[0] = 0;
+        a.band[1] = bh;
+        a.band[2] = bh + 1;
+        a.band[3] = bh + 2;
+        a.src = src;
+        a.f = p->filt;
+        c.pre();
+        c.chk(vdamp::launch_dwt_level(a, c.batch, c.st), VDAMP_KERNEL_DWT);
+        in = a.ll_out;
+        in_stride = p->N / 4;
+    }
+}
+
+vdamp::ColArgs col_args(const vdamp_plan* p, int mode, const float2* in, float2* out,
+                        const float2* y, const uint8_t* mask, const float* density) {
+    vdamp::ColArgs a;
+    memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.ny = p->ny;
+    a.nx = p->nx;
+    a.cb = p->cb;
+    a.ax = p->axy;
+    a.mode = mode;
+    a.u_zero = 0;
+    const float isn = (float)(1.0 / std::sqrt((double)p->N));
+    a.scale_fwd = isn;
+    a.scale_inv = 1.0f;
+    a.y = y;
+    a.mask = mask;
+    a.density = density;
+    a.sigma = p->sigma_d;
+    a.ey = p->ey;
+    a.ex = p->ex;
+    a.ntypes = 2 * p->levels;
+    a.B = p->B;
+    for (int b = 0; b < p->B; ++b) {
+        a.ty[b] = p->ty[b];
+        a.tx[b] = p->tx[b];
+    }
+    a.tau_part = p->tau_part;
+    return a;
+}
+
+float inv_sqrt_n(const vdamp_plan* p) { return (float)(1.0 / std::sqrt((double)p->N)); }
+
+// k-space part of one iteration: from the image u (or zero) to u' = F^H P^-1 z
+void enq_kspace_iter(Ctx& c, bool u_zero, const float2* y, const uint8_t* mask,
+                     const float* density) {
+    vdamp_plan* p = c.p;
+    if (!u_zero)
+        c.pre();
+        c.chk(vdamp::launch_fft_rows(p->u, p->kbuf, p->ny, p->nx, c.batch, p->axx, 0, 1.0f,
+                                     p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+    vdamp::ColArgs a = col_args(p, vdamp::COL_ITER, p->kbuf, p->kbuf, y, mask, density);
+    a.u_zero = u_zero ? 1 : 0;
+    c.pre();
+    c.chk(vdamp::launch_col_pass(a, c.batch, c.st), VDAMP_KERNEL_COL_PASS);
+    c.pre();
+    c.chk(vdamp::launch_fft_rows(p->kbuf, p->u, p->ny, p->nx, c.batch, p->axx, 1, inv_sqrt_n(p),
+                                 p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+}
+
+// return line: x = u + F^H M^T (y - M F u) with u = Psi^H (src)
+void enq_final(Ctx& c, const SrcSpec& src, const float2* y, const uint8_t* mask, float2* x) {
+    vdamp_plan* p = c.p;
+    enq_psi_h(c, src, p->u);
+    c.pre();
+    c.chk(vdamp::launch_fft_rows(p->u, p->kbuf, p->ny, p->nx, c.batch, p->axx, 0, 1.0f, p->rpc,
+                                 c.st), VDAMP_KERNEL_FFT_ROWS);
+    vdamp::ColArgs a = col_args(p, vdamp::COL_FINAL, p->kbuf, p->kbuf, y, mask, nullptr);
+    c.pre();
+    c.chk(vdamp::launch_col_pass(a, c.batch, c.st), VDAMP_KERNEL_COL_PASS);
+    c.pre();
+    c.chk(vdamp::launch_fft_rows(p->kbuf, x, p->ny, p->nx, c.batch, p->axx, 1, inv_sqrt_n(p),
+                                 p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+}
+
+void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* thr,
+              double* alpha) {
+    vdamp_plan* p = c.p;
+    vdamp::SureArgs a;
+    a.r = r;
+    a.N = p->N;
+    a.B = p->B;
+    for (int b = 0; b <= p->B; ++b) a.off[b] = p->off[b];
+    a.tau_part = p->tau_part;
+    a.nparts = p->nparts;
+    a.iters = iters;
+    a.k = k;
+    a.tau_out = tau;
+    a.thr_out = thr;
+    a.alpha_out = alpha;
+    a.coef = p->coef;
+    a.status = p->status;
+    c.pre();
+    c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), c.st), VDAMP_KERNEL_SURE);
+}
+
+void enq_line8(Ctx& c, const float2* r, float2* out) {
+    vdamp_plan* p = c.p;
+    vdamp::Line8Args a;
+    a.src = make_src(p, vdamp::SRC_LINE8, r);
+    a.out = out;
+    a.N = p->N;
+    a.B = p->B;
+    for (int b = 0; b <= p->B; ++b) a.off[b] = p->off[b];
+    c.pre();
+    c.chk(vdamp::launch_line8(a, c.batch, c.st), VDAMP_KERNEL_OTHER);
+}
+
+struct SolveArgs {
+    const float2* y;
+    const uint8_t* mask;
+    const float* density;
+    int iters;
+    const float2* r_tilde0;
+    float2* x_hat;
+    double *tau, *thr, *alpha;
+    float2* r_tilde_out;
+    float2* x_hat_iters;
+};
+
+// Algorithm 1, lines 1-10.
+void enq_solve(Ctx& c, const SolveArgs& s) {
+    vdamp_plan* p = c.p;
+    if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status, 0, sizeof(int), c.st);
+    if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
+    float2* prev = p->rA;  // r_{k-1}
+    float2* cur = p->rB;   // r_k
+    for (int k = 0; k < s.iters; ++k) {
+        SrcSpec src;
+        bool zero = false;
+        if (k == 0) {
+            zero = (s.r_tilde0 == nullptr);
+            src = make_src(p, zero ? vdamp::SRC_ZERO : vdamp::SRC_EXPLICIT, s.r_tilde0);
+        } else {
+            src = make_src(p, vdamp::SRC_LINE8, prev);
+        }
+        if (!zero) enq_psi_h(c, src, p->u);            // Psi^H r~_k        (line 3)
+        enq_kspace_iter(c, zero, s.y, s.mask, s.density);  // z, tau parts, F^H P^-1 z (3-5)
+        enq_psi(c, p->u, cur, src);                     // r_k = r~_k + Psi u' (line 4)
+        enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha);  // tau, theta, alpha (5-7)
+        if (s.x_hat_iters)
+            enq_final(c, make_src(p, vdamp::SRC_SOFT, cur), s.y, s.mask,
+                      s.x_hat_iters + (size_t)k * p->N);
+        float2* t = prev;
+        prev = cur;
+        cur = t;
+    }
+    enq_final(c, make_src(p, vdamp::SRC_SOFT, prev), s.y, s.mask, s.x_hat);  // return line
+    if (s.r_tilde_out) enq_line8(c, prev, s.r_tilde_out);                      // line 8
+}
+
+vdamp_status set_sigma(vdamp_plan* p, const float* sigma, int batch, cudaStream_t st,
+                       int* launches) {
+    for (int b0 = 0; b0 < batch; b0 += 512) {
+        SigmaBlock blk;
+        blk.n = std::min(512, batch - b0);
+        for (int i = 0; i < blk.n; ++i) blk.v[i] = sigma[b0 + i];
+        set_sigma_kernel<<<1, 512, 0, st>>>(p->sigma_d + b0, blk);
+        CUDA_TRY(cudaGetLastError());
+        ++*launches;
+    }
+    return VDAMP_OK;
+}
+
+vdamp_status check_common(vdamp_plan* p, int batch, const char* who) {
+    if (!p) return fail(VDAMP_EINVAL, std::string(who) + ": NULL plan");
+    if (batch < 1 || batch > p->max_batch)
+        return fail(VDAMP_EINVAL, std::string(who) + ": batch outside [1, max_batch]");
+    return VDAMP_OK;
+}
+
+vdamp_status check_sigma(const float* sigma, int batch, const char* who) {
+    if (!sigma) return fail(VDAMP_EINVAL, std::string(who) + ": sigma is NULL");
+    for (int i = 0; i < batch; ++i)
+        if (!(sigma[i] >= 0.f) || !std::isfinite(sigma[i]))
+            return fail(VDAMP_EINVAL, std::string(who) + ": sigma must be finite and >= 0");
+    return VDAMP_OK;
+}
+
+}  // namespace
+
+extern "C" vdamp_status vdamp_solve(vdamp_plan* p, int batch, const float* y, const uint8_t* mask,
+                                    const float* density, const float* sigma, int iters,
+                                    const float* r_tilde0, float* x_hat, double* tau, double* thr,
+                                    double* alpha, float* r_tilde_out, float* x_hat_iters,
+                                    void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_solve");
+    if (st != VDAMP_OK) return st;
+    if (!y || !mask || !density || !x_hat || !tau || !thr || !alpha)
+        return fail(VDAMP_EINVAL, "vdamp_solve: a required pointer is NULL");
+    if (iters < 1) return fail(VDAMP_EINVAL, "vdamp_solve: iters must be >= 1");
+    if ((st = check_sigma(sigma, batch, "vdamp_solve")) != VDAMP_OK) return st;
+    cudaStream_t us = (cudaStream_t)stream;
+    int launches = 0;
+    if ((st = set_sigma(p, sigma, batch, us, &launches)) != VDAMP_OK) return st;
+
+    SolveArgs s;
+    s.y = (const float2*)y;
+    s.mask = mask;
+    s.density = density;
+    s.iters = iters;
+    s.r_tilde0 = (const float2*)r_tilde0;
+    s.x_hat = (float2*)x_hat;
+    s.tau = tau;
+    s.thr = thr;
+    s.alpha = alpha;
+    s.r_tilde_out = (float2*)r_tilde_out;
+    s.x_hat_iters = (float2*)x_hat_iters;
+
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(us, &cs));
+    if (p->use_graph && !p->timing && cs == cudaStreamCaptureStatusNone) {
+        GraphKey key;
+        memset(&key, 0, sizeof(key));
+        key.kind = 1;
+        key.batch = batch;
+        key.iters = iters;
+        const void* ptrs[] = {y, mask, density, r_tilde0, x_hat, tau, thr, alpha, r_tilde_out,
+                              x_hat_iters};
+        for (int i = 0; i < 10; ++i) key.p[i] = ptrs[i];
+        GraphEntry* hit = nullptr;
+        for (auto& g : p->graphs)
+            if (g.key == key) hit = &g;
+        if (!hit) {
+            Ctx c{p, batch, p->cap};
+            CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+            enq_solve(c, s);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
+            if (c.err != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return fail(VDAMP_ECUDA, std::string("vdamp_solve capture: ") +
+                                             cudaGetErrorString(c.err != cudaSuccess ? c.err : e2));
+            }
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess)
+                return fail(VDAMP_ECUDA, std::string("vdamp_solve instantiate: ") +
+                                             cudaGetErrorString(e3));
+            if (p->graphs.size() >= 16) {
+                cudaGraphExecDestroy(p->graphs.front().exec);
+                p->graphs.erase(p->graphs.begin());
+            }
+            p->graphs.push_back(GraphEntry{key, exec, c.launches});
+            hit = &p->graphs.back();
+        }
+        CUDA_TRY(cudaGraphLaunch(hit->exec, us));
+        p->last_launches = launches + hit->launches;
+        return VDAMP_OK;
+    }
+    Ctx c{p, batch, us};
+    c.timed = p->timing != 0;
+    enq_solve(c, s);
+    p->last_launches = launches + c.launches;
+    if (c.err != cudaSuccess)
+        return fail(VDAMP_ECUDA, std::string("vdamp_solve: ") + cudaGetErrorString(c.err));
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_solve_host(vdamp_plan* p, int batch, const float* y,
+                                         const uint8_t* mask, const float* density,
+                                         const float* sigma, int iters, const float* r_tilde0,
+                                         float* x_hat, double* tau, double* thr, double* alpha,
+                                         void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_solve_host");
+    if (st != VDAMP_OK) return st;
+    if (!y || !mask || !density || !x_hat || !tau || !thr || !alpha)
+        return fail(VDAMP_EINVAL, "vdamp_solve_host: a required pointer is NULL");
+    if (iters < 1) return fail(VDAMP_EINVAL, "vdamp_solve_host: iters must be >= 1");
+    if ((st = check_sigma(sigma, batch, "vdamp_solve_host")) != VDAMP_OK) return st;
+    const size_t MB = (size_t)p->max_batch, N = p->N;
+    if (!p->st_y) {
+        cudaError_t e = cudaSuccess;
+        size_t acc = 0;
+        auto A = [&](cudaError_t r) {
+            if (e == cudaSuccess) e = r;
+        };
+        A(dalloc(&p->st_y, MB * N, &acc));
+        A(dalloc(&p->st_mask, MB * N, &acc));
+        A(dalloc(&p->st_p, MB * N, &acc));
+        A(dalloc(&p->st_x, MB * N, &acc));
+        A(dalloc(&p->st_r0, MB * N, &acc));
+        if (e != cudaSuccess)
+            return fail(VDAMP_ENOMEM, std::string("vdamp_solve_host: ") + cudaGetErrorString(e));
+        p->ws_bytes += acc;
+    }
+    const size_t nout = (size_t)batch * iters * p->B;
+    if (p->st_out_cap < 3 * nout) {
+        if (p->st_out) cudaFree(p->st_out);
+        p->st_out = nullptr;
+        p->st_out_cap = 0;
+        size_t acc = 0;
+        if (dalloc(&p->st_out, 3 * nout, &acc) != cudaSuccess)
+            return fail(VDAMP_ENOMEM, "vdamp_solve_host: output staging");
+        p->st_out_cap = 3 * nout;
+    }
+    cudaStream_t us = (cudaStream_t)stream;
+    const size_t n = (size_t)batch * N;
+    CUDA_TRY(cudaMemcpyAsync(p->st_y, y, n * sizeof(float2), cudaMemcpyHostToDevice, us));
+    CUDA_TRY(cudaMemcpyAsync(p->st_mask, mask, n, cudaMemcpyHostToDevice, us));
+    CUDA_TRY(cudaMemcpyAsync(p->st_p, density, n * sizeof(float), cudaMemcpyHostToDevice, us));
+    if (r_tilde0)
+        CUDA_TRY(cudaMemcpyAsync(p->st_r0, r_tilde0, n * sizeof(float2), cudaMemcpyHostToDevice,
+                                 us));
+    st = vdamp_solve(p, batch, (const float*)p->st_y, p->st_mask, p->st_p, sigma, iters,
+                     r_tilde0 ? (const float*)p->st_r0 : nullptr, (float*)p->st_x, p->st_out,
+                     p->st_out + nout, p->st_out + 2 * nout, nullptr, nullptr, stream);
+    if (st != VDAMP_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(x_hat, p->st_x, n * sizeof(float2), cudaMemcpyDeviceToHost, us));
+    CUDA_TRY(cudaMemcpyAsync(tau, p->st_out, nout * sizeof(double), cudaMemcpyDeviceToHost, us));
+    CUDA_TRY(cudaMemcpyAsync(thr, p->st_out + nout, nout * sizeof(double), cudaMemcpyDeviceToHost,
+                             us));
+    CUDA_TRY(cudaMemcpyAsync(alpha, p->st_out + 2 * nout, nout * sizeof(double),
+                             cudaMemcpyDeviceToHost, us));
+    int it = 0;
+    return vdamp_device_status(p, &it, stream);
+}
+
+extern "C" vdamp_status vdamp_iterate(vdamp_plan* p, int batch, const float* r_tilde,
+                                      const float* y, const uint8_t* mask, const float* density,
+                                      const float* sigma, float* r, double* tau, double* thr,
+                                      double* alpha, float* r_tilde_next, void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_iterate");
+    if (st != VDAMP_OK) return st;
+    if (!r_tilde || !y || !mask || !density || !r || !tau || !thr || !alpha || !r_tilde_next)
+        return fail(VDAMP_EINVAL, "vdamp_iterate: a pointer is NULL");
+    if (r == r_tilde) return fail(VDAMP_EINVAL, "vdamp_iterate: r must not alias r_tilde");
+    if ((st = check_sigma(sigma, batch, "vdamp_iterate")) != VDAMP_OK) return st;
+    cudaStream_t us = (cudaStream_t)stream;
+    int launches = 0;
+    if ((st = set_sigma(p, sigma, batch, us, &launches)) != VDAMP_OK) return st;
+    Ctx c{p, batch, us};
+    c.timed = p->timing != 0;
+    if (cudaMemsetAsync(p->status, 0, sizeof(int), us) != cudaSuccess ||
+        cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), us) != cudaSuccess)
+        return fail(VDAMP_ECUDA, "vdamp_iterate: memset");
+    SrcSpec src = make_src(p, vdamp::SRC_EXPLICIT, (const float2*)r_tilde);
+    enq_psi_h(c, src, p->u);
+    enq_kspace_iter(c, false, (const float2*)y, mask, density);
+    enq_psi(c, p->u, (float2*)r, src);
+    enq_sure(c, (const float2*)r, 1, 0, tau, thr, alpha);
+    enq_line8(c, (const float2*)r, (float2*)r_tilde_next);
+    p->last_launches = launches + c.launches;
+    if (c.err != cudaSuccess)
+        return fail(VDAMP_ECUDA, std::string("vdamp_iterate: ") + cudaGetErrorString(c.err));
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_final_estimate(vdamp_plan* p, int batch, const float* w,
+                                             const float* y, const uint8_t* mask, float* x_hat,
+                                             void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_final_estimate");
+    if (st != VDAMP_OK) return st;
+    if (!w || !y || !mask || !x_hat) return fail(VDAMP_EINVAL, "vdamp_final_estimate: NULL");
+    Ctx c{p, batch, (cudaStream_t)stream};
+    c.timed = p->timing != 0;
+    enq_final(c, make_src(p, vdamp::SRC_EXPLICIT, (const float2*)w), (const float2*)y, mask,
+              (float2*)x_hat);
+    p->last_launches = c.launches;
+    if (c.err != cudaSuccess)
+        return fail(VDAMP_ECUDA, std::string("vdamp_final_estimate: ") + cudaGetErrorString(c.err));
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_psi(vdamp_plan* p, int batch, const float* x, float* w,
+                                  void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_psi");
+    if (st != VDAMP_OK) return st;
+    if (!x || !w) return fail(VDAMP_EINVAL, "vdamp_psi: NULL");
+    Ctx c{p, batch, (cudaStream_t)stream};
+    c.timed = p->timing != 0;
+    enq_psi(c, (const float2*)x, (float2*)w, make_src(p, vdamp::SRC_ZERO, nullptr));
+    p->last_launches = c.launches;
+    if (c.err != cudaSuccess)
+        return fail(VDAMP_ECUDA, std::string("vdamp_psi: ") + cudaGetErrorString(c.err));
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_psi_h(vdamp_plan* p, int batch, const float* w, float* x,
+                                    void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_psi_h");
+    if (st != VDAMP_OK) return st;
+    if (!x || !w) return fail(VDAMP_EINVAL, "vdamp_psi_h: NULL");
+    Ctx c{p, batch, (cudaStream_t)stream};
+    c.timed = p->timing != 0;
+    enq_psi_h(c, make_src(p, vdamp::SRC_EXPLICIT, (const float2*)w), (float2*)x);
+    p->last_launches = c.launches;
+    if (c.err != cudaSuccess)
+        return fail(VDAMP_ECUDA, std::string("vdamp_psi_h: ") + cudaGetErrorString(c.err));
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_fft2(vdamp_plan* p, int batch, const float* in, float* out,
+                                   int inverse, void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_fft2");
+    if (st != VDAMP_OK) return st;
+    if (!in || !out || in == out) return fail(VDAMP_EINVAL, "vdamp_fft2: NULL or aliased");
+    Ctx c{p, batch, (cudaStream_t)stream};
+    c.timed = p->timing != 0;
+    c.pre();
+    c.chk(vdamp::launch_fft_rows((const float2*)in, (float2*)out, p->ny, p->nx, batch, p->axx,
+                                 inverse ? 1 : 0, 1.0f, p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+    vdamp::ColArgs a = col_args(p, inverse ? vdamp::COL_INV : vdamp::COL_FWD, (float2*)out,
+                                (float2*)out, nullptr, nullptr, nullptr);
+    a.scale_inv = inv_sqrt_n(p);
+    c.pre();
+    c.chk(vdamp::launch_col_pass(a, batch, c.st), VDAMP_KERNEL_COL_PASS);
+    p->last_launches = c.launches;
+    if (c.err != cudaSuccess)
+        return fail(VDAMP_ECUDA, std::string("vdamp_fft2: ") + cudaGetErrorString(c.err));
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_device_status(vdamp_plan* p, int* iter, void* stream) {
+    if (!p) return fail(VDAMP_EINVAL, "vdamp_device_status: NULL plan");
+    cudaStream_t us = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamSynchronize(us));
+    int h[2] = {0, 0};
+    CUDA_TRY(cudaMemcpy(h, p->status, sizeof(h), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+    if (h[0] == VDAMP_ENUMERIC) {
+        if (iter) *iter = h[1];
+        return fail(VDAMP_ENUMERIC, "non-finite tau or alpha at iteration " + std::to_string(h[1]));
+    }
+    if (iter) *iter = -1;
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_kernel_times(vdamp_plan* p, double* ms, int* counts) {
+    if (!p || !ms || !counts) return fail(VDAMP_EINVAL, "vdamp_kernel_times: NULL");
+    for (int k = 0; k < VDAMP_KERNEL_KINDS; ++k) {
+        ms[k] = 0.0;
+        counts[k] = 0;
+    }
+    for (auto& u : p->ev_used) {
+        cudaEvent_t a = p->ev_pool[u.second], b = p->ev_pool[u.second + 1];
+        CUDA_TRY(cudaEventSynchronize(b));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+        ms[u.first] += t;
+        counts[u.first] += 1;
+    }
+    p->ev_used.clear();
+    p->ev_next = 0;
+    return VDAMP_OK;
+}

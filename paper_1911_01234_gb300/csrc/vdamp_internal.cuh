@@ -1,0 +1,175 @@
+// Internal declarations shared by the VDAMP CUDA translation units.
+//
+// Data layout (all per slice, slices contiguous):
+//   image / k-space : float2 [ny][nx], k-space unshifted
+//   packed wavelet  : float2 [ny*nx], subbands A_s, H_s, V_s, D_s, ..., D_1
+//   coef            : float4 [B] per slice = (theta, alpha, 1/(1-alpha), 0):
+//                     what the denoiser of the previous iteration chose
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define VDAMP_MAX_LEVELS 6
+#define VDAMP_MAX_BANDS (1 + 3 * VDAMP_MAX_LEVELS)
+#define VDAMP_MAX_TAPS 8
+#define VDAMP_MAX_STAGES 12
+
+namespace vdamp {
+
+// ---------------------------------------------------------------- complex ---
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// |v| computed the same way everywhere, so that the SURE keys and the
+// threshold tests in the transforms classify a coefficient identically.
+__device__ __forceinline__ float cabs_f(float2 v) {
+    return sqrtf(__fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)));
+}
+
+// ----------------------------------------------------------------- params ---
+struct Filt {
+    float h[VDAMP_MAX_TAPS];
+    float g[VDAMP_MAX_TAPS];
+    int L;
+};
+
+struct FftAxis {
+    int n;
+    int nstages;
+    int radix[VDAMP_MAX_STAGES];
+    const float2* tw;  // device, tw[k] = exp(-2 pi i k / n)
+};
+
+// How a transform forms the coefficient it reads from a packed array.
+enum SrcMode {
+    SRC_ZERO = 0,      // r~ = 0 (Algorithm 1 line 1)
+    SRC_EXPLICIT = 1,  // r~ read as given
+    SRC_LINE8 = 2,     // r~ = (soft(r, theta) - alpha r) / (1 - alpha) (line 8)
+    SRC_SOFT = 3       // w_hat = soft(r, theta) (line 6, for the return line)
+};
+
+struct SrcSpec {
+    int mode;
+    const float2* r;     // packed base (slice 0)
+    const float4* coef;  // [batch][B]
+    int B;
+};
+
+__device__ __forceinline__ float2 src_value(const SrcSpec& s, int slice, size_t N, size_t idx,
+                                            int b) {
+    if (s.mode == SRC_ZERO) return make_float2(0.f, 0.f);
+    float2 v = s.r[(size_t)slice * N + idx];
+    if (s.mode == SRC_EXPLICIT) return v;
+    float4 c = s.coef[slice * s.B + b];
+    float a = cabs_f(v);
+    float sc = a > c.x ? 1.f - c.x / a : 0.f;
+    if (s.mode == SRC_SOFT) return cscale(v, sc);
+    return cscale(v, (sc - c.y) * c.z);
+}
+
+// Column-pass modes of the fused k-space kernel.
+enum ColMode {
+    COL_FWD = 0,    // out = F-column of in, scaled (plain transform)
+    COL_INV = 1,    // out = inverse F-column of in, scaled (plain transform)
+    COL_ITER = 2,   // U = F u; z = m(y - U); tau partials; out = F^H-column (w z)
+    COL_FINAL = 3   // U = F u; out = F^H-column (m y + (1-m) U)
+};
+
+struct ColArgs {
+    const float2* in;    // row-transformed data [batch][ny][nx] (ignored if u_zero)
+    float2* out;         // [batch][ny][nx]
+    int ny, nx, cb;      // cb = columns per CTA
+    FftAxis ax;          // along y
+    int mode;
+    int u_zero;          // 1: the image is zero, skip the forward transform
+    float scale_fwd;     // applied after the forward column transform
+    float scale_inv;     // applied after the inverse column transform
+    const float2* y;
+    const uint8_t* mask;
+    const float* density;
+    const float* sigma;  // device [batch]
+    // tau (Algorithm 1 line 5): tau_b = sum_k Ey[ty_b][ky] Ex[tx_b][kx] v(k)
+    const float* ey;     // [2 levels][ny]
+    const float* ex;     // [2 levels][nx]
+    int ntypes;          // 2 levels
+    int B;
+    int ty[VDAMP_MAX_BANDS];
+    int tx[VDAMP_MAX_BANDS];
+    double* tau_part;    // [batch][nx / cb][B]
+};
+
+struct DwtArgs {   // one analysis level: image (H x W) -> four (H/2 x W/2) bands
+    const float2* in;
+    size_t in_stride;
+    int H, W;
+    float2* ll_out;    // dense LL (when not last)
+    size_t ll_stride;
+    int last;          // 1: LL is A_s and goes to the packed array
+    float2* packed;    // packed output base
+    size_t N;
+    int off[4];        // packed offsets of A (if last), H, V, D
+    int band[4];       // subband indices of A, H, V, D
+    SrcSpec src;       // r~ added to every packed output (ZERO for plain Psi)
+    Filt f;
+};
+
+struct IdwtArgs {  // one synthesis level: four (h x w) bands -> image (2h x 2w)
+    const float2* ll_in;  // dense LL (when not first)
+    size_t ll_stride;
+    int h, w;
+    int first;            // 1: LL is A_s, read from the packed source
+    float2* out;
+    size_t out_stride;
+    size_t N;
+    int off[4];
+    int band[4];
+    SrcSpec src;          // how packed coefficients are formed
+    Filt f;
+};
+
+struct SureArgs {
+    const float2* r;      // packed r_k
+    size_t N;
+    int B;
+    int off[VDAMP_MAX_BANDS + 1];
+    const double* tau_part;  // [batch][nparts][B]
+    int nparts;
+    int iters, k;         // output row
+    double* tau_out;      // [batch][iters][B]
+    double* thr_out;
+    double* alpha_out;
+    float4* coef;         // [batch][B]
+    int* status;          // [0] code, [1] first bad iteration
+};
+
+struct Line8Args {
+    SrcSpec src;
+    float2* out;
+    size_t N;
+    int B;
+    int off[VDAMP_MAX_BANDS + 1];
+};
+
+// --------------------------------------------------------------- launchers ---
+// All return cudaGetLastError() after the launch.
+cudaError_t launch_fft_rows(const float2* in, float2* out, int ny, int nx, int batch,
+                            const FftAxis& ax, int inverse, float scale, int rows_per_cta,
+                            cudaStream_t st);
+cudaError_t launch_col_pass(const ColArgs& a, int batch, cudaStream_t st);
+size_t col_pass_smem(int ny, int cb, int ntypes);
+cudaError_t launch_dwt_level(const DwtArgs& a, int batch, cudaStream_t st);
+cudaError_t launch_idwt_level(const IdwtArgs& a, int batch, cudaStream_t st);
+cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, cudaStream_t st);
+size_t sure_smem(int max_band);
+cudaError_t launch_line8(const Line8Args& a, int batch, cudaStream_t st);
+cudaError_t configure_col_pass(size_t smem_bytes);
+cudaError_t configure_fft_rows(size_t smem_bytes);
+cudaError_t configure_sure(size_t smem_bytes);
+
+}  // namespace vdamp

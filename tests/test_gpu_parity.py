@@ -1,0 +1,339 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 kernels against FP64 arithmetic):
+* transforms F, F^H, Psi, Psi^H: relative L2 error <= 2e-6 (a few FP32 ulps
+  accumulated over log2(n) butterfly stages or s filter levels);
+* the solve: x_hat and tau within 1e-4 relative at every iteration, thresholds
+  within 1e-3 relative, final NMSE within 0.01 dB;
+* a threshold outside 1e-3 is accepted only as a SURE tie: the oracle's FP64
+  SURE at both thresholds differs by at most 1e-6 of the scale of its terms
+  (sum a^2 + N_b tau), the resolution of the kernel's FP32 curve.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import vdamp_oracle as O
+from paper_1911_01234_gb300 import binding as vb
+from paper_1911_01234_gb300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    vb.load()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def crand(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def theta_ok(r, sbs, tau, th_gpu, th_orc):
+    """Thresholds agree within 1e-3, or the oracle's SURE says they tie."""
+    for sb in sbs:
+        a, b = th_gpu[sb.index], th_orc[sb.index]
+        if abs(a - b) <= 1e-3 * max(abs(b), 1e-30):
+            continue
+        mag = np.abs(r[sb.offset:sb.offset + sb.size])
+        t = float(tau[sb.index])
+        scale = float(np.sum(mag ** 2)) + sb.size * t
+        if abs(O.sure_value(mag, a, t) - O.sure_value(mag, b, t)) > 1e-6 * scale:
+            return False, sb.name
+    return True, None
+
+
+# ------------------------------------------------------------ transforms ---
+
+@pytest.mark.parametrize("ny,nx", [(64, 64), (256, 256), (128, 128), (384, 320), (320, 320),
+                                   (48, 80), (8, 8), (1024, 16), (24, 40)])
+def test_fft2_matches_oracle(ny, nx):
+    rng = np.random.default_rng(ny * 1000 + nx)
+    plan = vb.Plan(ny, nx, "haar", 1, max_batch=2)
+    x = crand(rng, (2, ny, nx)).astype(np.complex64)
+    xd = dev(x)
+    out = torch.empty_like(xd)
+    back = torch.empty_like(xd)
+    vb.vdamp_fft2(plan.handle, 2, xd, out, inverse=False)
+    vb.vdamp_fft2(plan.handle, 2, out, back, inverse=True)
+    torch.cuda.synchronize()
+    x64 = x.astype(np.complex128)
+    ref = np.stack([O.fft2u(xi) for xi in x64])
+    assert rel(out.cpu().numpy(), ref) < 2e-6
+    assert rel(back.cpu().numpy(), x64) < 2e-6
+    plan.close()
+
+
+@pytest.mark.parametrize("wav,ny,nx,s", [("haar", 64, 64, 3), ("db4", 256, 256, 4),
+                                         ("db4", 48, 80, 2), ("db4", 384, 320, 4),
+                                         ("db4", 320, 320, 5), ("haar", 16, 16, 4),
+                                         ("db4", 32, 32, 3), ("db4", 24, 40, 3)])
+def test_psi_and_adjoint_match_oracle(wav, ny, nx, s):
+    rng = np.random.default_rng(ny + nx + s)
+    plan = vb.Plan(ny, nx, wav, s, max_batch=2)
+    h, g = O.wavelet_filters(wav)
+    x = crand(rng, (2, ny, nx)).astype(np.complex64)
+    w = torch.empty((2, ny * nx), dtype=torch.complex64, device="cuda")
+    vb.vdamp_psi(plan.handle, 2, dev(x), w)
+    c = crand(rng, (2, ny * nx)).astype(np.complex64)
+    img = torch.empty((2, ny, nx), dtype=torch.complex64, device="cuda")
+    vb.vdamp_psi_h(plan.handle, 2, dev(c), img)
+    torch.cuda.synchronize()
+    for i in range(2):
+        assert rel(w.cpu().numpy()[i], O.dwt2(x[i].astype(np.complex128), h, g, s)) < 2e-6
+        assert rel(img.cpu().numpy()[i],
+                   O.idwt2(c[i].astype(np.complex128), h, g, s, ny, nx)) < 2e-6
+    plan.close()
+
+
+# ------------------------------------------------- one iteration, forced ---
+
+def _problem_on_device(pr):
+    return dev(pr.y[None]), dev(pr.mask[None]), dev(pr.density[None])
+
+
+@pytest.mark.parametrize("wl,K", [(synth.PLAIN_64_HAAR3, 20), (synth.PLAIN_256_DB4_4, 10)])
+def test_iteration_teacher_forced(wl, K):
+    """Each iteration k from the oracle's own r~_k: lines 3-8 against the oracle."""
+    pr = synth.make_problem(wl)
+    ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, K, ops=ops)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    N, B = wl.ny * wl.nx, plan.B
+    y64 = np.where(pr.mask == 1, pr.y.astype(np.complex128), 0.0)
+    s2 = float(pr.sigma) ** 2
+    r = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    rn = torch.empty_like(r)
+    tau = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+    for k in range(K):
+        rt32 = res.records[k].r_tilde.astype(np.complex64)
+        rec = O.iterate(rt32.astype(np.complex128), y64, ops, s2)
+        vb.vdamp_iterate(plan.handle, 1, dev(rt32[None]), y, m, p, [pr.sigma], r, tau, thr, alpha,
+                         rn)
+        torch.cuda.synchronize()
+        rg = r.cpu().numpy()[0]
+        assert rel(rg, rec.r) < 1e-5, k
+        tg = tau.cpu().numpy()[0]
+        assert np.max(np.abs(tg - rec.tau) / rec.tau) < 1e-4, k
+        ok, band = theta_ok(rec.r, ops.sbs, rec.tau, thr.cpu().numpy()[0], rec.theta)
+        assert ok, (k, band)
+        if np.allclose(thr.cpu().numpy()[0], rec.theta, rtol=1e-3, atol=0):
+            assert np.max(np.abs(alpha.cpu().numpy()[0] - rec.alpha)) < 1e-4, k
+            assert rel(rn.cpu().numpy()[0], O.next_r_tilde(rec, ops)) < 1e-4, k
+    assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+    plan.close()
+
+
+# ------------------------------------------------------ the whole solve ---
+
+@pytest.mark.parametrize("wl", [synth.PLAIN_64_HAAR3, synth.PLAIN_256_DB4_4])
+def test_solve_free_running(wl):
+    """Algorithm 1 end to end, every iteration, against the FP64 oracle."""
+    pr = synth.make_problem(wl)
+    ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, wl.iters,
+                  want_x=True, ops=ops)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    out = plan.solve(y, m, p, [pr.sigma], wl.iters, want_iters=True)
+    torch.cuda.synchronize()
+    assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+    xi = out["x_hat_iters"].cpu().numpy()[0]
+    tau = out["tau"].cpu().numpy()[0]
+    thr = out["thr"].cpu().numpy()[0]
+    for k, rec in enumerate(res.records):
+        assert rel(xi[k], rec.x_hat) < 1e-4, k
+        assert np.max(np.abs(tau[k] - rec.tau) / rec.tau) < 1e-4, k
+        ok, band = theta_ok(rec.r, ops.sbs, rec.tau, thr[k], rec.theta)
+        assert ok, (k, band)
+    xh = out["x_hat"].cpu().numpy()[0]
+    assert rel(xh, res.x_hat) < 1e-4
+    assert abs(O.nmse_db(xh, pr.x0) - O.nmse_db(res.x_hat, pr.x0)) < 0.01
+    plan.close()
+
+
+@pytest.mark.parametrize("ny,nx,wav,s,K", [(384, 320, "db4", 4, 3), (320, 320, "db4", 5, 3),
+                                           (48, 80, "db4", 2, 6), (128, 128, "db4", 4, 4)])
+def test_solve_other_sizes(ny, nx, wav, s, K):
+    """Mixed radix (3, 5), non-square and deeper decompositions, ragged subbands."""
+    wl = synth.Workload("t", 77, ny, nx, 12, True, wav, s, 5.0, 5.0, 16, 30.0, 30.0, K, 1)
+    pr = synth.make_problem(wl)
+    ops = O.make_operators(pr.mask, pr.density, wav, s)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, wav, s, K, want_x=True, ops=ops)
+    plan = vb.Plan(ny, nx, wav, s)
+    y, m, p = _problem_on_device(pr)
+    out = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
+    torch.cuda.synchronize()
+    xi = out["x_hat_iters"].cpu().numpy()[0]
+    tau = out["tau"].cpu().numpy()[0]
+    thr = out["thr"].cpu().numpy()[0]
+    for k, rec in enumerate(res.records):
+        assert rel(xi[k], rec.x_hat) < 1e-4, k
+        assert np.max(np.abs(tau[k] - rec.tau) / rec.tau) < 1e-4, k
+        assert theta_ok(rec.r, ops.sbs, rec.tau, thr[k], rec.theta)[0], k
+    plan.close()
+
+
+def test_return_line_consistency():
+    """m F x_hat = y (Algorithm 1 return line, exact consistency, Sec. 2)."""
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    out = plan.solve(y, m, p, [pr.sigma], 5)
+    k = O.fft2u(out["x_hat"].cpu().numpy()[0].astype(np.complex128))
+    sel = pr.mask == 1
+    assert np.max(np.abs(k[sel] - pr.y[sel])) < 1e-5 * np.max(np.abs(pr.y))
+    plan.close()
+
+
+def test_resume_is_bit_identical():
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    full = plan.solve(y, m, p, [pr.sigma], 12)
+    a = plan.solve(y, m, p, [pr.sigma], 7, want_state=True)
+    b = plan.solve(y, m, p, [pr.sigma], 5, r_tilde0=a["r_tilde"])
+    torch.cuda.synchronize()
+    assert torch.equal(full["tau"][:, 7:], b["tau"])
+    assert torch.equal(full["thr"][:, 7:], b["thr"])
+    assert torch.equal(full["x_hat"], b["x_hat"])
+    plan.close()
+
+
+def test_graph_and_direct_launches_agree():
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    g = plan.solve(y, m, p, [pr.sigma], 6)
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_GRAPH, 0)
+    d = plan.solve(y, m, p, [pr.sigma], 6)
+    torch.cuda.synchronize()
+    assert torch.equal(g["x_hat"], d["x_hat"]) and torch.equal(g["tau"], d["tau"])
+    plan.close()
+
+
+def test_batch_matches_single_slices():
+    wl = synth.PLAIN_64_HAAR3
+    probs = [synth.make_problem(wl, i) for i in range(3)]
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=3)
+    y = dev(np.stack([q.y for q in probs]))
+    m = dev(np.stack([q.mask for q in probs]))
+    p = dev(np.stack([q.density for q in probs]))
+    sig = [q.sigma for q in probs]
+    bat = plan.solve(y, m, p, sig, 8)
+    for i in range(3):
+        one = plan.solve(y[i:i + 1].contiguous(), m[i:i + 1].contiguous(),
+                         p[i:i + 1].contiguous(), [sig[i]], 8)
+        torch.cuda.synchronize()
+        assert torch.equal(one["x_hat"][0], bat["x_hat"][i])
+        assert torch.equal(one["tau"][0], bat["tau"][i])
+    plan.close()
+
+
+def test_host_buffer_entry_point_matches_device():
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    K = 6
+    d = plan.solve(y, m, p, [pr.sigma], K)
+    torch.cuda.synchronize()
+    x = np.zeros((1, wl.ny, wl.nx), np.complex64)
+    tau = np.zeros((1, K, plan.B))
+    thr, alpha = np.zeros_like(tau), np.zeros_like(tau)
+    vb.vdamp_solve_host(plan.handle, 1, np.ascontiguousarray(pr.y[None]),
+                        np.ascontiguousarray(pr.mask[None]), np.ascontiguousarray(pr.density[None]),
+                        [pr.sigma], K, None, x, tau, thr, alpha)
+    assert np.array_equal(x, d["x_hat"].cpu().numpy())
+    assert np.array_equal(tau, d["tau"].cpu().numpy())
+    plan.close()
+
+
+# ---------------------------------------------------------- edge cases ---
+
+def test_full_sampling_noiseless_is_exact():
+    """p = 1, sigma = 0: tau = 0, no thresholding, x_hat = x0 (degenerate case)."""
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    ones = np.ones_like(pr.mask)
+    y = O.fft2u(pr.x0).astype(np.complex64)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    out = plan.solve(dev(y[None]), dev(ones[None]), dev(np.ones((1, 64, 64), np.float32)), [0.0], 3)
+    torch.cuda.synchronize()
+    assert torch.all(out["tau"] == 0) and torch.all(out["thr"] == 0)
+    assert torch.all(out["alpha"] == 0)
+    assert rel(out["x_hat"].cpu().numpy()[0], pr.x0) < 1e-6
+    plan.close()
+
+
+def test_empty_mask_gives_zero():
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    zero = np.zeros((1, 64, 64), np.uint8)
+    out = plan.solve(dev(pr.y[None]), dev(zero), dev(pr.density[None]), [pr.sigma], 2)
+    torch.cuda.synchronize()
+    assert torch.all(out["x_hat"] == 0) and torch.all(out["tau"] == 0)
+    plan.close()
+
+
+def test_non_finite_input_is_reported():
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    y = pr.y.copy()
+    idx = np.argwhere(pr.mask == 1)[5]
+    y[tuple(idx)] = np.nan
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    plan.solve(dev(y[None]), dev(pr.mask[None]), dev(pr.density[None]), [pr.sigma], 3)
+    st, it = vb.vdamp_device_status(plan.handle)
+    assert st == vb.VDAMP_ENUMERIC and it == 0
+    plan.close()
+
+
+def test_invalid_solve_arguments_launch_nothing():
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    with pytest.raises(vb.VdampError):
+        plan.solve(y, m, p, [-1.0], 3)
+    with pytest.raises(vb.VdampError):
+        plan.solve(y, m, p, [float("nan")], 3)
+    with pytest.raises(vb.VdampError):
+        plan.solve(y, m, p, [pr.sigma], 0)
+    plan.close()
+
+
+def test_largest_supported_slice():
+    """256 x 512: the largest finest subband (32768) the SURE kernel holds."""
+    ny, nx, s, K = 256, 512, 4, 2
+    wl = synth.Workload("big", 78, ny, nx, 20, True, "db4", s, 5.0, 5.0, 24, 30.0, 30.0, K, 1)
+    pr = synth.make_problem(wl)
+    ops = O.make_operators(pr.mask, pr.density, "db4", s)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, "db4", s, K, ops=ops)
+    plan = vb.Plan(ny, nx, "db4", s)
+    y, m, p = _problem_on_device(pr)
+    out = plan.solve(y, m, p, [pr.sigma], K)
+    torch.cuda.synchronize()
+    assert rel(out["x_hat"].cpu().numpy()[0], res.x_hat) < 1e-4
+    plan.close()
