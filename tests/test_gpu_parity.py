@@ -3,8 +3,9 @@
 Tolerances (FP32 kernels against FP64 arithmetic):
 * transforms F, F^H, Psi, Psi^H: relative L2 error <= 2e-6 (a few FP32 ulps
   accumulated over log2(n) butterfly stages or s filter levels);
-* the solve: x_hat and tau within 1e-4 relative at every iteration, thresholds
-  within 1e-3 relative, final NMSE within 0.01 dB;
+* the solve: x_hat and the tau vector within 1e-4 relative L2 at every
+  iteration (each subband's tau within 1e-3 relative), thresholds within 1e-3
+  relative, final NMSE within 0.01 dB;
 * a threshold outside 1e-3 is accepted only as a SURE tie: the oracle's FP64
   SURE at both thresholds differs by at most 1e-6 of the scale of its terms
   (sum a^2 + N_b tau), the resolution of the kernel's FP32 curve.
@@ -42,6 +43,11 @@ def crand(rng, shape):
 def rel(a, b):
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def tau_ok(t_gpu, t_orc):
+    """tau vector within 1e-4 relative L2, every subband within 1e-3 relative."""
+    return rel(t_gpu, t_orc) < 1e-4 and np.max(np.abs(t_gpu - t_orc) / t_orc) < 1e-3
 
 
 def theta_ok(r, sbs, tau, th_gpu, th_orc):
@@ -131,7 +137,7 @@ def test_iteration_teacher_forced(wl, K):
         rg = r.cpu().numpy()[0]
         assert rel(rg, rec.r) < 1e-5, k
         tg = tau.cpu().numpy()[0]
-        assert np.max(np.abs(tg - rec.tau) / rec.tau) < 1e-4, k
+        assert tau_ok(tg, rec.tau), (k, rel(tg, rec.tau))
         ok, band = theta_ok(rec.r, ops.sbs, rec.tau, thr.cpu().numpy()[0], rec.theta)
         assert ok, (k, band)
         if np.allclose(thr.cpu().numpy()[0], rec.theta, rtol=1e-3, atol=0):
@@ -160,7 +166,7 @@ def test_solve_free_running(wl):
     thr = out["thr"].cpu().numpy()[0]
     for k, rec in enumerate(res.records):
         assert rel(xi[k], rec.x_hat) < 1e-4, k
-        assert np.max(np.abs(tau[k] - rec.tau) / rec.tau) < 1e-4, k
+        assert tau_ok(tau[k], rec.tau), (k, rel(tau[k], rec.tau))
         ok, band = theta_ok(rec.r, ops.sbs, rec.tau, thr[k], rec.theta)
         assert ok, (k, band)
     xh = out["x_hat"].cpu().numpy()[0]
@@ -186,7 +192,7 @@ def test_solve_other_sizes(ny, nx, wav, s, K):
     thr = out["thr"].cpu().numpy()[0]
     for k, rec in enumerate(res.records):
         assert rel(xi[k], rec.x_hat) < 1e-4, k
-        assert np.max(np.abs(tau[k] - rec.tau) / rec.tau) < 1e-4, k
+        assert tau_ok(tau[k], rec.tau), (k, rel(tau[k], rec.tau))
         assert theta_ok(rec.r, ops.sbs, rec.tau, thr[k], rec.theta)[0], k
     plan.close()
 
