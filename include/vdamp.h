@@ -205,6 +205,38 @@ vdamp_status vdamp_wavelet_filter(int wavelet, double* h, int* len);
  */
 vdamp_status vdamp_subband_spectra(int wavelet, int levels, int n, double* out);
 
+/* ---- no device allocation ------------------------------------------------ */
+
+/* Largest ny or nx that vdamp_tau_estimate_noalloc accepts. */
+#define VDAMP_NOALLOC_MAX_SIDE 1024
+
+/*
+ * The colored noise estimate tau (Algorithm 1 line 5,
+ * tau = S^H P^-1 [(P^-1 - 1)|z|^2 + sigma^2]) from a k-space residual z, for
+ * callers that cannot allocate device memory.  The paper has no counterpart:
+ * this is a service of the library, not a step of the method.
+ *
+ * It needs no plan and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Its device scratch (the S tables and per-block partial sums, about
+ * 175 KB) is one fixed array inside the library that every GPU which loads
+ * the library keeps until the process exits.  Limits: 8 <= ny, nx <=
+ * VDAMP_NOALLOC_MAX_SIDE, of the form 2^a 3^b 5^c, divisible by 2^levels,
+ * 1 <= levels <= 6; larger sizes return VDAMP_EINVAL with a message.
+ *   z        device [ny][nx] complex64 residual (only entries with mask = 1 are read)
+ *   mask     device [ny][nx] uint8;  density device [ny][nx] float32 (p, > 0 on the mask)
+ *   sigma    noise level sigma_eps >= 0
+ *   tau      device out [1 + 3 levels] double, subbands in packed order
+ * Asynchronous on `stream`.  The first call on each device looks up the
+ * scratch address with that device current; make that first call before any
+ * stream capture.  All calls share the one scratch array: calls that overlap
+ * on the GPU (different streams, no ordering) race and give wrong results.
+ * Every partial sum is written before it is read, so nothing needs clearing
+ * between calls.
+ */
+vdamp_status vdamp_tau_estimate_noalloc(int ny, int nx, int wavelet, int levels, const float* z,
+                                        const uint8_t* mask, const float* density, float sigma,
+                                        double* tau, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

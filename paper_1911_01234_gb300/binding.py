@@ -53,6 +53,7 @@ _SIGS = {
     "vdamp_wavelet_filter": (_I, [_I, _D, ctypes.POINTER(_I)]),
     "vdamp_subband_spectra": (_I, [_I, _I, _I, _D]),
     "vdamp_kernel_times": (_I, [_P, _D, ctypes.POINTER(_I)]),
+    "vdamp_tau_estimate_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P, ctypes.c_float, _P, _P]),
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -203,6 +204,15 @@ def vdamp_kernel_times(plan):
     cnt = (_I * n)()
     check(load().vdamp_kernel_times(plan, ms, cnt), "vdamp_kernel_times")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def vdamp_tau_estimate_noalloc(ny, nx, wavelet, levels, z, mask, density, sigma, tau,
+                               stream=None) -> None:
+    """tau of Algorithm 1 line 5 from a residual z, with no device allocation (no plan)."""
+    w = WAVELETS.get(wavelet, wavelet) if isinstance(wavelet, str) else int(wavelet)
+    check(load().vdamp_tau_estimate_noalloc(ny, nx, w, levels, _ptr(z), _ptr(mask), _ptr(density),
+                                            float(sigma), _ptr(tau), _stream(stream)),
+          "vdamp_tau_estimate_noalloc")
 
 
 def vdamp_wavelet_filter(wavelet):

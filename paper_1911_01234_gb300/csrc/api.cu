@@ -233,6 +233,10 @@ static bool fft_size_ok(int n) {
 
 extern "C" const char* vdamp_last_error(void) { return g_last_error.c_str(); }
 
+namespace vdamp {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace vdamp
+
 extern "C" vdamp_status vdamp_wavelet_filter(int wavelet, double* h, int* len) {
     const int L = wavelet_taps(wavelet);
     if (!L || !h || !len) return fail(VDAMP_EINVAL, "vdamp_wavelet_filter: bad wavelet or NULL");
