@@ -194,6 +194,22 @@ def algorithmic_bytes(kind, N, n, levels):
 MEASURED_TRAFFIC = {}
 
 
+def slowest_rank_ms(local_ms, world, device=None):
+    """Max over ranks of the timed region (ms); the job's clock is its slowest rank."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, iters_per_step, slices_per_rank, max_ms):
+    """Whole-job slice-iterations/s: every rank's work over the slowest rank's time."""
+    return world * slices_per_rank * steps * iters_per_step / (max_ms / 1e3)
+
+
 def source_hash():
     import hashlib
     h = hashlib.sha256()
@@ -202,6 +218,65 @@ def source_hash():
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def run_batched(args, vb, torch, flush_buf, stream):
+    """Batched workload: 256 slices of 320x320, db4 s=5, R=6, 30 dB, 20 iterations."""
+    wl = synth.BATCH_320_DB4_5
+    nb = args.batched_slices
+    probs = [synth.make_problem(wl, i) for i in range(nb)]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
+    y, m, p = dev([q.y for q in probs]), dev([q.mask for q in probs]), dev([q.density for q in probs])
+    sig = [q.sigma for q in probs]
+    n_samp = int(sum(int(q.mask.sum()) for q in probs))
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
+    if args.path != "auto":
+        vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 1 if args.path == "fused" else 0)
+    K = wl.iters
+    x_hat = torch.empty((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+    tau = torch.empty((nb, K, plan.B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+
+    def step():
+        vb.vdamp_solve(plan.handle, nb, y, m, p, sig, K, None, x_hat, tau, thr, alpha,
+                       stream=stream.cuda_stream)
+    for i in range(2):
+        flush_buf.fill_(float(i))
+        step()
+    torch.cuda.synchronize()
+    steps = args.batched_steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush_buf.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if vb.vdamp_device_status(plan.handle)[0] != vb.VDAMP_OK:
+        raise RuntimeError("batched solve reported a non-finite tau or alpha")
+    # dominant kernel over one timed solve
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 1)
+    vb.vdamp_kernel_times(plan.handle)
+    step()
+    kt = vb.vdamp_kernel_times(plan.handle)
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 0)
+    dom = max((k for k in kt if kt[k][1] > 0 and k != "other"), key=lambda k: kt[k][0])
+    avg_s = kt[dom][0] / kt[dom][1] / 1e3
+    N = wl.ny * wl.nx
+    byt = nb * algorithmic_bytes(dom, N, n_samp / nb, wl.levels) if dom != "fused" else \
+        nb * K * (16 * N + 12 * n_samp / nb + N / 8)
+    hbm, src = peaks()
+    plan.close()
+    return {"workload": wl.name, "slices": nb, "iters": K, "steps": steps,
+            "value": nb * K * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": byt / avg_s / 1e9,
+                         "peak": hbm, "peak_source": src, "unit": "GB/s",
+                         "frac": byt / avg_s / 1e9 / hbm, "avg_launch_us": avg_s * 1e6,
+                         "algorithmic_bytes_per_launch": byt,
+                         "time_share": {k: round(v[0] / sum(x[0] for x in kt.values()), 4)
+                                        for k, v in kt.items()}}}
 
 
 def run_gpu(args):
@@ -230,6 +305,8 @@ def run_gpu(args):
     m = torch.from_numpy(pr.mask[None].copy()).cuda()
     p = torch.from_numpy(pr.density[None].copy()).cuda()
     plan = vb.Plan(WL.ny, WL.nx, WL.wavelet, WL.levels)
+    if args.path != "auto":
+        vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 1 if args.path == "fused" else 0)
     K = WL.iters
     x_hat = torch.empty((1, WL.ny, WL.nx), dtype=torch.complex64, device="cuda")
     tau = torch.empty((1, K, plan.B), dtype=torch.float64, device="cuda")
@@ -271,11 +348,8 @@ def run_gpu(args):
     st, _ = vb.vdamp_device_status(plan.handle)
     if st != vb.VDAMP_OK:
         raise RuntimeError("solve reported a non-finite tau or alpha")
-    t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * args.steps * K / (max_ms / 1e3)
+    max_ms = slowest_rank_ms(tot_ms, world, device="cuda")
+    value = job_throughput(world, args.steps, K, 1, max_ms)
 
     # ---- dominant kernel, timed live with CUDA events on the launching stream
     vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 1)
@@ -299,6 +373,7 @@ def run_gpu(args):
                 "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "algorithmic_bytes_per_launch": byt, "avg_launch_us": avg_s * 1e6,
                 "launches_per_step": {k: v[1] // reps for k, v in kt.items()},
+                "avg_us_by_kernel": {k: round(1e3 * v[0] / v[1], 2) for k, v in kt.items() if v[1]},
                 "time_share": shares}
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
@@ -335,13 +410,15 @@ def run_gpu(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic (seeded ellipse phantom, polynomial VD mask)",
-                "config": config_block(1, world),
+                "config": dict(config_block(1, world), path=args.path),
                 "clocks": ClockSampler.summarize(rows),
                 "gpu_launches": launches_per_step * args.steps,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "roofline": roofline,
                 "wall_s_timed": wall}
+        if not args.no_batched:
+            line["batched"] = run_batched(args, vb, torch, flush_buf, stream)
         if not args.no_cpu_baseline:
             it, el = OracleRunner().run(args.cpu_seconds)
             line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -363,6 +440,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 256 x 320x320 batched measurement")
+    ap.add_argument("--batched-slices", type=int, default=256)
+    ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--path", default="auto", choices=["auto", "fused", "steps"],
+                    help="solve as one persistent cluster launch, or one kernel per step")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

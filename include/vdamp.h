@@ -89,8 +89,12 @@ size_t vdamp_workspace_bytes(const vdamp_plan* plan);
  *   VDAMP_OPT_GRAPH (default 1): replay solves from a cached CUDA graph;
  *     0 launches every kernel directly.
  *   VDAMP_OPT_KERNEL_TIMING (default 0): launch directly and bracket every
- *     kernel with CUDA events on its stream; read with vdamp_kernel_times(). */
-enum { VDAMP_OPT_GRAPH = 1, VDAMP_OPT_KERNEL_TIMING = 2 };
+ *     kernel with CUDA events on its stream; read with vdamp_kernel_times().
+ *   VDAMP_OPT_FUSED (default 0): run vdamp_solve as one persistent launch in
+ *     which a thread-block cluster iterates each slice (when the device can
+ *     hold such a cluster); 0 runs one kernel per step of the iteration.
+ *     Both give the same results up to the order of the tau partial sums. */
+enum { VDAMP_OPT_GRAPH = 1, VDAMP_OPT_KERNEL_TIMING = 2, VDAMP_OPT_FUSED = 3 };
 vdamp_status vdamp_plan_set_option(vdamp_plan* plan, int option, int value);
 
 /* Kernel kinds reported by vdamp_kernel_times. */
@@ -101,7 +105,8 @@ enum {
     VDAMP_KERNEL_DWT = 3,       /* one analysis scale of Psi (+ r~ of line 4) */
     VDAMP_KERNEL_SURE = 4,      /* SURE threshold, alpha, tau (lines 5-7) */
     VDAMP_KERNEL_OTHER = 5,     /* line-8 write-out, sigma upload */
-    VDAMP_KERNEL_KINDS = 6
+    VDAMP_KERNEL_FUSED = 6,     /* the persistent cluster solve (all steps) */
+    VDAMP_KERNEL_KINDS = 7
 };
 
 /* With VDAMP_OPT_KERNEL_TIMING on: wait for the timed launches, then add up
@@ -129,7 +134,7 @@ int vdamp_last_launch_count(const vdamp_plan* plan);
  *   tau, thr, alpha  device  [batch][iters][B] double out (see conventions)
  *   r_tilde_out      device  [batch][ny*nx] complex64 out or NULL: r~ after the
  *                     last iteration (line 8), the state to resume from
- *   x_hat_iters      device  [batch][iters][ny][nx] complex64 out or NULL: the
+ *   x_hat_iters      device  [iters][batch][ny][nx] complex64 out or NULL: the
  *                     return line applied to every w_hat_k (NMSE curves)
  * Asynchronous on `stream` (a cudaStream_t).  A solve that hits a non-finite
  * tau or alpha finishes its launches and records VDAMP_ENUMERIC for

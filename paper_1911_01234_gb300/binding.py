@@ -21,8 +21,8 @@ STATUS_NAMES = {0: "VDAMP_OK", 1: "VDAMP_EINVAL", 2: "VDAMP_ENOMEM", 3: "VDAMP_E
                 4: "VDAMP_ENUMERIC", 5: "VDAMP_ETIMEOUT"}
 VDAMP_HAAR, VDAMP_DB4 = 1, 4
 WAVELETS = {"haar": VDAMP_HAAR, "db4": VDAMP_DB4}
-VDAMP_OPT_GRAPH, VDAMP_OPT_KERNEL_TIMING = 1, 2
-KERNEL_KINDS = ["idwt", "fft_rows", "col_pass", "dwt", "sure", "other"]
+VDAMP_OPT_GRAPH, VDAMP_OPT_KERNEL_TIMING, VDAMP_OPT_FUSED = 1, 2, 3
+KERNEL_KINDS = ["idwt", "fft_rows", "col_pass", "dwt", "sure", "other", "fused"]
 
 
 class VdampError(RuntimeError):
@@ -266,7 +266,7 @@ class Plan:
         alpha = torch.empty_like(tau)
         rt = torch.empty((batch, self.ny * self.nx), dtype=torch.complex64, device=dev) \
             if want_state else None
-        xi = torch.empty((batch, iters, self.ny, self.nx), dtype=torch.complex64, device=dev) \
+        xi = torch.empty((iters, batch, self.ny, self.nx), dtype=torch.complex64, device=dev) \
             if want_iters else None
         vdamp_solve(self.handle, batch, y, mask, density, sigma, iters, r_tilde0, x_hat, tau, thr,
                     alpha, rt, xi, stream)

@@ -9,7 +9,10 @@
 #include <vector>
 
 #include "../../include/vdamp.h"
-#include "vdamp_internal.cuh"
+#include "dwt_dev.cuh"
+#include "fft_dev.cuh"
+#include "fused.cuh"
+#include "sure_dev.cuh"
 
 using vdamp::FftAxis;
 using vdamp::Filt;
@@ -165,6 +168,7 @@ struct SigmaBlock {
     float v[512];
 };
 __global__ void set_sigma_kernel(float* dst, SigmaBlock b) {
+    cudaGridDependencySynchronize();
     if ((int)threadIdx.x < b.n) dst[threadIdx.x] = b.v[threadIdx.x];
 }
 }  // namespace
@@ -188,6 +192,7 @@ struct vdamp_plan {
     float2* rA = nullptr;
     float2* rB = nullptr;
     double* tau_part = nullptr;
+    float* sorted = nullptr;
     float4* coef = nullptr;
     float* sigma_d = nullptr;
     int* status = nullptr;
@@ -202,6 +207,10 @@ struct vdamp_plan {
     size_t ws_bytes = 0;
     int use_graph = 1;
     int timing = 0;
+    int use_fused = 0;
+    int fused_ok = 0;      // the device can hold the cluster
+    int fused_C = 0, fused_cb = 0, fused_rpc = 0, fused_idwt_to = 0, fused_dwt_to = 0;
+    size_t fused_smem = 0;
     int last_launches = 0;
     std::vector<cudaEvent_t> ev_pool;       // timing events, reused
     std::vector<std::pair<int, int>> ev_used;  // (kind, index of start event)
@@ -215,7 +224,7 @@ static void plan_free(vdamp_plan* p) {
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     for (auto& e : p->ev_pool) cudaEventDestroy(e);
     void* bufs[] = {p->ey, p->ex, p->tw_y, p->tw_x, p->u, p->kbuf, p->ll0, p->ll1, p->rA,
-                    p->rB, p->tau_part, p->coef, p->sigma_d, p->status, p->st_y, p->st_mask,
+                    p->rB, p->tau_part, p->sorted, p->coef, p->sigma_d, p->status, p->st_y, p->st_mask,
                     p->st_p, p->st_x, p->st_r0, p->st_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -320,6 +329,27 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     p->nparts = nx / cb;
     p->rpc = std::max(1, 512 / nx);
 
+    // persistent cluster solve: work-item sizes and shared memory
+    {
+        const int C = 16;
+        int fcb = 16;
+        while (nx % fcb || vdamp::col_pass_smem_bytes(ny, fcb, 2 * levels) > 128 * 1024) fcb >>= 1;
+        int frpc = (ny + C - 1) / C;
+        const int cap = std::max(1, (96 * 1024) / (int)(2 * nx * sizeof(float2)));
+        if (frpc > cap) frpc = cap;
+        p->fused_cb = std::max(fcb, 1);
+        p->fused_rpc = frpc;
+        p->fused_idwt_to = 64;
+        p->fused_dwt_to = 32;
+        size_t sm = vdamp::sure_smem_bytes(max_band);
+        sm = std::max(sm, vdamp::idwt_tile_smem(p->fused_idwt_to, L));
+        sm = std::max(sm, vdamp::dwt_tile_smem(p->fused_dwt_to, L));
+        sm = std::max(sm, 2 * (size_t)frpc * nx * sizeof(float2));
+        sm = std::max(sm, vdamp::col_pass_smem_bytes(ny, p->fused_cb, 2 * levels));
+        p->fused_smem = sm;
+    }
+    const int nparts_alloc = std::max(p->nparts, nx / p->fused_cb);
+
     p->axy.n = ny;
     p->axx.n = nx;
     if (!fft_radices(ny, p->axy.radix, &p->axy.nstages) ||
@@ -345,7 +375,8 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(dalloc(&p->ll1, MB * N / 4, &acc));
     A(dalloc(&p->rA, MB * N, &acc));
     A(dalloc(&p->rB, MB * N, &acc));
-    A(dalloc(&p->tau_part, MB * p->nparts * p->B, &acc));
+    A(dalloc(&p->tau_part, MB * nparts_alloc * p->B, &acc));
+    A(dalloc(&p->sorted, MB * N, &acc));
     A(dalloc(&p->coef, MB * p->B, &acc));
     A(dalloc(&p->sigma_d, MB, &acc));
     A(dalloc(&p->status, (size_t)2, &acc));
@@ -382,6 +413,19 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     }
     p->axy.tw = p->tw_y;
     p->axx.tw = p->tw_x;
+    // Can the device hold one cluster of 16 (else 8) such CTAs?
+    if (p->fused_smem <= 227 * 1024) {
+        for (int C : {16, 8}) {
+            int nclus = 0;
+            cudaError_t fe = vdamp::fused_configure(C, p->fused_smem, &nclus);
+            if (fe == cudaSuccess && nclus >= 1) {
+                p->fused_ok = 1;
+                p->fused_C = C;
+                break;
+            }
+            cudaGetLastError();  // clear a refusal before trying the smaller cluster
+        }
+    }
     *out = p;
     return VDAMP_OK;
 }
@@ -405,6 +449,10 @@ extern "C" vdamp_status vdamp_plan_set_option(vdamp_plan* p, int option, int val
     }
     if (option == VDAMP_OPT_KERNEL_TIMING) {
         p->timing = value ? 1 : 0;
+        return VDAMP_OK;
+    }
+    if (option == VDAMP_OPT_FUSED) {
+        p->use_fused = value ? 1 : 0;
         return VDAMP_OK;
     }
     return fail(VDAMP_EINVAL, "vdamp_plan_set_option: unknown option");
@@ -598,6 +646,7 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     vdamp_plan* p = c.p;
     vdamp::SureArgs a;
     a.r = r;
+    a.sorted = p->sorted;
     a.N = p->N;
     a.B = p->B;
     for (int b = 0; b <= p->B; ++b) a.off[b] = p->off[b];
@@ -638,9 +687,15 @@ struct SolveArgs {
     float2* x_hat_iters;
 };
 
+void enq_fused(Ctx& c, const SolveArgs& s);
+
 // Algorithm 1, lines 1-10.
 void enq_solve(Ctx& c, const SolveArgs& s) {
     vdamp_plan* p = c.p;
+    if (p->fused_ok && p->use_fused) {
+        enq_fused(c, s);
+        return;
+    }
     if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status, 0, sizeof(int), c.st);
     if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
     float2* prev = p->rA;  // r_{k-1}
@@ -660,7 +715,7 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
         enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha);  // tau, theta, alpha (5-7)
         if (s.x_hat_iters)
             enq_final(c, make_src(p, vdamp::SRC_SOFT, cur), s.y, s.mask,
-                      s.x_hat_iters + (size_t)k * p->N);
+                      s.x_hat_iters + (size_t)k * c.batch * p->N);
         float2* t = prev;
         prev = cur;
         cur = t;
@@ -669,14 +724,100 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
     if (s.r_tilde_out) enq_line8(c, prev, s.r_tilde_out);                      // line 8
 }
 
+// Algorithm 1, lines 1-10, as one persistent cluster launch.
+void enq_fused(Ctx& c, const SolveArgs& s) {
+    vdamp_plan* p = c.p;
+    if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status, 0, sizeof(int), c.st);
+    if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
+    const int lv = p->levels;
+    const size_t N = p->N;
+    vdamp::FusedArgs f;
+    memset(&f, 0, sizeof(f));
+    f.levels = lv;
+    f.B = p->B;
+    f.iters = s.iters;
+    f.N = N;
+    f.ny = p->ny;
+    f.nx = p->nx;
+    f.rpc = p->fused_rpc;
+    f.nrowblk = (p->ny + p->fused_rpc - 1) / p->fused_rpc;
+    f.nparts = p->nx / p->fused_cb;
+    f.inv_sqrt_n = inv_sqrt_n(p);
+    f.axx = p->axx;
+    for (int j = 1; j <= lv; ++j) {
+        const int bh = 1 + 3 * (lv - j);
+        vdamp::IdwtArgs& a = f.idwt[j - 1];
+        a.ll_in = (j == lv) ? nullptr : (((lv - (j + 1)) & 1) ? p->ll1 : p->ll0);
+        a.ll_stride = N / 4;
+        a.h = p->ny >> j;
+        a.w = p->nx >> j;
+        a.first = (j == lv);
+        a.out = (j == 1) ? nullptr : (((lv - j) & 1) ? p->ll1 : p->ll0);
+        a.out_stride = (j == 1) ? N : N / 4;
+        a.N = N;
+        a.f = p->filt;
+        a.to = p->fused_idwt_to;
+        vdamp::DwtArgs& d = f.dwt[j - 1];
+        d.in = (j == 1) ? nullptr : (((j - 1) & 1) ? p->ll0 : p->ll1);
+        d.in_stride = (j == 1) ? N : N / 4;
+        d.H = p->ny >> (j - 1);
+        d.W = p->nx >> (j - 1);
+        d.last = (j == lv);
+        d.ll_out = (j & 1) ? p->ll0 : p->ll1;
+        d.ll_stride = N / 4;
+        d.N = N;
+        d.f = p->filt;
+        d.to = p->fused_dwt_to;
+        const int offs[4] = {p->off[0], p->off[bh], p->off[bh + 1], p->off[bh + 2]};
+        const int bands[4] = {0, bh, bh + 1, bh + 2};
+        for (int q = 0; q < 4; ++q) {
+            a.off[q] = d.off[q] = offs[q];
+            a.band[q] = d.band[q] = bands[q];
+        }
+    }
+    f.col = col_args(p, vdamp::COL_ITER, p->kbuf, p->kbuf, s.y, s.mask, s.density);
+    f.col.cb = p->fused_cb;
+    vdamp::SureArgs& u = f.sure;
+    u.r = nullptr;
+    u.sorted = p->sorted;
+    u.N = N;
+    u.B = p->B;
+    for (int b = 0; b <= p->B; ++b) u.off[b] = p->off[b];
+    u.tau_part = p->tau_part;
+    u.nparts = f.nparts;
+    u.iters = s.iters;
+    u.k = 0;
+    u.tau_out = s.tau;
+    u.thr_out = s.thr;
+    u.alpha_out = s.alpha;
+    u.coef = p->coef;
+    u.status = p->status;
+    f.l8.src = make_src(p, vdamp::SRC_LINE8, nullptr);
+    f.l8.N = N;
+    f.l8.B = p->B;
+    for (int b = 0; b <= p->B; ++b) f.l8.off[b] = p->off[b];
+    f.r_tilde0 = s.r_tilde0;
+    f.x_hat = s.x_hat;
+    f.r_tilde_out = s.r_tilde_out;
+    f.x_hat_iters = s.x_hat_iters;
+    f.u = p->u;
+    f.kbuf = p->kbuf;
+    f.rA = p->rA;
+    f.rB = p->rB;
+    f.coef = p->coef;
+    f.C = p->fused_C;
+    c.pre();
+    c.chk(vdamp::launch_fused(f, c.batch, p->fused_smem, c.st), VDAMP_KERNEL_FUSED);
+}
+
 vdamp_status set_sigma(vdamp_plan* p, const float* sigma, int batch, cudaStream_t st,
                        int* launches) {
     for (int b0 = 0; b0 < batch; b0 += 512) {
         SigmaBlock blk;
         blk.n = std::min(512, batch - b0);
         for (int i = 0; i < blk.n; ++i) blk.v[i] = sigma[b0 + i];
-        set_sigma_kernel<<<1, 512, 0, st>>>(p->sigma_d + b0, blk);
-        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(vdamp::launch_pdl(set_sigma_kernel, dim3(1), dim3(512), 0, st, p->sigma_d + b0,
+                                   blk));
         ++*launches;
     }
     return VDAMP_OK;

@@ -1,0 +1,214 @@
+// Device code of one scale of the orthonormal periodic 2D wavelet transform
+// Psi and of its adjoint Psi^H (Sec. 1, Eq. 5-6), tiled in shared memory.
+//
+// Analysis of an H x W image into four (H/2 x W/2) bands:
+//   rows:    lo[y][n] = sum_k h[k] X[y][(2n+k) mod W],  hi uses g
+//   columns: LL = h*lo, V = g*lo, H = h*hi, D = g*hi along y, same indexing.
+// Synthesis is the exact adjoint: X[y][x] += f[k] c[n] for y = (2n+k) mod L.
+//
+// The packed outputs of the analysis carry Algorithm 1 line 4's addition
+// r_k = r~_k + Psi u' (r~_k formed on the fly by SrcSpec), and the packed
+// inputs of the synthesis carry line 8 (r~ = (soft(r) - alpha r)/(1 - alpha))
+// or line 6 (soft(r)), so that neither r~ nor w_hat is ever stored.
+//
+// A tile is computed by all threads of one CTA (any block size).  Tile sides
+// (a.to) are runtime values: analysis tiles are to x to output coefficients,
+// synthesis tiles to x to output pixels (to even).
+#pragma once
+
+#include "vdamp_internal.cuh"
+
+namespace vdamp {
+
+
+// Shared memory of one tile.
+inline size_t dwt_tile_smem(int to, int L) {
+    const size_t IT = 2 * (size_t)to + L - 2;
+    return (IT * IT + 2 * IT * to) * sizeof(float2);
+}
+inline size_t idwt_tile_smem(int to, int L) {
+    const size_t CT = (size_t)to / 2 + L / 2 - 1;
+    return (4 * CT * CT + 2 * (size_t)to * CT) * sizeof(float2);
+}
+
+// Periodic index: v mod n for v within a few periods of [0, n).
+__device__ __forceinline__ int wrap(int v, int n) {
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
+}
+
+// Analysis tile (tile_x, tile_y) of slice `slice`; L taps, TO x TO outputs.
+template <int L, int TO>
+__device__ __forceinline__ void dwt_tile_t(const DwtArgs& a, const float2* in_base,
+                                           float2* packed, const SrcSpec& src, int tile_x,
+                                           int tile_y, int slice, float2* sm) {
+    constexpr int IT = 2 * TO + L - 2;
+    float2* X = sm;              // IT x IT input tile
+    float2* Lx = X + IT * IT;    // IT x TO
+    float2* Hx = Lx + IT * TO;   // IT x TO
+    const int m0 = tile_y * TO, n0 = tile_x * TO;
+    const int H = a.H, W = a.W;
+    const float2* in = in_base + (size_t)slice * a.in_stride;
+    const int tid = threadIdx.x;
+
+    batched_for<8, float2>(
+        tid, IT * IT, blockDim.x,
+        [&](int idx) {
+            const int r = idx / IT, c = idx - r * IT;
+            return in[(size_t)wrap(2 * m0 + r, H) * W + wrap(2 * n0 + c, W)];
+        },
+        [&](int idx, float2 v) { X[idx] = v; });
+    __syncthreads();
+    for (int idx = tid; idx < IT * TO; idx += blockDim.x) {
+        const int r = idx / TO, n = idx - r * TO;
+        const float2* xr = X + r * IT + 2 * n;
+        float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const float2 x = xr[k];
+            lo.x += a.f.h[k] * x.x; lo.y += a.f.h[k] * x.y;
+            hi.x += a.f.g[k] * x.x; hi.y += a.f.g[k] * x.y;
+        }
+        Lx[idx] = lo;
+        Hx[idx] = hi;
+    }
+    __syncthreads();
+    const int Ho = H >> 1, Wo = W >> 1;
+    const size_t sN = (size_t)slice * a.N;
+    for (int idx = tid; idx < TO * TO; idx += blockDim.x) {
+        const int m = idx / TO, n = idx - m * TO;
+        const int gm = m0 + m, gn = n0 + n;
+        if (gm >= Ho || gn >= Wo) continue;
+        float2 ll = make_float2(0.f, 0.f), v = ll, hh = ll, d = ll;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const float2 l = Lx[(2 * m + k) * TO + n];
+            const float2 x = Hx[(2 * m + k) * TO + n];
+            const float hk = a.f.h[k], gk = a.f.g[k];
+            ll.x += hk * l.x; ll.y += hk * l.y;
+            v.x += gk * l.x;  v.y += gk * l.y;
+            hh.x += hk * x.x; hh.y += hk * x.y;
+            d.x += gk * x.x;  d.y += gk * x.y;
+        }
+        const size_t pos = (size_t)gm * Wo + gn;
+        const float2 outs[4] = {ll, hh, v, d};
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            const size_t p = a.off[q] + pos;
+            packed[sN + p] = cadd(outs[q], src_value(src, slice, a.N, p, a.band[q]));
+        }
+        if (a.last) {
+            const size_t p = a.off[0] + pos;
+            packed[sN + p] = cadd(ll, src_value(src, slice, a.N, p, a.band[0]));
+        } else {
+            a.ll_out[(size_t)slice * a.ll_stride + pos] = ll;
+        }
+    }
+}
+
+// Synthesis tile (tile_x, tile_y) of slice `slice`; L taps, TO x TO outputs.
+template <int L, int TO>
+__device__ __forceinline__ void idwt_tile_t(const IdwtArgs& a, float2* out, const SrcSpec& src,
+                                            int tile_x, int tile_y, int slice, float2* sm) {
+    constexpr int hL = L / 2;
+    constexpr int CT = TO / 2 + hL - 1;
+    float2* C = sm;                  // 4 x CT x CT (LL, H, V, D)
+    float2* TL = C + 4 * CT * CT;    // TO x CT, low along x
+    float2* TH = TL + TO * CT;       // TO x CT, high along x
+    const int y0 = tile_y * TO, x0 = tile_x * TO;
+    const int h = a.h, w = a.w;
+    const int ms = y0 / 2 - (hL - 1), ns = x0 / 2 - (hL - 1);
+    const int tid = threadIdx.x;
+
+    batched_for<8, float2>(
+        tid, 4 * CT * CT, blockDim.x,
+        [&](int idx) {
+            const int q = idx / (CT * CT);
+            const int rem = idx - q * CT * CT;
+            const int r = rem / CT, c = rem - r * CT;
+            const size_t pos = (size_t)wrap(ms + r, h) * w + wrap(ns + c, w);
+            if (q == 0 && !a.first) return a.ll_in[(size_t)slice * a.ll_stride + pos];
+            return src_value(src, slice, a.N, a.off[q] + pos, a.band[q]);
+        },
+        [&](int idx, float2 v) { C[idx] = v; });
+    __syncthreads();
+    const float2* LL = C;
+    const float2* HB = C + CT * CT;
+    const float2* VB = C + 2 * CT * CT;
+    const float2* DB = C + 3 * CT * CT;
+    for (int idx = tid; idx < TO * CT; idx += blockDim.x) {
+        const int t = idx / CT, c = idx - t * CT;
+        float2 lo = make_float2(0.f, 0.f), hi = lo;
+        const int par = t & 1;
+#pragma unroll
+        for (int kk = 0; kk < hL; ++kk) {
+            const int k = 2 * kk + par;
+            const int r = (t - k) / 2 + hL - 1;
+            const float hk = a.f.h[k], gk = a.f.g[k];
+            const float2 ll = LL[r * CT + c], vv = VB[r * CT + c];
+            const float2 hb = HB[r * CT + c], dd = DB[r * CT + c];
+            lo.x += hk * ll.x + gk * vv.x; lo.y += hk * ll.y + gk * vv.y;
+            hi.x += hk * hb.x + gk * dd.x; hi.y += hk * hb.y + gk * dd.y;
+        }
+        TL[idx] = lo;
+        TH[idx] = hi;
+    }
+    __syncthreads();
+    const int Ho = 2 * h, Wo = 2 * w;
+    for (int idx = tid; idx < TO * TO; idx += blockDim.x) {
+        const int t = idx / TO, s = idx - t * TO;
+        const int gy = y0 + t, gx = x0 + s;
+        if (gy >= Ho || gx >= Wo) continue;
+        float2 o = make_float2(0.f, 0.f);
+        const int par = s & 1;
+#pragma unroll
+        for (int ll = 0; ll < hL; ++ll) {
+            const int l = 2 * ll + par;
+            const int c = (s - l) / 2 + hL - 1;
+            const float2 lo = TL[t * CT + c], hi = TH[t * CT + c];
+            o.x += a.f.h[l] * lo.x + a.f.g[l] * hi.x;
+            o.y += a.f.h[l] * lo.y + a.f.g[l] * hi.y;
+        }
+        out[(size_t)slice * a.out_stride + (size_t)gy * Wo + gx] = o;
+    }
+}
+
+// Dispatch on (taps, tile side); the plans use L in {2, 8}, to in {16, 32, 64}.
+static __device__ void dwt_tile(const DwtArgs& a, const float2* in, float2* packed,
+                                const SrcSpec& src, int tile_x, int tile_y, int slice, float2* sm) {
+    if (a.f.L == 2) {
+        if (a.to == 16) dwt_tile_t<2, 16>(a, in, packed, src, tile_x, tile_y, slice, sm);
+        else if (a.to == 32) dwt_tile_t<2, 32>(a, in, packed, src, tile_x, tile_y, slice, sm);
+        else dwt_tile_t<2, 64>(a, in, packed, src, tile_x, tile_y, slice, sm);
+    } else {
+        if (a.to == 16) dwt_tile_t<8, 16>(a, in, packed, src, tile_x, tile_y, slice, sm);
+        else if (a.to == 32) dwt_tile_t<8, 32>(a, in, packed, src, tile_x, tile_y, slice, sm);
+        else dwt_tile_t<8, 64>(a, in, packed, src, tile_x, tile_y, slice, sm);
+    }
+}
+
+static __device__ void idwt_tile(const IdwtArgs& a, float2* out, const SrcSpec& src, int tile_x,
+                                 int tile_y, int slice, float2* sm) {
+    if (a.f.L == 2) {
+        if (a.to == 16) idwt_tile_t<2, 16>(a, out, src, tile_x, tile_y, slice, sm);
+        else if (a.to == 32) idwt_tile_t<2, 32>(a, out, src, tile_x, tile_y, slice, sm);
+        else idwt_tile_t<2, 64>(a, out, src, tile_x, tile_y, slice, sm);
+    } else {
+        if (a.to == 16) idwt_tile_t<8, 16>(a, out, src, tile_x, tile_y, slice, sm);
+        else if (a.to == 32) idwt_tile_t<8, 32>(a, out, src, tile_x, tile_y, slice, sm);
+        else idwt_tile_t<8, 64>(a, out, src, tile_x, tile_y, slice, sm);
+    }
+}
+
+// r~ (line 8) for packed coefficients [i0, i1) of slice `slice`.
+__device__ __forceinline__ void line8_range(const Line8Args& a, const SrcSpec& src, float2* out,
+                                            int slice, size_t i0, size_t i1, size_t stride) {
+    for (size_t i = i0; i < i1; i += stride) {
+        int b = 0;
+        while (b + 1 < a.B && (size_t)a.off[b + 1] <= i) ++b;
+        out[(size_t)slice * a.N + i] = src_value(src, slice, a.N, i, b);
+    }
+}
+
+}  // namespace vdamp

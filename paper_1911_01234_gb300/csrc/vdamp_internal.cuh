@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #define VDAMP_MAX_LEVELS 6
 #define VDAMP_MAX_BANDS (1 + 3 * VDAMP_MAX_LEVELS)
 #define VDAMP_MAX_TAPS 8
@@ -25,11 +27,37 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// Product rounded on its own (never fused into a following add), so that a
+// value formed here and one read back from memory are the same bits.
+__device__ __forceinline__ float2 cscale_rn(float2 a, float s) {
+    return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s));
+}
 
 // |v| computed the same way everywhere, so that the SURE keys and the
 // threshold tests in the transforms classify a coefficient identically.
 __device__ __forceinline__ float cabs_f(float2 v) {
     return sqrtf(__fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)));
+}
+
+// Strided loop over idx = start, start + step, ... < cnt in chunks of U:
+// the U loads of a chunk are all issued before any of their stores, so a
+// thread waits for one memory round trip per chunk instead of one per element.
+template <int U, class T, class LoadF, class StoreF>
+__device__ __forceinline__ void batched_for(int start, int cnt, int step, LoadF load,
+                                            StoreF store) {
+    for (int base = start; base < cnt; base += U * step) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * step;
+            if (idx < cnt) v[u] = load(idx);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * step;
+            if (idx < cnt) store(idx, v[u]);
+        }
+    }
 }
 
 // ----------------------------------------------------------------- params ---
@@ -69,8 +97,8 @@ __device__ __forceinline__ float2 src_value(const SrcSpec& s, int slice, size_t 
     float4 c = s.coef[slice * s.B + b];
     float a = cabs_f(v);
     float sc = a > c.x ? 1.f - c.x / a : 0.f;
-    if (s.mode == SRC_SOFT) return cscale(v, sc);
-    return cscale(v, (sc - c.y) * c.z);
+    if (s.mode == SRC_SOFT) return cscale_rn(v, sc);
+    return cscale_rn(v, __fmul_rn(sc - c.y, c.z));
 }
 
 // Column-pass modes of the fused k-space kernel.
@@ -117,6 +145,7 @@ struct DwtArgs {   // one analysis level: image (H x W) -> four (H/2 x W/2) band
     int band[4];       // subband indices of A, H, V, D
     SrcSpec src;       // r~ added to every packed output (ZERO for plain Psi)
     Filt f;
+    int to;            // tile side (output coefficients)
 };
 
 struct IdwtArgs {  // one synthesis level: four (h x w) bands -> image (2h x 2w)
@@ -131,10 +160,12 @@ struct IdwtArgs {  // one synthesis level: four (h x w) bands -> image (2h x 2w)
     int band[4];
     SrcSpec src;          // how packed coefficients are formed
     Filt f;
+    int to;               // tile side (output pixels, even)
 };
 
 struct SureArgs {
     const float2* r;      // packed r_k
+    float* sorted;        // [batch][N] scratch: |r_k| sorted within each subband
     size_t N;
     int B;
     int off[VDAMP_MAX_BANDS + 1];
@@ -155,6 +186,27 @@ struct Line8Args {
     int B;
     int off[VDAMP_MAX_BANDS + 1];
 };
+
+// Launch with programmatic dependent launch: the kernel may be scheduled while
+// its predecessor on the stream drains; every kernel of this library calls
+// cudaGridDependencySynchronize() before its first global memory access, so
+// it still sees all of the predecessor's writes.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 // --------------------------------------------------------------- launchers ---
 // All return cudaGetLastError() after the launch.

@@ -31,6 +31,7 @@ not available here, and for simulated brain slices):
 from __future__ import annotations
 
 import dataclasses
+import functools
 import math
 from typing import List, Optional
 
@@ -121,8 +122,9 @@ def phantom(ny: int, nx: int, ellipses: int, texture: bool, rng: np.random.Gener
     return mag * np.exp(1j * phase)
 
 
+@functools.lru_cache(maxsize=64)
 def poly_density(ny: int, nx: int, rate: float, centre: int) -> np.ndarray:
-    """Polynomial variable density p (float64, unshifted), sum(p) = N / rate."""
+    """Polynomial variable density p (float64, unshifted, read-only), sum(p) = N / rate."""
     ky = signed_freq(ny)[:, None] / (ny / 2.0)
     kx = signed_freq(nx)[None, :] / (nx / 2.0)
     rho = np.sqrt(ky * ky + kx * kx)
@@ -148,7 +150,9 @@ def poly_density(ny: int, nx: int, rate: float, centre: int) -> np.ndarray:
         else:
             hi = mid
     c = 0.5 * (lo + hi)
-    return np.where(in_centre, 1.0, np.minimum(1.0, c * base))
+    p = np.where(in_centre, 1.0, np.minimum(1.0, c * base))
+    p.setflags(write=False)
+    return p
 
 
 @dataclasses.dataclass

@@ -9,6 +9,20 @@ Tolerances (FP32 kernels against FP64 arithmetic):
 * a threshold outside 1e-3 is accepted only as a SURE tie: the oracle's FP64
   SURE at both thresholds differs by at most 1e-6 of the scale of its terms
   (sum a^2 + N_b tau), the resolution of the kernel's FP32 curve.
+
+On the 256x256 db4 workload the iteration itself amplifies perturbations by
+about 1.5x per iteration (test_iteration_sensitivity_to_state_rounding in the
+oracle pins): the FP64 oracle with its state merely rounded to complex64 drifts
+to 1e-3 of itself by the end, and FP64 runs perturbed at 1e-7 end 0.017 dB
+apart in NMSE.  An FP32 trajectory therefore follows the FP64 one to 1e-4 only
+for its first iterations, and a SURE near-tie (two local minima whose order
+flips under an FP32-level change of r_k) can send the two runs to different
+thresholds.  The free-running test therefore holds the tolerances for k < 10
+or until the runs first pick different thresholds (which must not happen
+before k = 5); every iteration is held to them teacher-forced (each step
+started from the oracle's own r~_k, where a threshold difference must be a
+certified tie); and the final NMSE must fall within 0.01 dB of the range
+spanned by FP64 oracle runs perturbed at the FP32 level.
 """
 import math
 
@@ -113,7 +127,7 @@ def _problem_on_device(pr):
     return dev(pr.y[None]), dev(pr.mask[None]), dev(pr.density[None])
 
 
-@pytest.mark.parametrize("wl,K", [(synth.PLAIN_64_HAAR3, 20), (synth.PLAIN_256_DB4_4, 10)])
+@pytest.mark.parametrize("wl,K", [(synth.PLAIN_64_HAAR3, 20), (synth.PLAIN_256_DB4_4, 30)])
 def test_iteration_teacher_forced(wl, K):
     """Each iteration k from the oracle's own r~_k: lines 3-8 against the oracle."""
     pr = synth.make_problem(wl)
@@ -149,9 +163,28 @@ def test_iteration_teacher_forced(wl, K):
 
 # ------------------------------------------------------ the whole solve ---
 
-@pytest.mark.parametrize("wl", [synth.PLAIN_64_HAAR3, synth.PLAIN_256_DB4_4])
-def test_solve_free_running(wl):
-    """Algorithm 1 end to end, every iteration, against the FP64 oracle."""
+def _perturbed_oracle_nmse(wl, runs=3, eps=1e-7):
+    """Final NMSE of FP64 oracle runs whose state is rounded to complex64 and perturbed by
+    eps (relative) before every iteration: the spread the method itself gives an FP32 run."""
+    out = []
+    for seed in range(runs):
+        pr = synth.make_problem(wl)
+        ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+        y = np.where(pr.mask == 1, pr.y.astype(np.complex128), 0.0)
+        rt = np.zeros(wl.ny * wl.nx, dtype=np.complex128)
+        rng = np.random.default_rng(1000 + seed)
+        for _ in range(wl.iters):
+            rt = rt.astype(np.complex64).astype(np.complex128)
+            rt = rt * (1.0 + eps * rng.standard_normal(rt.shape))
+            rec = O.iterate(rt, y, ops, float(pr.sigma) ** 2)
+            rt = O.next_r_tilde(rec, ops)
+        out.append(O.nmse_db(O.final_estimate(rec.w_hat, y, ops), pr.x0))
+    return out
+
+
+@pytest.mark.parametrize("wl,k_strict", [(synth.PLAIN_64_HAAR3, 20), (synth.PLAIN_256_DB4_4, 10)])
+def test_solve_free_running(wl, k_strict):
+    """Algorithm 1 end to end against the FP64 oracle (see the module docstring for k_strict)."""
     pr = synth.make_problem(wl)
     ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
     res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, wl.iters,
@@ -161,17 +194,28 @@ def test_solve_free_running(wl):
     out = plan.solve(y, m, p, [pr.sigma], wl.iters, want_iters=True)
     torch.cuda.synchronize()
     assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
-    xi = out["x_hat_iters"].cpu().numpy()[0]
+    xi = out["x_hat_iters"].cpu().numpy()[:, 0]
     tau = out["tau"].cpu().numpy()[0]
     thr = out["thr"].cpu().numpy()[0]
-    for k, rec in enumerate(res.records):
+    parted = None
+    for k, rec in enumerate(res.records[:k_strict]):
+        assert tau_ok(tau[k], rec.tau), (k, rel(tau[k], rec.tau))   # tau_k precedes line 6
+        if not np.allclose(thr[k], rec.theta, rtol=1e-3, atol=0):
+            parted = k     # the two runs pick different SURE minima from r_k that differ
+            break          # at the FP32 level: from here they follow different trajectories
         assert rel(xi[k], rec.x_hat) < 1e-4, k
-        assert tau_ok(tau[k], rec.tau), (k, rel(tau[k], rec.tau))
-        ok, band = theta_ok(rec.r, ops.sbs, rec.tau, thr[k], rec.theta)
-        assert ok, (k, band)
+    if parted is not None:
+        assert wl.iters > k_strict, "the stable workload must not part"
+        assert parted >= 5, parted
     xh = out["x_hat"].cpu().numpy()[0]
-    assert rel(xh, res.x_hat) < 1e-4
-    assert abs(O.nmse_db(xh, pr.x0) - O.nmse_db(res.x_hat, pr.x0)) < 0.01
+    assert np.array_equal(xh, xi[-1])
+    nm_gpu = O.nmse_db(xh, pr.x0)
+    if k_strict >= wl.iters:
+        assert rel(xh, res.x_hat) < 1e-4
+        assert abs(nm_gpu - O.nmse_db(res.x_hat, pr.x0)) < 0.01
+    else:
+        ens = _perturbed_oracle_nmse(wl) + [O.nmse_db(res.x_hat, pr.x0)]
+        assert min(ens) - 0.01 <= nm_gpu <= max(ens) + 0.01, (nm_gpu, ens)
     plan.close()
 
 
@@ -187,7 +231,7 @@ def test_solve_other_sizes(ny, nx, wav, s, K):
     y, m, p = _problem_on_device(pr)
     out = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
     torch.cuda.synchronize()
-    xi = out["x_hat_iters"].cpu().numpy()[0]
+    xi = out["x_hat_iters"].cpu().numpy()[:, 0]
     tau = out["tau"].cpu().numpy()[0]
     thr = out["thr"].cpu().numpy()[0]
     for k, rec in enumerate(res.records):
@@ -342,4 +386,22 @@ def test_largest_supported_slice():
     out = plan.solve(y, m, p, [pr.sigma], K)
     torch.cuda.synchronize()
     assert rel(out["x_hat"].cpu().numpy()[0], res.x_hat) < 1e-4
+    plan.close()
+
+
+@pytest.mark.parametrize("wl", [synth.PLAIN_64_HAAR3, synth.PLAIN_256_DB4_4])
+def test_fused_and_stepwise_paths_agree(wl):
+    """The persistent cluster solve and the one-kernel-per-step solve compute the same
+    iteration; they differ only in the blocking of the tau partial sums."""
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    K = wl.iters if wl is synth.PLAIN_64_HAAR3 else 5
+    fused = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 0)
+    step = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
+    torch.cuda.synchronize()
+    for k in range(K):
+        assert rel(fused["x_hat_iters"].cpu().numpy()[k, 0], step["x_hat_iters"].cpu().numpy()[k, 0]) < 1e-5, k
+        assert rel(fused["tau"].cpu().numpy()[0, k], step["tau"].cpu().numpy()[0, k]) < 1e-5, k
     plan.close()
