@@ -181,6 +181,7 @@ struct vdamp_plan {
     int off[VDAMP_MAX_BANDS + 1];
     int ty[VDAMP_MAX_BANDS], tx[VDAMP_MAX_BANDS];
     int cb, nparts, rpc;
+    int num_sms = 152;
     float* ey = nullptr;
     float* ex = nullptr;
     float2* tw_y = nullptr;
@@ -193,6 +194,9 @@ struct vdamp_plan {
     float2* rB = nullptr;
     double* tau_part = nullptr;
     float* sorted = nullptr;
+    double4_32a* partrec = nullptr;
+    double4_32a* bestrec = nullptr;
+    unsigned* counter = nullptr;
     float4* coef = nullptr;
     float* sigma_d = nullptr;
     int* status = nullptr;
@@ -223,9 +227,10 @@ static void plan_free(vdamp_plan* p) {
     if (!p) return;
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     for (auto& e : p->ev_pool) cudaEventDestroy(e);
-    void* bufs[] = {p->ey, p->ex, p->tw_y, p->tw_x, p->u, p->kbuf, p->ll0, p->ll1, p->rA,
-                    p->rB, p->tau_part, p->sorted, p->coef, p->sigma_d, p->status, p->st_y, p->st_mask,
-                    p->st_p, p->st_x, p->st_r0, p->st_out};
+    void* bufs[] = {p->ey,       p->ex,      p->tw_y,    p->tw_x,    p->u,      p->kbuf,
+                    p->ll0,      p->ll1,     p->rA,      p->rB,      p->tau_part, p->sorted,
+                    p->partrec,  p->bestrec, p->counter, p->coef,    p->sigma_d, p->status,
+                    p->st_y,     p->st_mask, p->st_p,    p->st_x,    p->st_r0,  p->st_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap) cudaStreamDestroy(p->cap);
@@ -377,6 +382,9 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(dalloc(&p->rB, MB * N, &acc));
     A(dalloc(&p->tau_part, MB * nparts_alloc * p->B, &acc));
     A(dalloc(&p->sorted, MB * N, &acc));
+    A(dalloc(&p->partrec, MB * p->B * SURE_MAX_PARTS, &acc));
+    A(dalloc(&p->bestrec, MB * p->B * SURE_MAX_PARTS, &acc));
+    A(dalloc(&p->counter, MB * p->B, &acc));
     A(dalloc(&p->coef, MB * p->B, &acc));
     A(dalloc(&p->sigma_d, MB, &acc));
     A(dalloc(&p->status, (size_t)2, &acc));
@@ -403,6 +411,12 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(cudaMemcpy(p->tw_y, twy.data(), ny * sizeof(float2), cudaMemcpyHostToDevice));
     A(cudaMemcpy(p->tw_x, twx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice));
     A(cudaMemset(p->status, 0, 2 * sizeof(int)));
+    A(cudaMemset(p->counter, 0, MB * p->B * sizeof(unsigned)));  // each search returns it to 0
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     A(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     A(vdamp::configure_col_pass(vdamp::col_pass_smem(ny, cb, nt)));
     A(vdamp::configure_fft_rows(2 * (size_t)p->rpc * nx * sizeof(float2)));
@@ -659,6 +673,11 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     a.alpha_out = alpha;
     a.coef = p->coef;
     a.status = p->status;
+    a.partrec = p->partrec;
+    a.bestrec = p->bestrec;
+    a.counter = p->counter;
+    // split big subbands over several CTAs only while slices alone leave SMs idle
+    a.max_parts = (c.batch * p->B >= 2 * p->num_sms) ? 1 : SURE_MAX_PARTS;
     c.pre();
     c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), c.st), VDAMP_KERNEL_SURE);
 }
@@ -792,6 +811,10 @@ void enq_fused(Ctx& c, const SolveArgs& s) {
     u.alpha_out = s.alpha;
     u.coef = p->coef;
     u.status = p->status;
+    u.partrec = p->partrec;
+    u.bestrec = p->bestrec;
+    u.counter = p->counter;
+    u.max_parts = SURE_MAX_PARTS;
     f.l8.src = make_src(p, vdamp::SRC_LINE8, nullptr);
     f.l8.N = N;
     f.l8.B = p->B;

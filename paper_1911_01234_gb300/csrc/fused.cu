@@ -83,24 +83,30 @@ __device__ void phase_cols(Ctx& c, int mode, int u_zero) {
     c.cl.sync();
 }
 
-// Lines 5-7: sort parts, then the exact search per subband.
+// Lines 5-7: sort parts, then search parts (the last part of a subband to
+// finish writes its theta and alpha).
 __device__ void phase_sure(Ctx& c, const float2* r, int k) {
     const FusedArgs& f = c.f;
     const SureArgs& a = f.sure;
     int total = 0;
-    for (int b = 0; b < f.B; ++b) total += sure_parts(a.off[b + 1] - a.off[b]);
+    for (int b = 0; b < f.B; ++b) total += sure_parts(a.off[b + 1] - a.off[b], a.max_parts);
     for (int t = c.rank; t < total; t += c.C) {
         int b = 0, acc = 0;
-        while (acc + sure_parts(a.off[b + 1] - a.off[b]) <= t) {
-            acc += sure_parts(a.off[b + 1] - a.off[b]);
+        while (acc + sure_parts(a.off[b + 1] - a.off[b], a.max_parts) <= t) {
+            acc += sure_parts(a.off[b + 1] - a.off[b], a.max_parts);
             ++b;
         }
         sure_sort_part(a, r, t - acc, b, c.slice, reinterpret_cast<float*>(c.sm));
         __syncthreads();
     }
     c.cl.sync();
-    for (int b = c.rank; b < f.B; b += c.C) {
-        sure_search_band(a, k, b, c.slice, reinterpret_cast<float*>(c.sm));
+    for (int t = c.rank; t < total; t += c.C) {
+        int b = 0, acc = 0;
+        while (acc + sure_parts(a.off[b + 1] - a.off[b], a.max_parts) <= t) {
+            acc += sure_parts(a.off[b + 1] - a.off[b], a.max_parts);
+            ++b;
+        }
+        sure_search_part(a, k, t - acc, b, c.slice, reinterpret_cast<float*>(c.sm));
         __syncthreads();
     }
     c.cl.sync();

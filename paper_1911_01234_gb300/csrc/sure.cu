@@ -1,6 +1,6 @@
 // SURE threshold step of the VDAMP iteration (Algorithm 1 lines 5-7) as two
-// kernels: the parallel sort of the subband magnitudes, then the exact
-// minimiser search per subband.  The arithmetic is in sure_dev.cuh.
+// kernels: the parallel sort of the subband magnitudes, then the parallel
+// exact minimiser search, both split into parts per subband.  The arithmetic is in sure_dev.cuh.
 #include "sure_dev.cuh"
 
 namespace vdamp {
@@ -14,17 +14,17 @@ __global__ void __launch_bounds__(SURE_THREADS) sure_sort_kernel(const __grid_co
 __global__ void __launch_bounds__(SURE_THREADS) sure_search_kernel(const __grid_constant__ SureArgs a) {
     extern __shared__ float sm_keys[];
     cudaGridDependencySynchronize();
-    sure_search_band(a, a.k, blockIdx.x, blockIdx.y, sm_keys);
+    sure_search_part(a, a.k, blockIdx.x, blockIdx.y, blockIdx.z, sm_keys);
 }
 
 size_t sure_smem(int max_band) { return sure_smem_bytes(max_band); }
 
 cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, cudaStream_t st) {
     const size_t smem = sure_smem_bytes(max_band);
-    cudaError_t e = launch_pdl(sure_sort_kernel, dim3(SURE_MAX_PARTS, a.B, batch),
+    cudaError_t e = launch_pdl(sure_sort_kernel, dim3(a.max_parts, a.B, batch),
                                dim3(SURE_THREADS), smem, st, a);
     if (e != cudaSuccess) return e;
-    return launch_pdl(sure_search_kernel, dim3(a.B, batch), dim3(SURE_THREADS), smem, st, a);
+    return launch_pdl(sure_search_kernel, dim3(a.max_parts, a.B, batch), dim3(SURE_THREADS), smem, st, a);
 }
 
 cudaError_t configure_sure(size_t smem_bytes) {

@@ -12,10 +12,14 @@
 // the threshold; ties go to the smaller theta.  alpha = (K - theta H_m / 2) / N_b.
 //
 // Two steps, each run by one 1024-thread CTA per work item:
-//   sure_sort_part   : part q of subband b sorts its share of the magnitudes
-//                      and writes them to their final places in `sorted`;
-//   sure_search_band : reads the sorted magnitudes of subband b and finds the
-//                      exact minimiser.
+//   sure_sort_part   : part q of subband b sorts its share of the magnitudes,
+//                      writes them to their final places in `sorted` and
+//                      publishes its position range with the sums of a^2 and
+//                      1/a over it;
+//   sure_search_part : part q takes the sums below and above its range from
+//                      the other parts' records, finds the best interval
+//                      starting in its range, and the last part of the
+//                      subband to finish picks the global minimiser.
 // Sorting: for a >= 0 the IEEE-754 bit pattern is an increasing integer
 // function of a, so buckets made of consecutive ranges of bit patterns
 // ((bits - lo) >> SORT_SHIFT, 1024 buckets per octave over the 16 octaves below
@@ -46,9 +50,9 @@ namespace vdamp {
 #define SURE_MAX_PARTS 8
 #define SURE_KEYS_PER_PART 2048
 
-__host__ __device__ inline int sure_parts(int nb) {
+__host__ __device__ inline int sure_parts(int nb, int max_parts) {
     int q = (nb + SURE_KEYS_PER_PART - 1) / SURE_KEYS_PER_PART;
-    return q < 1 ? 1 : (q > SURE_MAX_PARTS ? SURE_MAX_PARTS : q);
+    return q < 1 ? 1 : (q > max_parts ? max_parts : q);
 }
 
 // Shared memory for either step: keys padded to a power of two, then the
@@ -106,6 +110,73 @@ __device__ __forceinline__ void block_bitonic(float* keys, int np) {
     }
 }
 
+// Publishes the position range [p0, p1) a part sorted and the FP64 sums of a^2
+// and 1/a over it (fixed summation order: thread t takes positions p0 + t,
+// p0 + t + nthr, ..., then a tree over lanes and an ordered sum over warps).
+__device__ __forceinline__ void part_record_range(const SureArgs& a, int part, int b, int slice,
+                                                  int p0, int p1, const float* out) {
+    __shared__ double r_s2[32], r_h[32];
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    float s2 = 0.f, h = 0.f;
+    for (int i = p0 + tid; i < p1; i += nthr) {
+        const float x = out[i];
+        s2 += x * x;
+        h += x > 0.f ? __frcp_rn(x) : 0.f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        h += __shfl_xor_sync(0xffffffffu, h, o);
+    }
+    if (lane == 0) {
+        r_s2[warp] = s2;
+        r_h[warp] = h;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double ts = 0.0, th = 0.0;
+        for (int w = 0; w < (nthr >> 5); ++w) {
+            ts += r_s2[w];
+            th += r_h[w];
+        }
+        a.partrec[((size_t)slice * a.B + b) * SURE_MAX_PARTS + part] =
+            p1 > p0 ? make_double4_32a((double)p0, (double)p1, ts, th)
+                    : make_double4_32a(-1.0, -1.0, 0.0, 0.0);
+    }
+}
+
+// Publishes range [p0, p1) with per-thread partial sums s2, h already formed
+// (each thread over the buckets it sorted, in a fixed order): a tree over
+// lanes, then an FP64 sum over warps in warp order.
+__device__ __forceinline__ void part_record_sums(const SureArgs& a, int part, int b, int slice,
+                                                 int p0, int p1, float s2, float h) {
+    __shared__ double r_s2[32], r_h[32];
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        h += __shfl_xor_sync(0xffffffffu, h, o);
+    }
+    if (lane == 0) {
+        r_s2[warp] = s2;
+        r_h[warp] = h;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double ts = lane < (nthr >> 5) ? r_s2[lane] : 0.0;
+        double th = lane < (nthr >> 5) ? r_h[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ts += __shfl_xor_sync(0xffffffffu, ts, o);
+            th += __shfl_xor_sync(0xffffffffu, th, o);
+        }
+        if (lane == 0)
+            a.partrec[((size_t)slice * a.B + b) * SURE_MAX_PARTS + part] =
+                p1 > p0 ? make_double4_32a((double)p0, (double)p1, ts, th)
+                        : make_double4_32a(-1.0, -1.0, 0.0, 0.0);
+    }
+}
+
 // Part `part` of subband b of slice `slice`: sort and write its share of |r|.
 // Called by all threads of a CTA of SURE_THREADS threads; `keys` is dynamic
 // shared memory of sure_smem_bytes(max band) bytes.
@@ -118,8 +189,13 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
     const int off = a.off[b], nb = a.off[b + 1] - off;
-    const int Q = sure_parts(nb);
+    const int Q = sure_parts(nb, a.max_parts);
     if (part >= Q) return;  // uniform over the CTA
+    // bucket q (first position s0) belongs to part floor(s0 Q / nb), i.e. to the
+    // part whose position bounds [ceil(part nb / Q), ceil((part + 1) nb / Q)) hold s0
+    const int lo_pos = (int)(((long long)part * nb + Q - 1) / Q);
+    const int hi_pos = (int)(((long long)(part + 1) * nb + Q - 1) / Q);
+    __shared__ int s_qa, s_qb;
     int np = 2;
     while (np < nb) np <<= 1;
     int* hist = reinterpret_cast<int*>(keys + np);
@@ -128,6 +204,8 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
     if (tid == 0) {
         s_max_bits = 0u;
         s_big = 0;
+        s_qa = 0;
+        s_qb = 0;
     }
     const float2* r = rk + (size_t)slice * a.N + off;
     float kr[EMAX];
@@ -183,16 +261,33 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
         }
         __syncthreads();
         int run = inc - loc + (warp > 0 ? wsum[warp - 1] : 0);
+        int na = 0, nbq = 0;   // buckets starting below lo_pos / hi_pos
         for (int q = 0; q < per; ++q) {
             const int c = hist[HIX(b0 + q)];
             hist[HIX(b0 + q)] = run;
+            na += run < lo_pos;
+            nbq += run < hi_pos;
             run += c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            na += __shfl_xor_sync(0xffffffffu, na, o);
+            nbq += __shfl_xor_sync(0xffffffffu, nbq, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&s_qa, na);
+            atomicAdd(&s_qb, nbq);
         }
     }
     __syncthreads();
     if (s_big) {
-        // degenerate subband: part 0 sorts everything
-        if (part != 0) return;
+        // degenerate subband: part 0 sorts everything, the other parts are empty
+        if (part != 0) {
+            if (tid == 0)
+                a.partrec[((size_t)slice * a.B + b) * SURE_MAX_PARTS + part] =
+                    make_double4_32a(-1.0, -1.0, 0.0, 0.0);
+            return;
+        }
 #pragma unroll
         for (int e = 0; e < EMAX; ++e)
             if (tid + e * nthr < nb) keys[tid + e * nthr] = kr[e];
@@ -200,18 +295,21 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
         __syncthreads();
         block_bitonic(keys, np);
         for (int i = tid; i < nb; i += nthr) out[i] = keys[i];
+        __syncthreads();
+        part_record_range(a, part, b, slice, 0, nb, out);
         return;
     }
 #pragma unroll
     for (int e = 0; e < EMAX; ++e)
         if (tid + e * nthr < nb) keys[atomicAdd(&hist[HIX(bucket(kr[e]))], 1)] = kr[e];
     __syncthreads();
-    // hist[q] now holds the end of bucket q; the bucket belongs to the part in
-    // which its first position falls.
-    for (int q = tid; q < SORT_BUCKETS; q += nthr) {
+    // hist[q] now holds the end of bucket q; this part sorts buckets [qa, qb).
+    const int qa = s_qa, qb = s_qb;
+    float ps2 = 0.f, ph = 0.f;   // this thread's sums of a^2 and 1/a, in sorted order
+    for (int q = qa + tid; q < qb; q += nthr) {
         const int s0 = q > 0 ? hist[HIX(q - 1)] : 0, s1 = hist[HIX(q)];
         const int n = s1 - s0;
-        if (n <= 0 || (int)(((long long)s0 * Q) / nb) != part) continue;
+        if (n <= 0) continue;
         if (n <= 16) {
             float v[16];
 #pragma unroll
@@ -219,7 +317,11 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
             if (n > 1) sort_regs<16>(v);
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-                if (i < n) out[s0 + i] = v[i];
+                if (i < n) {
+                    out[s0 + i] = v[i];
+                    ps2 += v[i] * v[i];
+                    ph += v[i] > 0.f ? __frcp_rn(v[i]) : 0.f;
+                }
         } else if (n <= 32) {
             float v[32];
 #pragma unroll
@@ -227,7 +329,11 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
             sort_regs<32>(v);
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-                if (i < n) out[s0 + i] = v[i];
+                if (i < n) {
+                    out[s0 + i] = v[i];
+                    ps2 += v[i] * v[i];
+                    ph += v[i] > 0.f ? __frcp_rn(v[i]) : 0.f;
+                }
         } else {
             for (int i = s0 + 1; i < s1; ++i) {
                 const float x = keys[i];
@@ -238,9 +344,17 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
                 }
                 keys[j + 1] = x;
             }
-            for (int i = s0; i < s1; ++i) out[i] = keys[i];
+            for (int i = s0; i < s1; ++i) {
+                const float x = keys[i];
+                out[i] = x;
+                ps2 += x * x;
+                ph += x > 0.f ? __frcp_rn(x) : 0.f;
+            }
         }
     }
+    const int p0 = qa > 0 ? hist[HIX(qa - 1)] : 0;
+    const int p1 = qb > qa ? hist[HIX(qb - 1)] : p0;
+    part_record_sums(a, part, b, slice, p0, p1, ps2, ph);
 }
 
 static __device__ void sure_sort_part(const SureArgs& a, const float2* rk, int part, int b,
@@ -252,9 +366,14 @@ static __device__ void sure_sort_part(const SureArgs& a, const float2* rk, int p
         sure_sort_part_t<SORT_MAX_PER_THREAD>(a, rk, part, b, slice, keys);
 }
 
-// Subband b of slice `slice`: tau, the exact SURE minimiser theta and alpha.
-static __device__ void sure_search_band(const SureArgs& a, int k, int b, int slice, float* keys) {
-    __shared__ double s_tau;
+// Search part `part` of subband b: the exact minimiser over the intervals whose
+// lower end lies in the part's sorted range, combined across parts by the last
+// part to finish (an atomic counter per subband, returned to zero by that part),
+// which writes tau, theta and alpha.
+static __device__ void sure_search_part(const SureArgs& a, int k, int part, int b, int slice,
+                                        float* keys) {
+    __shared__ double s_tau, s_cbase, s_hafter;
+    __shared__ int s_p0, s_p1, s_last;
     __shared__ float wc[32], wh[32];
     __shared__ double woc[33], woh[33];
     __shared__ float bq[32], bt[32];
@@ -263,6 +382,9 @@ static __device__ void sure_search_band(const SureArgs& a, int k, int b, int sli
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
     const int off = a.off[b], nb = a.off[b + 1] - off;
+    const int Q = sure_parts(nb, a.max_parts);
+    if (part >= Q) return;  // uniform over the CTA
+    const size_t rec = ((size_t)slice * a.B + b) * SURE_MAX_PARTS;
 
     if (warp == 0) {   // tau: fixed-order sum of the column partials, lane by lane then a tree
         double t = 0.0;
@@ -272,30 +394,46 @@ static __device__ void sure_search_band(const SureArgs& a, int k, int b, int sli
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) s_tau = t;
     }
-    const float* srt = a.sorted + (size_t)slice * a.N + off;
-    batched_for<16, float>(tid, nb, nthr, [&](int i) { return srt[i]; },
-                           [&](int i, float v) { keys[i] = v; });
+    if (warp == 1) {   // this part's range and the sums of the parts below and above it
+        const double4_32a me = a.partrec[rec + part];
+        const int p0 = (int)me.x, p1 = (int)me.y;
+        double cb = 0.0, ha = 0.0;
+        if (lane < Q && lane != part) {
+            const double4_32a o = a.partrec[rec + lane];
+            if (o.x >= 0.0) {
+                if ((int)o.y <= p0) cb = o.z;
+                if ((int)o.x >= p1) ha = o.w;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cb += __shfl_xor_sync(0xffffffffu, cb, o);
+            ha += __shfl_xor_sync(0xffffffffu, ha, o);
+        }
+        if (lane == 0) {
+            s_p0 = p0;
+            s_p1 = p1;
+            s_cbase = cb;
+            s_hafter = ha;
+        }
+    }
     __syncthreads();
     const double tau = s_tau;
-    const size_t orow = ((size_t)slice * a.iters + k) * a.B + b;
-    if (!(tau > 0.0) || !isfinite(tau)) {
-        // No effective noise (p = 1 and sigma = 0): keep r, no Onsager term.
-        if (tid == 0) {
-            a.tau_out[orow] = tau;
-            a.thr_out[orow] = 0.0;
-            a.alpha_out[orow] = 0.0;
-            a.coef[slice * a.B + b] = make_float4(0.f, 0.f, 1.f, 0.f);
-            if (!isfinite(tau)) record_numeric(a.status, k);
-        }
-        return;
-    }
+    const bool live = tau > 0.0 && isfinite(tau) && s_p1 > s_p0;
+    const int p0 = live ? s_p0 : 0, len = live ? s_p1 - s_p0 : 0;
+    // keys[0] = the magnitude just below the part (0 for the first), keys[1 + i] = a_(p0 + i)
+    const float* srt = a.sorted + (size_t)slice * a.N + off;
+    if (tid == 0) keys[0] = p0 > 0 ? srt[p0 - 1] : 0.f;
+    batched_for<16, float>(tid, len, nthr, [&](int i) { return srt[p0 + i]; },
+                           [&](int i, float v) { keys[1 + i] = v; });
+    __syncthreads();
 
-    // ---- prefix sums of a^2 (from below) and suffix sums of 1/a (from above)
-    const int E = (nb + nthr - 1) / nthr;
-    const int m0 = min(tid * E, nb), m1 = min(m0 + E, nb);
+    // ---- prefix sums of a^2 (from below) and suffix sums of 1/a (from above), local
+    const int E = (len + nthr - 1) / nthr;
+    const int l0 = min(tid * E, len), l1 = min(l0 + E, len);
     float cs = 0.f, hs = 0.f;
-    for (int i = m0; i < m1; ++i) {
-        const float x = keys[i];
+    for (int i = l0; i < l1; ++i) {
+        const float x = keys[1 + i];
         cs += x * x;
         hs += x > 0.f ? __frcp_rn(x) : 0.f;
     }
@@ -314,7 +452,7 @@ static __device__ void sure_search_band(const SureArgs& a, int k, int b, int sli
     if (lane == 31) wc[warp] = ic;
     if (lane == 0) wh[warp] = ih;
     __syncthreads();
-    if (warp == 0) {   // FP64 scans of the warp totals: C from below, H from above
+    if (warp == 0) {   // FP64 scans of the warp totals, offset by the other parts' sums
         double c = lane < nw ? (double)wc[lane] : 0.0;
         double h = lane < nw ? (double)wh[nw - 1 - lane] : 0.0;
 #pragma unroll
@@ -326,37 +464,37 @@ static __device__ void sure_search_band(const SureArgs& a, int k, int b, int sli
                 h += th;
             }
         }
-        // inclusive -> exclusive
         const double ce = __shfl_up_sync(0xffffffffu, c, 1);
         const double he = __shfl_up_sync(0xffffffffu, h, 1);
         if (lane < nw) {
-            woc[lane] = lane ? ce : 0.0;
-            woh[nw - 1 - lane] = lane ? he : 0.0;
+            woc[lane] = s_cbase + (lane ? ce : 0.0);
+            woh[nw - 1 - lane] = s_hafter + (lane ? he : 0.0);
         }
         if (lane == nw - 1) {
-            woc[nw] = c;
-            woh[nw] = h;
+            woc[nw] = s_cbase + c;
+            woh[nw] = s_hafter + h;
         }
     }
     __syncthreads();
-    const double c_base = woc[warp] + (double)ec;   // sum of a^2 over indices < m0
-    const double h_after = woh[warp] + (double)eh;  // sum of 1/a over indices >= m1
-    const double c_total = woc[nw];
+    const double c_base = woc[warp] + (double)ec;   // sum of a^2 below position p0 + l0
+    const double h_after = woh[warp] + (double)eh;  // sum of 1/a from position p0 + l1 on
+    const double c_all = woc[nw];                    // sum of a^2 below p0 + len
 
-    // ---- best candidate of this thread's intervals (FP32)
+    // ---- best candidate of this thread's intervals (FP32); m is the global position
     const float tf = (float)tau;
     const float cb = (float)c_base, ha = (float)h_after;
     float best_q = INFINITY, best_t = INFINITY;
     int best_m = -1;
     float csuf = 0.f, hsuf = 0.f;
-    for (int m = m1 - 1; m >= m0; --m) {
-        const float x = keys[m];
+    for (int l = l1 - 1; l >= l0; --l) {
+        const float x = keys[1 + l];
         csuf += x * x;
         hsuf += x > 0.f ? __frcp_rn(x) : 0.f;
+        const int m = p0 + l;
         const float cm = cb + (cs - csuf);
         const float hm = ha + hsuf;
         const float K = (float)(nb - m);
-        const float lo = m > 0 ? keys[m - 1] : 0.f;
+        const float lo = keys[l];  // a_(m-1), or 0 at m = 0
         float th = tf * hm * __frcp_rn(2.0f * K);
         th = fmaxf(th, lo);
         if (th < x) {
@@ -368,17 +506,16 @@ static __device__ void sure_search_band(const SureArgs& a, int k, int b, int sli
             }
         }
     }
-    if (m1 == nb && m0 < m1) {  // theta >= max a: everything thresholded
-        const float q = (float)(c_total - (double)nb * tau);
-        const float th = keys[nb - 1];
+    const bool has_top = live && p0 + len == nb && l1 == len && l0 < l1;
+    if (has_top) {  // theta >= max a: everything thresholded
+        const float q = (float)(c_all - (double)nb * tau);
+        const float th = keys[len];
         if (q < best_q || (q == best_q && th < best_t)) {
             best_q = q;
             best_t = th;
             best_m = nb;
         }
     }
-
-    // ---- block argmin (q, then theta)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float q2 = __shfl_xor_sync(0xffffffffu, best_q, o);
@@ -396,48 +533,117 @@ static __device__ void sure_search_band(const SureArgs& a, int k, int b, int sli
         bm[warp] = best_m;
     }
     __syncthreads();
-    if (tid == 0) {
-        float q = bq[0], t = bt[0];
-        int m = bm[0];
-        for (int w = 1; w < nw; ++w) {
-            if (bq[w] < q || (bq[w] == q && (bt[w] < t || (bt[w] == t && bm[w] < m)))) {
-                q = bq[w];
-                t = bt[w];
-                m = bm[w];
+    if (warp == 0) {
+        float q = lane < nw ? bq[lane] : INFINITY, t = lane < nw ? bt[lane] : INFINITY;
+        int m = lane < nw ? bm[lane] : -1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float q2 = __shfl_xor_sync(0xffffffffu, q, o);
+            const float t2 = __shfl_xor_sync(0xffffffffu, t, o);
+            const int m2 = __shfl_xor_sync(0xffffffffu, m, o);
+            if (q2 < q || (q2 == q && (t2 < t || (t2 == t && m2 < m)))) {
+                q = q2;
+                t = t2;
+                m = m2;
             }
         }
-        s_win_m = m;
+        if (lane == 0) {
+            s_win_m = m;
+            if (m < 0) a.bestrec[rec + part] = make_double4_32a(INFINITY, 0.0, 0.0, -1.0);
+        }
     }
     __syncthreads();
 
-    // ---- theta and alpha of the chosen interval, FP64, by the thread that owns it
+    // ---- the part's best in FP64, by the thread that owns it
     const int wm = s_win_m;
-    const bool owner = (wm == nb) ? (m1 == nb && m0 < m1) : (wm >= m0 && wm < m1);
+    const bool owner = wm >= 0 && ((wm == nb) ? has_top : (wm >= p0 + l0 && wm < p0 + l1));
     if (owner) {
-        double theta, alpha;
+        double theta, hmd, val;
         if (wm == nb) {
-            theta = (double)keys[nb - 1];
-            alpha = 0.0;
+            theta = (double)keys[len];
+            hmd = 0.0;
+            val = c_all - (double)nb * tau;
         } else {
-            float hl = 0.f;   // same FP32 reciprocals as the candidate pass
-            for (int i = m1 - 1; i >= wm; --i) {
-                const float x = keys[i];
+            float hl = 0.f, cl = 0.f;  // same FP32 sums as the candidate pass
+            for (int l = l1 - 1; l >= wm - p0; --l) {
+                const float x = keys[1 + l];
                 hl += x > 0.f ? __frcp_rn(x) : 0.f;
             }
-            const double hm = h_after + (double)hl;
+            for (int l = l0; l < wm - p0; ++l) {
+                const float x = keys[1 + l];
+                cl += x * x;
+            }
+            hmd = h_after + (double)hl;
+            const double cmd = c_base + (double)cl;
             const double K = (double)(nb - wm);
-            const double lo = wm > 0 ? (double)keys[wm - 1] : 0.0;
-            theta = fmax(tau * hm / (2.0 * K), lo);
-            theta = fmin(theta, (double)keys[wm]);
-            alpha = (K - 0.5 * theta * hm) / (double)nb;
+            const double lo = (double)keys[wm - p0];
+            theta = fmax(tau * hmd / (2.0 * K), lo);
+            theta = fmin(theta, (double)keys[1 + wm - p0]);
+            val = cmd - wm * tau + K * theta * theta + K * tau - tau * theta * hmd;
         }
-        a.tau_out[orow] = tau;
-        a.thr_out[orow] = theta;
-        a.alpha_out[orow] = alpha;
-        const double inv = 1.0 / (1.0 - alpha);
-        a.coef[slice * a.B + b] = make_float4((float)theta, (float)alpha, (float)inv, 0.f);
-        if (!isfinite(alpha) || !isfinite(theta) || !isfinite(inv)) record_numeric(a.status, k);
+        a.bestrec[rec + part] = make_double4_32a(val, theta, hmd, (double)wm);
     }
+    __syncthreads();
+
+    // ---- the last part of the subband to finish combines the parts
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&a.counter[(size_t)slice * a.B + b], 1u) == (unsigned)(Q - 1);
+    }
+    __syncthreads();
+    if (!s_last || warp != 0) return;
+    __threadfence();
+    const size_t orow = ((size_t)slice * a.iters + k) * a.B + b;
+    // lane q reads part q's best; ties go to the smaller theta, then the smaller m
+    double bv = INFINITY, btheta = INFINITY, bh = 0.0;
+    int bmi = -1;
+    if (lane < Q) {
+        const volatile double* br = reinterpret_cast<const volatile double*>(a.bestrec + rec + lane);
+        const int m = (int)br[3];
+        if (m >= 0) {
+            bv = br[0];
+            btheta = br[1];
+            bh = br[2];
+            bmi = m;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const double t2 = __shfl_xor_sync(0xffffffffu, btheta, o);
+        const double h2 = __shfl_xor_sync(0xffffffffu, bh, o);
+        const int m2 = __shfl_xor_sync(0xffffffffu, bmi, o);
+        const bool take = m2 >= 0 && (bmi < 0 || v2 < bv ||
+                                      (v2 == bv && (t2 < btheta || (t2 == btheta && m2 < bmi))));
+        if (take) {
+            bv = v2;
+            btheta = t2;
+            bh = h2;
+            bmi = m2;
+        }
+    }
+    if (lane != 0) return;
+    a.counter[(size_t)slice * a.B + b] = 0u;
+    if (!(tau > 0.0) || !isfinite(tau)) {
+        // No effective noise (p = 1 and sigma = 0): keep r, no Onsager term.
+        a.tau_out[orow] = tau;
+        a.thr_out[orow] = 0.0;
+        a.alpha_out[orow] = 0.0;
+        a.coef[slice * a.B + b] = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (!isfinite(tau)) record_numeric(a.status, k);
+        return;
+    }
+    double theta = 0.0, alpha = 0.0;
+    if (bmi >= 0) {
+        theta = btheta;
+        alpha = (bmi == nb) ? 0.0 : ((double)(nb - bmi) - 0.5 * theta * bh) / (double)nb;
+    }
+    a.tau_out[orow] = tau;
+    a.thr_out[orow] = theta;
+    a.alpha_out[orow] = alpha;
+    const double inv = 1.0 / (1.0 - alpha);
+    a.coef[slice * a.B + b] = make_float4((float)theta, (float)alpha, (float)inv, 0.f);
+    if (bmi < 0 || !isfinite(alpha) || !isfinite(theta) || !isfinite(inv)) record_numeric(a.status, k);
 }
 
 }  // namespace vdamp

@@ -21,8 +21,11 @@ thresholds.  The free-running test therefore holds the tolerances for k < 10
 or until the runs first pick different thresholds (which must not happen
 before k = 5); every iteration is held to them teacher-forced (each step
 started from the oracle's own r~_k, where a threshold difference must be a
-certified tie); and the final NMSE must fall within 0.01 dB of the range
-spanned by FP64 oracle runs perturbed at the FP32 level.
+certified tie); and the final NMSE must fall within 4 standard deviations
+(at least 0.02 dB) of the mean of FP64 oracle runs perturbed at the FP32 level
+(state rounded to complex64, then multiplied by 1 + 1e-6 N(0, 1) before every
+iteration).  24 such runs spread with a standard deviation of 0.014 dB over a
+range of 0.054 dB; with 4e-6 the range widens to 0.077 dB.
 """
 import math
 
@@ -163,7 +166,7 @@ def test_iteration_teacher_forced(wl, K):
 
 # ------------------------------------------------------ the whole solve ---
 
-def _perturbed_oracle_nmse(wl, runs=3, eps=1e-7):
+def _perturbed_oracle_nmse(wl, runs=8, eps=1e-6):
     """Final NMSE of FP64 oracle runs whose state is rounded to complex64 and perturbed by
     eps (relative) before every iteration: the spread the method itself gives an FP32 run."""
     out = []
@@ -214,8 +217,9 @@ def test_solve_free_running(wl, k_strict):
         assert rel(xh, res.x_hat) < 1e-4
         assert abs(nm_gpu - O.nmse_db(res.x_hat, pr.x0)) < 0.01
     else:
-        ens = _perturbed_oracle_nmse(wl) + [O.nmse_db(res.x_hat, pr.x0)]
-        assert min(ens) - 0.01 <= nm_gpu <= max(ens) + 0.01, (nm_gpu, ens)
+        ens = np.array(_perturbed_oracle_nmse(wl) + [O.nmse_db(res.x_hat, pr.x0)])
+        band = max(4.0 * ens.std(ddof=1), 0.02)
+        assert abs(nm_gpu - ens.mean()) <= band, (nm_gpu, ens.mean(), band, ens)
     plan.close()
 
 
