@@ -328,8 +328,17 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     }
     p->off[p->B] = o;
 
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    // columns per CTA of the column pass: 8, fewer while a full batch would
+    // leave SMs without a column block (never below 2: each block stages the
+    // y spectra once for all its columns)
     int cb = 8;
     while (nx % cb) cb >>= 1;
+    while (cb > 2 && (size_t)max_batch * (nx / cb) < (size_t)std::max(p->num_sms, 1)) cb >>= 1;
     p->cb = cb;
     p->nparts = nx / cb;
     p->rpc = std::max(1, 512 / nx);
@@ -412,11 +421,6 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(cudaMemcpy(p->tw_x, twx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice));
     A(cudaMemset(p->status, 0, 2 * sizeof(int)));
     A(cudaMemset(p->counter, 0, MB * p->B * sizeof(unsigned)));  // each search returns it to 0
-    {
-        int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    }
     A(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     A(vdamp::configure_col_pass(vdamp::col_pass_smem(ny, cb, nt)));
     A(vdamp::configure_fft_rows(2 * (size_t)p->rpc * nx * sizeof(float2)));

@@ -76,6 +76,9 @@ __device__ __forceinline__ void dwt_tile_t(const DwtArgs& a, const float2* in_ba
     __syncthreads();
     const int Ho = H >> 1, Wo = W >> 1;
     const size_t sN = (size_t)slice * a.N;
+    const float4 kq[4] = {src_coef(src, slice, a.band[0]), src_coef(src, slice, a.band[1]),
+                          src_coef(src, slice, a.band[2]), src_coef(src, slice, a.band[3])};
+    const float2* rs = src.r + sN;
     for (int idx = tid; idx < TO * TO; idx += blockDim.x) {
         const int m = idx / TO, n = idx - m * TO;
         const int gm = m0 + m, gn = n0 + n;
@@ -91,16 +94,18 @@ __device__ __forceinline__ void dwt_tile_t(const DwtArgs& a, const float2* in_ba
             hh.x += hk * x.x; hh.y += hk * x.y;
             d.x += gk * x.x;  d.y += gk * x.y;
         }
-        const size_t pos = (size_t)gm * Wo + gn;
+        const int pos = gm * Wo + gn;
         const float2 outs[4] = {ll, hh, v, d};
+        float2 rv[4];
 #pragma unroll
-        for (int q = 1; q < 4; ++q) {
-            const size_t p = a.off[q] + pos;
-            packed[sN + p] = cadd(outs[q], src_value(src, slice, a.N, p, a.band[q]));
-        }
+        for (int q = 0; q < 4; ++q)   // the r~ values of the four bands, loads issued together
+            rv[q] = (src.mode == SRC_ZERO || (q == 0 && !a.last)) ? make_float2(0.f, 0.f)
+                                                                  : rs[a.off[q] + pos];
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+            packed[sN + a.off[q] + pos] = cadd(outs[q], src_apply(src.mode, rv[q], kq[q]));
         if (a.last) {
-            const size_t p = a.off[0] + pos;
-            packed[sN + p] = cadd(ll, src_value(src, slice, a.N, p, a.band[0]));
+            packed[sN + a.off[0] + pos] = cadd(ll, src_apply(src.mode, rv[0], kq[0]));
         } else {
             a.ll_out[(size_t)slice * a.ll_stride + pos] = ll;
         }
@@ -108,69 +113,106 @@ __device__ __forceinline__ void dwt_tile_t(const DwtArgs& a, const float2* in_ba
 }
 
 // Synthesis tile (tile_x, tile_y) of slice `slice`; L taps, TO x TO outputs.
+// Polyphase form: output rows 2u and 2u + 1 read the same coefficient rows
+// (u - kk + L/2 - 1 for tap pairs 2kk, 2kk + 1), and likewise along x, so a
+// thread forms both phases from one set of shared-memory reads with the taps
+// at compile-time positions.
 template <int L, int TO>
 __device__ __forceinline__ void idwt_tile_t(const IdwtArgs& a, float2* out, const SrcSpec& src,
                                             int tile_x, int tile_y, int slice, float2* sm) {
     constexpr int hL = L / 2;
     constexpr int CT = TO / 2 + hL - 1;
+    constexpr int CTT = CT * CT;
+    constexpr int TH2 = TO / 2;
     float2* C = sm;                  // 4 x CT x CT (LL, H, V, D)
-    float2* TL = C + 4 * CT * CT;    // TO x CT, low along x
+    float2* TL = C + 4 * CTT;        // TO x CT, low along x
     float2* TH = TL + TO * CT;       // TO x CT, high along x
     const int y0 = tile_y * TO, x0 = tile_x * TO;
     const int h = a.h, w = a.w;
     const int ms = y0 / 2 - (hL - 1), ns = x0 / 2 - (hL - 1);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    // per-band packed offsets and denoiser parameters, selected without indexing
+    const int o0 = a.off[0], o1 = a.off[1], o2 = a.off[2], o3 = a.off[3];
+    const float4 k0 = src_coef(src, slice, a.band[0]), k1 = src_coef(src, slice, a.band[1]);
+    const float4 k2 = src_coef(src, slice, a.band[2]), k3 = src_coef(src, slice, a.band[3]);
+    const float2* rs = src.r + (size_t)slice * a.N;
+    const float2* lls = a.ll_in + (size_t)slice * a.ll_stride;
+    const bool ll_dense = !a.first;
+    const int mode = src.mode;
 
     batched_for<8, float2>(
-        tid, 4 * CT * CT, blockDim.x,
+        tid, 4 * CTT, nthr,
         [&](int idx) {
-            const int q = idx / (CT * CT);
-            const int rem = idx - q * CT * CT;
+            const int q = idx / CTT;
+            const int rem = idx - q * CTT;
             const int r = rem / CT, c = rem - r * CT;
-            const size_t pos = (size_t)wrap(ms + r, h) * w + wrap(ns + c, w);
-            if (q == 0 && !a.first) return a.ll_in[(size_t)slice * a.ll_stride + pos];
-            return src_value(src, slice, a.N, a.off[q] + pos, a.band[q]);
+            const int pos = wrap(ms + r, h) * w + wrap(ns + c, w);
+            if (q == 0 && ll_dense) return lls[pos];
+            if (mode == SRC_ZERO) return make_float2(0.f, 0.f);
+            const int o = q == 0 ? o0 : (q == 1 ? o1 : (q == 2 ? o2 : o3));
+            return rs[o + pos];
         },
-        [&](int idx, float2 v) { C[idx] = v; });
+        [&](int idx, float2 v) {
+            const int q = idx / CTT;
+            if (!(q == 0 && ll_dense)) {
+                const float4 k = q == 0 ? k0 : (q == 1 ? k1 : (q == 2 ? k2 : k3));
+                v = src_apply(mode, v, k);
+            }
+            C[idx] = v;
+        });
     __syncthreads();
     const float2* LL = C;
-    const float2* HB = C + CT * CT;
-    const float2* VB = C + 2 * CT * CT;
-    const float2* DB = C + 3 * CT * CT;
-    for (int idx = tid; idx < TO * CT; idx += blockDim.x) {
-        const int t = idx / CT, c = idx - t * CT;
-        float2 lo = make_float2(0.f, 0.f), hi = lo;
-        const int par = t & 1;
+    const float2* HB = C + CTT;
+    const float2* VB = C + 2 * CTT;
+    const float2* DB = C + 3 * CTT;
+    // along y: rows 2u, 2u + 1 of TL (from LL, V) and TH (from H, D)
+    for (int idx = tid; idx < TH2 * CT; idx += nthr) {
+        const int u = idx / CT, c = idx - u * CT;
+        float2 le = make_float2(0.f, 0.f), lo = le, he = le, ho = le;
 #pragma unroll
         for (int kk = 0; kk < hL; ++kk) {
-            const int k = 2 * kk + par;
-            const int r = (t - k) / 2 + hL - 1;
-            const float hk = a.f.h[k], gk = a.f.g[k];
+            const int r = u - kk + hL - 1;
             const float2 ll = LL[r * CT + c], vv = VB[r * CT + c];
             const float2 hb = HB[r * CT + c], dd = DB[r * CT + c];
-            lo.x += hk * ll.x + gk * vv.x; lo.y += hk * ll.y + gk * vv.y;
-            hi.x += hk * hb.x + gk * dd.x; hi.y += hk * hb.y + gk * dd.y;
+            const float he0 = a.f.h[2 * kk], ge0 = a.f.g[2 * kk];
+            const float he1 = a.f.h[2 * kk + 1], ge1 = a.f.g[2 * kk + 1];
+            le.x += he0 * ll.x + ge0 * vv.x; le.y += he0 * ll.y + ge0 * vv.y;
+            lo.x += he1 * ll.x + ge1 * vv.x; lo.y += he1 * ll.y + ge1 * vv.y;
+            he.x += he0 * hb.x + ge0 * dd.x; he.y += he0 * hb.y + ge0 * dd.y;
+            ho.x += he1 * hb.x + ge1 * dd.x; ho.y += he1 * hb.y + ge1 * dd.y;
         }
-        TL[idx] = lo;
-        TH[idx] = hi;
+        TL[(2 * u) * CT + c] = le;
+        TL[(2 * u + 1) * CT + c] = lo;
+        TH[(2 * u) * CT + c] = he;
+        TH[(2 * u + 1) * CT + c] = ho;
     }
     __syncthreads();
+    // along x: pixels 2v, 2v + 1 of row t, stored as one 16-byte pair when the
+    // slice's output starts on a 16-byte boundary (rows have an even length)
     const int Ho = 2 * h, Wo = 2 * w;
-    for (int idx = tid; idx < TO * TO; idx += blockDim.x) {
-        const int t = idx / TO, s = idx - t * TO;
-        const int gy = y0 + t, gx = x0 + s;
+    float2* obase = out + (size_t)slice * a.out_stride;
+    const bool al16 = (reinterpret_cast<uintptr_t>(obase) & 15) == 0;
+    for (int idx = tid; idx < TO * TH2; idx += nthr) {
+        const int t = idx / TH2, v = idx - t * TH2;
+        const int gy = y0 + t, gx = x0 + 2 * v;
         if (gy >= Ho || gx >= Wo) continue;
-        float2 o = make_float2(0.f, 0.f);
-        const int par = s & 1;
+        float2 oe = make_float2(0.f, 0.f), oo = oe;
 #pragma unroll
-        for (int ll = 0; ll < hL; ++ll) {
-            const int l = 2 * ll + par;
-            const int c = (s - l) / 2 + hL - 1;
+        for (int l2 = 0; l2 < hL; ++l2) {
+            const int c = v - l2 + hL - 1;
             const float2 lo = TL[t * CT + c], hi = TH[t * CT + c];
-            o.x += a.f.h[l] * lo.x + a.f.g[l] * hi.x;
-            o.y += a.f.h[l] * lo.y + a.f.g[l] * hi.y;
+            const float h0 = a.f.h[2 * l2], g0 = a.f.g[2 * l2];
+            const float h1 = a.f.h[2 * l2 + 1], g1 = a.f.g[2 * l2 + 1];
+            oe.x += h0 * lo.x + g0 * hi.x; oe.y += h0 * lo.y + g0 * hi.y;
+            oo.x += h1 * lo.x + g1 * hi.x; oo.y += h1 * lo.y + g1 * hi.y;
         }
-        out[(size_t)slice * a.out_stride + (size_t)gy * Wo + gx] = o;
+        float2* o = obase + (size_t)gy * Wo + gx;
+        if (al16) {
+            *reinterpret_cast<float4*>(o) = make_float4(oe.x, oe.y, oo.x, oo.y);
+        } else {
+            o[0] = oe;
+            o[1] = oo;
+        }
     }
 }
 

@@ -5,8 +5,8 @@
 namespace vdamp {
 
 template <bool INV>
-__global__ void fft_rows_kernel(const float2* in, float2* out, int ny, int nx, FftAxis ax,
-                                float scale, int rpc) {
+__global__ void fft_rows_kernel(const float2* in, float2* out, int ny, int nx,
+                                const __grid_constant__ FftAxis ax, float scale, int rpc) {
     extern __shared__ float2 sm[];
     cudaGridDependencySynchronize();
     const int row0 = blockIdx.x * rpc;

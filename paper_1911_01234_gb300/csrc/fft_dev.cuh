@@ -159,41 +159,50 @@ __device__ __forceinline__ void bfly(const float2* __restrict__ src, float2* __r
     for (int r = 0; r < R; ++r) dst[tbase + (d + r * Ns) * es] = v[r];
 }
 
-// All stages for `ntrans` transforms.  ROWS: transform t at t*tstride with
+// One stage of radix R over all transforms; then fft_stages, all stages for
+// `ntrans` transforms.  ROWS: transform t at t*tstride with
 // unit element stride, consecutive threads take consecutive butterflies.
-// Otherwise (columns): transform t at t with element stride `es`,
-// consecutive threads take consecutive transforms.  Returns the buffer that
-// holds the result.  Ends with a __syncthreads().
-template <bool INV, bool ROWS>
-static __device__ float2* fft_stages(float2* a, float2* b, const FftAxis& ax, int ntrans, int tstride,
-                              int es) {
+// Otherwise (columns): CB transforms (a power of two), transform t at t with
+// element stride CB, consecutive threads take consecutive transforms.
+// Returns the buffer that holds the result.  Ends with a __syncthreads().
+template <int R, bool INV, bool ROWS, int CB>
+__device__ __forceinline__ void fft_stage(const float2* src, float2* dst, const FftAxis& ax,
+                                          int ntrans, int tstride, int nb, int Ns, int step) {
+    const int total = nb * ntrans;
+    const float inv_nb = 1.0f / (float)nb;
+    const float inv_ns = 1.0f / (float)Ns;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int t, j;
+        if (ROWS) {
+            t = fdivmod(idx, nb, inv_nb, j);
+        } else {
+            t = idx & (CB - 1);
+            j = idx / CB;
+        }
+        bfly<R, INV>(src, dst, ROWS ? t * tstride : t, ROWS ? 1 : CB, nb, j, Ns, inv_ns, step,
+                     ax.tw);
+    }
+}
+
+template <bool INV, bool ROWS, int CB = 1>
+static __device__ float2* fft_stages(float2* a, float2* b, const FftAxis& ax, int ntrans,
+                                     int tstride) {
     const int n = ax.n;
     int Ns = 1;
     float2* src = a;
     float2* dst = b;
-    const float inv_tr = 1.0f / (float)ntrans;
+    if (!ROWS) ntrans = CB;
     for (int s = 0; s < ax.nstages; ++s) {
         const int R = ax.radix[s];
         const int nb = n / R;
-        const int total = nb * ntrans;
         const int step = n / (Ns * R);
-        const float inv_nb = 1.0f / (float)nb;
-        const float inv_ns = 1.0f / (float)Ns;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            int t, j;
-            if (ROWS)
-                t = fdivmod(idx, nb, inv_nb, j);
-            else
-                j = fdivmod(idx, ntrans, inv_tr, t);
-            const int tb = ROWS ? t * tstride : t;
-            const int e = ROWS ? 1 : es;
-            switch (R) {
-                case 2: bfly<2, INV>(src, dst, tb, e, nb, j, Ns, inv_ns, step, ax.tw); break;
-                case 3: bfly<3, INV>(src, dst, tb, e, nb, j, Ns, inv_ns, step, ax.tw); break;
-                case 4: bfly<4, INV>(src, dst, tb, e, nb, j, Ns, inv_ns, step, ax.tw); break;
-                case 5: bfly<5, INV>(src, dst, tb, e, nb, j, Ns, inv_ns, step, ax.tw); break;
-                default: bfly<8, INV>(src, dst, tb, e, nb, j, Ns, inv_ns, step, ax.tw); break;
-            }
+        // one dispatch per stage; the butterfly loop itself has no indirect branch
+        switch (R) {
+            case 2: fft_stage<2, INV, ROWS, CB>(src, dst, ax, ntrans, tstride, nb, Ns, step); break;
+            case 3: fft_stage<3, INV, ROWS, CB>(src, dst, ax, ntrans, tstride, nb, Ns, step); break;
+            case 4: fft_stage<4, INV, ROWS, CB>(src, dst, ax, ntrans, tstride, nb, Ns, step); break;
+            case 5: fft_stage<5, INV, ROWS, CB>(src, dst, ax, ntrans, tstride, nb, Ns, step); break;
+            default: fft_stage<8, INV, ROWS, CB>(src, dst, ax, ntrans, tstride, nb, Ns, step); break;
         }
         __syncthreads();
         float2* t = src;
@@ -215,61 +224,53 @@ static __device__ void fft_rows_block(const float2* in, float2* out, int ny, int
     batched_for<8, float2>(threadIdx.x, cnt, blockDim.x, [&](int i) { return in[base + i]; },
                            [&](int i, float2 v) { A[i] = v; });
     __syncthreads();
-    float2* res = fft_stages<INV, true>(A, Bf, ax, rows, nx, 1);
+    float2* res = fft_stages<INV, true>(A, Bf, ax, rows, nx);
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[base + i] = cscale(res[i], scale);
 }
 
+// Shared memory of a column block: two ny x cb work buffers, the per-column
+// tau sums (FP64), the y spectra and the per-warp column sums (up to 32 warps).
 inline size_t col_pass_smem_bytes(int ny, int cb, int ntypes) {
-    return 2 * (size_t)ny * cb * sizeof(float2) + (size_t)ntypes * ny * sizeof(float);
+    return 2 * (size_t)ny * cb * sizeof(float2) + (size_t)ntypes * cb * sizeof(double) +
+           (size_t)ntypes * ny * sizeof(float) + (size_t)32 * ntypes * cb * sizeof(float);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Column block cblk (columns [cblk cb, (cblk + 1) cb)) of slice `slice`; its
+// Column block cblk (columns [cblk CB, (cblk + 1) CB)) of slice `slice`; its
 // tau partial sums go to tau_part[slice][cblk][B] (nparts blocks per slice).
-// blockDim.x must be a multiple of cb.
-static __device__ void col_pass_block(const ColArgs& a, int mode, int u_zero, int cblk, int nparts,
-                                      int slice, float2* sm) {
-    const int ny = a.ny, nx = a.nx, cb = a.cb;
+// Element idx of the block is row idx / CB, column idx % CB; blockDim.x must
+// be a multiple of 32 (and so of CB), so a thread keeps one column.
+template <int CB>
+__device__ __forceinline__ void col_pass_block_t(const ColArgs& a, int mode, int u_zero, int cblk,
+                                                 int nparts, int slice, float2* sm) {
+    const int ny = a.ny, nx = a.nx;
+    const int nt = a.ntypes;
     float2* A = sm;
-    float2* Bf = sm + ny * cb;
-    float* eys = reinterpret_cast<float*>(sm + 2 * ny * cb);
-    const int c0 = cblk * cb;
-    const size_t sbase = (size_t)slice * ny * nx;
-    const int tid = threadIdx.x;
-    const int cnt = ny * cb;
+    float2* Bf = sm + ny * CB;
+    double* colq = reinterpret_cast<double*>(sm + 2 * ny * CB);  // [nt][CB]
+    float* eys = reinterpret_cast<float*>(colq + nt * CB);        // [nt][ny]
+    float* red = eys + nt * ny;                                    // [warp][nt][CB]
+    const int c0 = cblk * CB;
+    const size_t sbase = (size_t)slice * ny * nx + c0;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int cnt = ny * CB;
+    auto gidx = [&](int idx) { return sbase + (size_t)(idx / CB) * nx + (idx & (CB - 1)); };
 
     // ---- forward column transform (or U = 0)
     float2* U = nullptr;
     if (mode != COL_INV && u_zero) {
         U = nullptr;
     } else {
-        batched_for<8, float2>(
-            tid, cnt, blockDim.x,
-            [&](int idx) {
-                const int c = idx % cb, i = idx / cb;
-                return a.in[sbase + (size_t)i * nx + c0 + c];
-            },
-            [&](int idx, float2 v) { A[idx] = v; });
+        batched_for<8, float2>(tid, cnt, nthr, [&](int idx) { return a.in[gidx(idx)]; },
+                               [&](int idx, float2 v) { A[idx] = v; });
         __syncthreads();
         if (mode == COL_INV) {
-            float2* res = fft_stages<true, false>(A, Bf, a.ax, cb, 0, cb);
-            for (int idx = tid; idx < cnt; idx += blockDim.x) {
-                int c = idx % cb, i = idx / cb;
-                a.out[sbase + (size_t)i * nx + c0 + c] = cscale(res[idx], a.scale_inv);
-            }
+            float2* res = fft_stages<true, false, CB>(A, Bf, a.ax, CB, 0);
+            for (int idx = tid; idx < cnt; idx += nthr) a.out[gidx(idx)] = cscale(res[idx], a.scale_inv);
             return;
         }
-        U = fft_stages<false, false>(A, Bf, a.ax, cb, 0, cb);
+        U = fft_stages<false, false, CB>(A, Bf, a.ax, CB, 0);
         if (mode == COL_FWD) {
-            for (int idx = tid; idx < cnt; idx += blockDim.x) {
-                int c = idx % cb, i = idx / cb;
-                a.out[sbase + (size_t)i * nx + c0 + c] = cscale(U[idx], a.scale_fwd);
-            }
+            for (int idx = tid; idx < cnt; idx += nthr) a.out[gidx(idx)] = cscale(U[idx], a.scale_fwd);
             return;
         }
     }
@@ -277,26 +278,25 @@ static __device__ void col_pass_block(const ColArgs& a, int mode, int u_zero, in
     // ---- k-space step of Algorithm 1 (lines 3-5), written into X
     float2* X = (U == A) ? Bf : A;
     if (mode == COL_ITER) {
-        batched_for<8, float>(tid, a.ntypes * ny, blockDim.x, [&](int i) { return a.ey[i]; },
+        batched_for<8, float>(tid, nt * ny, nthr, [&](int i) { return a.ey[i]; },
                               [&](int i, float v) { eys[i] = v; });
         __syncthreads();
     }
     const float sig = mode == COL_ITER ? a.sigma[slice] : 0.f;
     const float sig2 = sig * sig;
-    float q[2 * VDAMP_MAX_LEVELS];
+    float q[2 * VDAMP_MAX_LEVELS];  // this thread's column: sum over its rows of S_y,t(ky) v
 #pragma unroll
     for (int t = 0; t < 2 * VDAMP_MAX_LEVELS; ++t) q[t] = 0.f;
     // chunks of 4 elements per thread: the mask, y and p loads of a chunk go out together
-    for (int base = tid; base < cnt; base += 4 * blockDim.x) {
+    for (int base = tid; base < cnt; base += 4 * nthr) {
         bool mv[4];
         float2 yv[4];
         float pv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * blockDim.x;
+            const int idx = base + u * nthr;
             if (idx < cnt) {
-                const int c = idx % cb, i = idx / cb;
-                const size_t g = sbase + (size_t)i * nx + c0 + c;
+                const size_t g = gidx(idx);
                 mv[u] = a.mask[g] != 0;
                 yv[u] = a.y[g];
                 pv[u] = mode == COL_ITER ? a.density[g] : 1.f;
@@ -304,9 +304,9 @@ static __device__ void col_pass_block(const ColArgs& a, int mode, int u_zero, in
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * blockDim.x;
+            const int idx = base + u * nthr;
             if (idx >= cnt) continue;
-            const int i = idx / cb;
+            const int i = idx / CB;
             const float2 uu = U ? cscale(U[idx], a.scale_fwd) : make_float2(0.f, 0.f);
             const bool m = mv[u];
             if (mode == COL_FINAL) {
@@ -314,47 +314,64 @@ static __device__ void col_pass_block(const ColArgs& a, int mode, int u_zero, in
                 continue;
             }
             const float2 z = m ? csub(yv[u], uu) : make_float2(0.f, 0.f);
-            const float w = m ? 1.0f / pv[u] : 0.f;  // P^-1 on Omega, 0 elsewhere
+            const float w = m ? __frcp_rn(pv[u]) : 0.f;  // P^-1 on Omega (1/p rounded once), 0 elsewhere
             const float z2 = z.x * z.x + z.y * z.y;
             const float v = w * ((w - 1.0f) * z2 + sig2);
 #pragma unroll
             for (int t = 0; t < 2 * VDAMP_MAX_LEVELS; ++t)
-                if (t < a.ntypes) q[t] += eys[t * ny + i] * v;
+                if (t < nt) q[t] += eys[t * ny + i] * v;
             X[idx] = cscale(z, w);
         }
     }
-    __syncthreads();
 
     if (mode == COL_ITER) {
-        // tau partials: column kx = c0 + tid % cb is fixed for this thread
-        __shared__ float red[32][VDAMP_MAX_BANDS];
-        const int kx = c0 + tid % cb;
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int b = 0; b < a.B; ++b) {
-            float val = 0.f;
-            if (tid < cnt) {
+        // Per-column sums: lanes of a warp that share a column (lane mod CB) are
+        // combined by shuffles, then the warps by an FP64 sum in warp order;
+        // the partial of band b is sum over the block's columns of S_x(kx) Q_ty(b)(kx).
+        const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
 #pragma unroll
-                for (int t = 0; t < 2 * VDAMP_MAX_LEVELS; ++t)
-                    if (t == a.ty[b]) val = a.ex[a.tx[b] * nx + kx] * q[t];
+        for (int t = 0; t < 2 * VDAMP_MAX_LEVELS; ++t) {
+            if (t < nt) {
+                float v = q[t];
+#pragma unroll
+                for (int o = 16; o >= CB; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane < CB) red[(warp * nt + t) * CB + lane] = v;
             }
-            val = warp_sum(val);
-            if (lane == 0) red[warp][b] = val;
         }
         __syncthreads();
-        const int nw = (blockDim.x + 31) >> 5;
-        if (tid < a.B) {
+        for (int e = tid; e < nt * CB; e += nthr) {
+            const int t = e / CB, c = e & (CB - 1);
             double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += (double)red[w][tid];
-            a.tau_part[((size_t)slice * nparts + cblk) * a.B + tid] = s;
+            for (int w = 0; w < nw; ++w) s += (double)red[(w * nt + t) * CB + c];
+            colq[t * CB + c] = s;
         }
+        __syncthreads();
+        if (tid < a.B) {
+            const int b = tid, t = a.ty[b];
+            const float* exr = a.ex + (size_t)a.tx[b] * nx + c0;
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < CB; ++c) s += (double)exr[c] * colq[t * CB + c];
+            a.tau_part[((size_t)slice * nparts + cblk) * a.B + b] = s;
+        }
+    } else {
+        __syncthreads();
     }
 
     // ---- inverse column transform (line 4: F^H of P^-1 z, or the return line)
     float2* other = (X == A) ? Bf : A;
-    float2* res = fft_stages<true, false>(X, other, a.ax, cb, 0, cb);
-    for (int idx = tid; idx < cnt; idx += blockDim.x) {
-        int c = idx % cb, i = idx / cb;
-        a.out[sbase + (size_t)i * nx + c0 + c] = cscale(res[idx], a.scale_inv);
+    float2* res = fft_stages<true, false, CB>(X, other, a.ax, CB, 0);
+    for (int idx = tid; idx < cnt; idx += nthr) a.out[gidx(idx)] = cscale(res[idx], a.scale_inv);
+}
+
+static __device__ void col_pass_block(const ColArgs& a, int mode, int u_zero, int cblk, int nparts,
+                                      int slice, float2* sm) {
+    switch (a.cb) {
+        case 1: col_pass_block_t<1>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+        case 2: col_pass_block_t<2>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+        case 4: col_pass_block_t<4>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+        case 8: col_pass_block_t<8>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+        default: col_pass_block_t<16>(a, mode, u_zero, cblk, nparts, slice, sm); break;
     }
 }
 

@@ -8,23 +8,24 @@ namespace vdamp {
 __global__ void __launch_bounds__(SURE_THREADS) sure_sort_kernel(const __grid_constant__ SureArgs a) {
     extern __shared__ float sm_keys[];
     cudaGridDependencySynchronize();
-    sure_sort_part(a, a.r, blockIdx.x, blockIdx.y, blockIdx.z, sm_keys);
+    // the finest (largest) subbands first: the long CTAs start in the first wave
+    sure_sort_part(a, a.r, blockIdx.x, a.B - 1 - (int)blockIdx.y, blockIdx.z, sm_keys);
 }
 
 __global__ void __launch_bounds__(SURE_THREADS) sure_search_kernel(const __grid_constant__ SureArgs a) {
     extern __shared__ float sm_keys[];
     cudaGridDependencySynchronize();
-    sure_search_part(a, a.k, blockIdx.x, blockIdx.y, blockIdx.z, sm_keys);
+    sure_search_part(a, a.k, blockIdx.x, a.B - 1 - (int)blockIdx.y, blockIdx.z, sm_keys);
 }
 
 size_t sure_smem(int max_band) { return sure_smem_bytes(max_band); }
 
 cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, cudaStream_t st) {
-    const size_t smem = sure_smem_bytes(max_band);
     cudaError_t e = launch_pdl(sure_sort_kernel, dim3(a.max_parts, a.B, batch),
-                               dim3(SURE_THREADS), smem, st, a);
+                               dim3(SURE_THREADS), sure_smem_bytes(max_band), st, a);
     if (e != cudaSuccess) return e;
-    return launch_pdl(sure_search_kernel, dim3(a.max_parts, a.B, batch), dim3(SURE_THREADS), smem, st, a);
+    return launch_pdl(sure_search_kernel, dim3(a.max_parts, a.B, batch), dim3(SURE_THREADS),
+                      sure_search_smem_bytes(max_band), st, a);
 }
 
 cudaError_t configure_sure(size_t smem_bytes) {

@@ -22,8 +22,9 @@
 //                      subband to finish picks the global minimiser.
 // Sorting: for a >= 0 the IEEE-754 bit pattern is an increasing integer
 // function of a, so buckets made of consecutive ranges of bit patterns
-// ((bits - lo) >> SORT_SHIFT, 1024 buckets per octave over the 16 octaves below
-// the maximum; smaller magnitudes share bucket 0) are exactly ordered.  Each
+// ((bits - lo) >> shift over the 16 octaves below the maximum, 16 to 1024
+// buckets per octave growing with the subband size; smaller magnitudes share
+// bucket 0) are exactly ordered.  Each
 // bucket belongs to the part in which its first position falls, and is
 // sorted in registers by a bitonic network (up to 32 keys) or in shared
 // memory.  A bucket above SORT_MAX_BUCKET keys (ties, or a degenerate subband)
@@ -40,8 +41,7 @@
 
 namespace vdamp {
 
-#define SORT_BUCKETS 16384
-#define SORT_SHIFT 13
+#define SORT_BUCKETS 16384                // most buckets (1024 per octave)
 #define SORT_MAX_BUCKET 96
 #define SORT_MAX_PER_THREAD 32            // largest subband = 32 x 1024 keys
 #define SORT_HIST_WORDS (SORT_BUCKETS + SORT_BUCKETS / 32)
@@ -50,13 +50,25 @@ namespace vdamp {
 #define SURE_MAX_PARTS 8
 #define SURE_KEYS_PER_PART 2048
 
+// Buckets per octave: about nb / 16, between 16 and 1024 (a power of two).
+__host__ __device__ inline int sort_log2_per_octave(int nb) {
+    int l = 4;
+    while (l < 10 && (16 << l) < nb) ++l;
+    return l;
+}
+
 __host__ __device__ inline int sure_parts(int nb, int max_parts) {
     int q = (nb + SURE_KEYS_PER_PART - 1) / SURE_KEYS_PER_PART;
     return q < 1 ? 1 : (q > max_parts ? max_parts : q);
 }
 
-// Shared memory for either step: keys padded to a power of two, then the
-// bucket counters.
+// Shared memory of the search: the keys of a part and the one below it.
+inline size_t sure_search_smem_bytes(int max_band) {
+    return ((size_t)max_band + 4) * sizeof(float);
+}
+
+// Shared memory of the sort (and an upper bound for the search): keys padded
+// to a power of two, then the bucket counters.
 inline size_t sure_smem_bytes(int max_band) {
     int np = 2;
     while (np < max_band) np <<= 1;
@@ -216,27 +228,31 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
         kr[e] = i < nb ? cabs_f(r[i]) : 0.f;
         mx = max(mx, __float_as_uint(kr[e]));
     }
-    for (int i = tid; i < SORT_HIST_WORDS; i += nthr) hist[i] = 0;
+    const int lpo = sort_log2_per_octave(nb);
+    const int nbk = 16 << lpo;          // buckets
+    const int shift = 23 - lpo;         // an octave spans 2^23 bit patterns
+    for (int i = tid; i < nbk + (nbk >> 5); i += nthr) hist[i] = 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     __syncthreads();
     if (lane == 0) atomicMax(&s_max_bits, mx);
     __syncthreads();
-    const unsigned span = (unsigned)SORT_BUCKETS << SORT_SHIFT;
+    const unsigned span = (unsigned)nbk << shift;
     const unsigned lo_bits = s_max_bits + 1u > span ? s_max_bits + 1u - span : 0u;
     auto bucket = [&](float x) -> int {
         const unsigned u = __float_as_uint(x);
-        return u < lo_bits ? 0 : (int)((u - lo_bits) >> SORT_SHIFT);
+        return u < lo_bits ? 0 : (int)((u - lo_bits) >> shift);
     };
 #pragma unroll
     for (int e = 0; e < EMAX; ++e)
         if (tid + e * nthr < nb) atomicAdd(&hist[HIX(bucket(kr[e]))], 1);
     __syncthreads();
-    {   // exclusive scan of the counts; each thread owns SORT_BUCKETS / nthr consecutive buckets
-        const int per = SORT_BUCKETS / nthr;
-        const int b0 = tid * per;
+    {   // exclusive scan of the counts; each thread owns `per` consecutive buckets
+        const int per = nbk >= nthr ? nbk / nthr : 1;
+        const int b0 = min(tid * per, nbk);
+        const int nq = min(per, nbk - b0);   // 0 for threads past the last bucket
         int loc = 0, big = 0;
-        for (int q = 0; q < per; ++q) {
+        for (int q = 0; q < nq; ++q) {
             const int c = hist[HIX(b0 + q)];
             big = max(big, c);
             loc += c;
@@ -262,7 +278,7 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
         __syncthreads();
         int run = inc - loc + (warp > 0 ? wsum[warp - 1] : 0);
         int na = 0, nbq = 0;   // buckets starting below lo_pos / hi_pos
-        for (int q = 0; q < per; ++q) {
+        for (int q = 0; q < nq; ++q) {
             const int c = hist[HIX(b0 + q)];
             hist[HIX(b0 + q)] = run;
             na += run < lo_pos;

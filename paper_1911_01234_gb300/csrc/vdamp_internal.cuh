@@ -89,16 +89,28 @@ struct SrcSpec {
     int B;
 };
 
+// The coefficient a source forms from the stored value v of subband b, whose
+// denoiser parameters are c = coef[slice][b].
+__device__ __forceinline__ float2 src_apply(int mode, float2 v, float4 c) {
+    if (mode == SRC_ZERO) return make_float2(0.f, 0.f);
+    if (mode == SRC_EXPLICIT) return v;
+    float a = cabs_f(v);
+    float sc = a > c.x ? 1.f - c.x / a : 0.f;
+    if (mode == SRC_SOFT) return cscale_rn(v, sc);
+    return cscale_rn(v, __fmul_rn(sc - c.y, c.z));
+}
+
+__device__ __forceinline__ float4 src_coef(const SrcSpec& s, int slice, int b) {
+    return (s.mode == SRC_LINE8 || s.mode == SRC_SOFT) ? s.coef[slice * s.B + b]
+                                                        : make_float4(0.f, 0.f, 1.f, 0.f);
+}
+
 __device__ __forceinline__ float2 src_value(const SrcSpec& s, int slice, size_t N, size_t idx,
                                             int b) {
     if (s.mode == SRC_ZERO) return make_float2(0.f, 0.f);
     float2 v = s.r[(size_t)slice * N + idx];
     if (s.mode == SRC_EXPLICIT) return v;
-    float4 c = s.coef[slice * s.B + b];
-    float a = cabs_f(v);
-    float sc = a > c.x ? 1.f - c.x / a : 0.f;
-    if (s.mode == SRC_SOFT) return cscale_rn(v, sc);
-    return cscale_rn(v, __fmul_rn(sc - c.y, c.z));
+    return src_apply(s.mode, v, s.coef[slice * s.B + b]);
 }
 
 // Column-pass modes of the fused k-space kernel.
