@@ -232,6 +232,7 @@ def run_batched(args, vb, torch, flush_buf, stream):
     plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
     if args.path != "auto":
         vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 1 if args.path == "fused" else 0)
+    tuning = None if args.no_autotune else plan.autotune(nb, trials=3, stream=stream.cuda_stream)
     K = wl.iters
     x_hat = torch.empty((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
     tau = torch.empty((nb, K, plan.B), dtype=torch.float64, device="cuda")
@@ -271,12 +272,64 @@ def run_batched(args, vb, torch, flush_buf, stream):
     plan.close()
     return {"workload": wl.name, "slices": nb, "iters": K, "steps": steps,
             "value": nb * K * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "tuning": tuning,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": byt / avg_s / 1e9,
                          "peak": hbm, "peak_source": src, "unit": "GB/s",
                          "frac": byt / avg_s / 1e9 / hbm, "avg_launch_us": avg_s * 1e6,
                          "algorithmic_bytes_per_launch": byt,
                          "time_share": {k: round(v[0] / sum(x[0] for x in kt.values()), 4)
                                         for k, v in kt.items()}}}
+
+
+def run_mixed(args, vb, torch, flush_buf, stream):
+    """Mixed-size batch: 32 slices each of 128x128, 256x256 and 384x320 (db4 s=4,
+    per-slice R ~ U[3, 8] and SNR ~ U[25, 40] dB, 30 iterations) as one grouped
+    graph launch, next to the same groups solved one after another."""
+    wls = synth.mixed_batch_workloads()
+    groups, plans, tunings = [], [], {}
+    for wl in wls:
+        probs = [synth.make_problem(wl, i) for i in range(wl.batch)]
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
+        plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=wl.batch)
+        if not args.no_autotune:
+            tunings[f"{wl.ny}x{wl.nx}"] = plan.autotune(wl.batch, trials=3, stream=stream.cuda_stream)
+        plans.append(plan)
+        groups.append((plan, dev([q.y for q in probs]), dev([q.mask for q in probs]),
+                       dev([q.density for q in probs]), [q.sigma for q in probs]))
+    K = wls[0].iters
+    slices = sum(wl.batch for wl in wls)
+
+    def timed(fn, steps):
+        for i in range(2):
+            flush_buf.fill_(float(i))
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for i in range(steps):
+            flush_buf.fill_(float(i))
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    steps = args.batched_steps
+    ms_grouped = timed(lambda: vb.solve_groups(groups, K, stream=stream.cuda_stream), steps)
+    ms_serial = timed(lambda: [g[0].solve(*g[1:], K, stream=stream.cuda_stream) for g in groups],
+                      steps)
+    for plan in plans:
+        if vb.vdamp_device_status(plan.handle)[0] != vb.VDAMP_OK:
+            raise RuntimeError("mixed solve reported a non-finite tau or alpha")
+        plan.close()
+    return {"workload": "batched 96 mixed slices (32 x 128x128, 32 x 256x256, 32 x 384x320) "
+                        "db4 s=4 R~U[3,8] SNR~U[25,40] K=30",
+            "slices": slices, "iters": K, "steps": steps,
+            "value": slices * K * steps / (ms_grouped / 1e3), "unit": UNIT,
+            "ms_per_step": ms_grouped / steps,
+            "one_group_after_another": {"value": slices * K * steps / (ms_serial / 1e3),
+                                        "ms_per_step": ms_serial / steps},
+            "tuning": tunings or None}
 
 
 def run_gpu(args):
@@ -312,6 +365,7 @@ def run_gpu(args):
     tau = torch.empty((1, K, plan.B), dtype=torch.float64, device="cuda")
     thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
     stream = torch.cuda.current_stream()
+    tuning = None if args.no_autotune else plan.autotune(1, trials=5, stream=stream.cuda_stream)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -410,7 +464,7 @@ def run_gpu(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic (seeded ellipse phantom, polynomial VD mask)",
-                "config": dict(config_block(1, world), path=args.path),
+                "config": dict(config_block(1, world), path=args.path, tuning=tuning),
                 "clocks": ClockSampler.summarize(rows),
                 "gpu_launches": launches_per_step * args.steps,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -419,6 +473,7 @@ def run_gpu(args):
                 "wall_s_timed": wall}
         if not args.no_batched:
             line["batched"] = run_batched(args, vb, torch, flush_buf, stream)
+            line["mixed"] = run_mixed(args, vb, torch, flush_buf, stream)
         if not args.no_cpu_baseline:
             it, el = OracleRunner().run(args.cpu_seconds)
             line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -444,6 +499,8 @@ def main():
                     help="skip the 256 x 320x320 batched measurement")
     ap.add_argument("--batched-slices", type=int, default=256)
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plans' default launch shapes")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "steps"],
                     help="solve as one persistent cluster launch, or one kernel per step")
     args = ap.parse_args()

@@ -119,6 +119,66 @@ vdamp_status vdamp_kernel_times(vdamp_plan* plan, double* ms, int* counts);
 int vdamp_last_launch_count(const vdamp_plan* plan);
 
 /*
+ * Launch shapes of a plan ("tuning"), int[VDAMP_TUNING_LEN]:
+ *   [0] columns per CTA of the column pass: 2, 4, 8 or 16 (dividing nx)
+ *   [1] rows per CTA of the row pass: 1, 2, 4 or 8
+ *   [2] synthesis (Psi^H) tile side in pixels: 16, 32 or 64
+ *   [3] analysis (Psi) tile side in coefficients: 16 or 32
+ *   [4], [5] radix plan of the transform along y and x: 0 = radix 8 first,
+ *            1 = radix 4 only, 2 = radix 8 with the radices 3 and 5 first
+ * Every tuning computes the same method; tunings differ in FP32 summation
+ * order only (the tau partial sums depend on [0], the DFT on [4], [5]).
+ * get copies the current tuning out; set validates and applies one
+ * (VDAMP_EINVAL for an unsupported value, nothing changed) and drops the
+ * plan's cached graphs.
+ */
+#define VDAMP_TUNING_LEN 6
+vdamp_status vdamp_plan_get_tuning(const vdamp_plan* plan, int* tuning);
+vdamp_status vdamp_plan_set_tuning(vdamp_plan* plan, const int* tuning);
+
+/*
+ * Autotuner: times one iteration (lines 3-8) of `batch` synthetic slices
+ * `trials` times per candidate on `stream` and keeps, one parameter after
+ * another (coordinate descent over the tuning above, starting from the
+ * current one), the fastest shape.  Blocks until done; allocates and frees
+ * its own temporary device buffers (about 6 batch ny nx complex values).
+ * Writes the chosen tuning to `tuning` (int[VDAMP_TUNING_LEN]) if not NULL.
+ */
+vdamp_status vdamp_plan_autotune(vdamp_plan* plan, int batch, int trials, int* tuning,
+                                 void* stream);
+
+/*
+ * One group of same-size slices for vdamp_solve_groups: the arguments of
+ * vdamp_solve for a cold start (r_tilde0 = NULL), without the optional
+ * outputs.  Each group has its own plan (the plan's size fixes the slices').
+ */
+typedef struct {
+    vdamp_plan* plan;
+    int batch;
+    const float* y;          /* device [batch][ny][nx] complex64 */
+    const uint8_t* mask;     /* device [batch][ny][nx] */
+    const float* density;    /* device [batch][ny][nx] */
+    const float* sigma;      /* host [batch] */
+    int iters;
+    float* x_hat;            /* device [batch][ny][nx] complex64 out */
+    double* tau;             /* device [batch][iters][B] out */
+    double* thr;
+    double* alpha;
+} vdamp_group;
+
+/*
+ * Mixed-size batched VDAMP: solves `count` groups (1 <= count <= 64, each
+ * with a distinct plan) as ONE CUDA graph launch on `stream`, in which every
+ * group's kernels run on a branch of their own, so that groups of different
+ * slice sizes overlap on the GPU.  The graph is cached per argument set (the
+ * sigma values are uploaded before each launch).  Results are identical to
+ * solving each group with vdamp_solve.  Errors met inside kernels are
+ * recorded per plan (vdamp_device_status).  With graphs off on the first
+ * plan, or kernel timing on any, the groups run one after another.
+ */
+vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count, void* stream);
+
+/*
  * VDAMP solve, Algorithm 1 lines 1-10 with the SURE soft threshold of Sec. 3,
  * on `batch` independent slices (1 <= batch <= max_batch).
  *   y         device  [batch][ny][nx] complex64  measurements (ignored off the mask)

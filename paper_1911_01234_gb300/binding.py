@@ -54,7 +54,21 @@ _SIGS = {
     "vdamp_subband_spectra": (_I, [_I, _I, _I, _D]),
     "vdamp_kernel_times": (_I, [_P, _D, ctypes.POINTER(_I)]),
     "vdamp_tau_estimate_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P, ctypes.c_float, _P, _P]),
+    "vdamp_plan_get_tuning": (_I, [_P, ctypes.POINTER(_I)]),
+    "vdamp_plan_set_tuning": (_I, [_P, ctypes.POINTER(_I)]),
+    "vdamp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), _P]),
+    "vdamp_solve_groups": (_I, [_P, _I, _P]),
 }
+
+VDAMP_TUNING_LEN = 6
+TUNING_FIELDS = ("col_block", "rows_per_cta", "idwt_tile", "dwt_tile", "radix_y", "radix_x")
+
+
+class vdamp_group(ctypes.Structure):
+    """struct vdamp_group of include/vdamp.h."""
+    _fields_ = [("plan", _P), ("batch", _I), ("y", _P), ("mask", _P), ("density", _P),
+                ("sigma", ctypes.POINTER(ctypes.c_float)), ("iters", _I), ("x_hat", _P),
+                ("tau", _P), ("thr", _P), ("alpha", _P)]
 
 _lib: Optional[ctypes.CDLL] = None
 
@@ -233,6 +247,39 @@ def vdamp_subband_spectra(wavelet, levels, n):
     return out.reshape(2 * levels, n)
 
 
+def vdamp_plan_get_tuning(plan) -> list:
+    t = (_I * VDAMP_TUNING_LEN)()
+    check(load().vdamp_plan_get_tuning(plan, t), "vdamp_plan_get_tuning")
+    return list(t)
+
+
+def vdamp_plan_set_tuning(plan, tuning) -> None:
+    t = (_I * VDAMP_TUNING_LEN)(*[int(v) for v in tuning])
+    check(load().vdamp_plan_set_tuning(plan, t), "vdamp_plan_set_tuning")
+
+
+def vdamp_plan_autotune(plan, batch, trials=5, stream=None) -> list:
+    t = (_I * VDAMP_TUNING_LEN)()
+    check(load().vdamp_plan_autotune(plan, batch, trials, t, _stream(stream)),
+          "vdamp_plan_autotune")
+    return list(t)
+
+
+def vdamp_solve_groups(groups, stream=None) -> None:
+    """groups: list of dicts with the vdamp_group fields (tensors for device arrays)."""
+    arr = (vdamp_group * len(groups))()
+    keep = []
+    for i, g in enumerate(groups):
+        sig = _sigma_array(g["sigma"], g["batch"])
+        keep.append(sig)
+        arr[i] = vdamp_group(g["plan"], g["batch"], _ptr(g["y"]), _ptr(g["mask"]),
+                             _ptr(g["density"]), ctypes.cast(sig, ctypes.POINTER(ctypes.c_float)),
+                             g["iters"], _ptr(g["x_hat"]), _ptr(g["tau"]), _ptr(g["thr"]),
+                             _ptr(g["alpha"]))
+    check(load().vdamp_solve_groups(ctypes.cast(arr, _P), len(groups), _stream(stream)),
+          "vdamp_solve_groups")
+
+
 # --------------------------------------------------------- convenience ---
 
 class Plan:
@@ -272,3 +319,33 @@ class Plan:
                     alpha, rt, xi, stream)
         return {"x_hat": x_hat, "tau": tau, "thr": thr, "alpha": alpha, "r_tilde": rt,
                 "x_hat_iters": xi}
+
+    def tuning(self):
+        return dict(zip(TUNING_FIELDS, vdamp_plan_get_tuning(self.handle)))
+
+    def set_tuning(self, tuning):
+        vdamp_plan_set_tuning(self.handle, [tuning[k] for k in TUNING_FIELDS]
+                              if isinstance(tuning, dict) else tuning)
+
+    def autotune(self, batch=None, trials=5, stream=None):
+        vdamp_plan_autotune(self.handle, batch or self.max_batch, trials, stream)
+        return self.tuning()
+
+
+def solve_groups(groups, iters, stream=None):
+    """Mixed-size batched solve: groups = [(plan, y, mask, density, sigma), ...] with
+    torch device tensors [batch][ny][nx]; returns one output dict per group."""
+    import torch
+    descs, outs = [], []
+    for plan, y, mask, density, sigma in groups:
+        batch = y.shape[0]
+        dev = y.device
+        o = {"x_hat": torch.empty((batch, plan.ny, plan.nx), dtype=torch.complex64, device=dev),
+             "tau": torch.empty((batch, iters, plan.B), dtype=torch.float64, device=dev)}
+        o["thr"] = torch.empty_like(o["tau"])
+        o["alpha"] = torch.empty_like(o["tau"])
+        outs.append(o)
+        descs.append({"plan": plan.handle, "batch": batch, "y": y, "mask": mask,
+                      "density": density, "sigma": sigma, "iters": iters, **o})
+    vdamp_solve_groups(descs, stream)
+    return outs

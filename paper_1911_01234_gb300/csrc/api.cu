@@ -130,20 +130,37 @@ static void spectra(const double* h, int L, int levels, int n, double* out) {
 }
 
 // ----------------------------------------------------------- fft plan ---
-static bool fft_radices(int n, int* radix, int* nst) {
+// Radix plan of an n-point transform (n = 2^a 3^b 5^c).  Variant 0: radix 8
+// first (then 4, 4 / 4 / 2), then 3s and 5s; variant 1: radix 4 (one 2 for an
+// odd power of two), then 3s and 5s; variant 2: variant 0 with the odd radices
+// first.
+static bool fft_radices(int n, int* radix, int* nst, int variant = 0) {
     int m = n, a = 0;
     while (m % 2 == 0) { m /= 2; ++a; }
+    int p2[VDAMP_MAX_STAGES], n2 = 0;
+    if (variant == 1) {
+        for (int i = 0; i < a / 2; ++i) p2[n2++] = 4;
+        if (a & 1) p2[n2++] = 2;
+    } else {
+        int e8 = a / 3, rem = a % 3;
+        if (rem == 1 && e8 > 0) { --e8; rem = 4; }
+        for (int i = 0; i < e8; ++i) p2[n2++] = 8;
+        if (rem == 4) { p2[n2++] = 4; p2[n2++] = 4; }
+        else if (rem == 2) p2[n2++] = 4;
+        else if (rem == 1) p2[n2++] = 2;
+    }
+    int odd[VDAMP_MAX_STAGES], no = 0;
+    while (m % 3 == 0) { odd[no++] = 3; m /= 3; }
+    while (m % 5 == 0) { odd[no++] = 5; m /= 5; }
+    if (m != 1 || n2 + no > VDAMP_MAX_STAGES) return false;
     int s = 0;
-    int e8 = a / 3, rem = a % 3;
-    if (rem == 1 && e8 > 0) { --e8; rem = 4; }
-    for (int i = 0; i < e8; ++i) radix[s++] = 8;
-    if (rem == 4) { radix[s++] = 4; radix[s++] = 4; }
-    else if (rem == 2) radix[s++] = 4;
-    else if (rem == 1) radix[s++] = 2;
-    while (m % 3 == 0) { radix[s++] = 3; m /= 3; }
-    while (m % 5 == 0) { radix[s++] = 5; m /= 5; }
+    if (variant == 2)
+        for (int i = 0; i < no; ++i) radix[s++] = odd[i];
+    for (int i = 0; i < n2; ++i) radix[s++] = p2[i];
+    if (variant != 2)
+        for (int i = 0; i < no; ++i) radix[s++] = odd[i];
     *nst = s;
-    return m == 1 && s <= VDAMP_MAX_STAGES;
+    return true;
 }
 
 // -------------------------------------------------------------- plan ---
@@ -181,6 +198,9 @@ struct vdamp_plan {
     int off[VDAMP_MAX_BANDS + 1];
     int ty[VDAMP_MAX_BANDS], tx[VDAMP_MAX_BANDS];
     int cb, nparts, rpc;
+    int idwt_to = 32, dwt_to = 16;     // wavelet tile sides
+    size_t smem_col = 0, smem_rows = 0, smem_dwt = 0;  // attributes raised for the tuner's choices
+    int radix_var[2] = {0, 0};         // radix plan variant along y, x
     int num_sms = 152;
     float* ey = nullptr;
     float* ex = nullptr;
@@ -223,8 +243,11 @@ struct vdamp_plan {
     std::vector<GraphEntry> graphs;
 };
 
+static void purge_group_graphs(const vdamp_plan* p);
+
 static void plan_free(vdamp_plan* p) {
     if (!p) return;
+    purge_group_graphs(p);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     for (auto& e : p->ev_pool) cudaEventDestroy(e);
     void* bufs[] = {p->ey,       p->ex,      p->tw_y,    p->tw_x,    p->u,      p->kbuf,
@@ -362,7 +385,7 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
         sm = std::max(sm, vdamp::col_pass_smem_bytes(ny, p->fused_cb, 2 * levels));
         p->fused_smem = sm;
     }
-    const int nparts_alloc = std::max(p->nparts, nx / p->fused_cb);
+    const int nparts_alloc = std::max(nx / 2, nx / p->fused_cb);  // any column block >= 2 columns
 
     p->axy.n = ny;
     p->axx.n = nx;
@@ -422,8 +445,21 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(cudaMemset(p->status, 0, 2 * sizeof(int)));
     A(cudaMemset(p->counter, 0, MB * p->B * sizeof(unsigned)));  // each search returns it to 0
     A(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
-    A(vdamp::configure_col_pass(vdamp::col_pass_smem(ny, cb, nt)));
-    A(vdamp::configure_fft_rows(2 * (size_t)p->rpc * nx * sizeof(float2)));
+    // shared-memory attributes large enough for every tile choice the tuner may make
+    p->smem_col = vdamp::col_pass_smem(ny, cb, nt);
+    for (int c2 = 2; c2 <= 16; c2 *= 2) {
+        const size_t sm = vdamp::col_pass_smem(ny, c2, nt);
+        if (nx % c2 == 0 && sm <= 200 * 1024) p->smem_col = std::max(p->smem_col, sm);
+    }
+    p->smem_rows = 2 * (size_t)p->rpc * nx * sizeof(float2);
+    for (int r2 = 1; r2 <= 8; r2 *= 2) {
+        const size_t sm = 2 * (size_t)r2 * nx * sizeof(float2);
+        if (sm <= 128 * 1024) p->smem_rows = std::max(p->smem_rows, sm);
+    }
+    p->smem_dwt = std::max(vdamp::idwt_tile_smem(64, L), vdamp::dwt_tile_smem(32, L));
+    A(vdamp::configure_col_pass(p->smem_col));
+    A(vdamp::configure_fft_rows(p->smem_rows));
+    A(vdamp::configure_dwt(p->smem_dwt));
     A(vdamp::configure_sure(vdamp::sure_smem(max_band)));
     if (e != cudaSuccess) {
         plan_free(p);
@@ -553,6 +589,7 @@ void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
         a.band[3] = bh + 2;
         a.src = src;
         a.f = p->filt;
+        a.to = p->idwt_to;
         c.pre();
         c.chk(vdamp::launch_idwt_level(a, c.batch, c.st), VDAMP_KERNEL_IDWT);
         ll_in = a.out;
@@ -587,6 +624,7 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
         a.band[3] = bh + 2;
         a.src = src;
         a.f = p->filt;
+        a.to = p->dwt_to;
         c.pre();
         c.chk(vdamp::launch_dwt_level(a, c.batch, c.st), VDAMP_KERNEL_DWT);
         in = a.ll_out;
@@ -1131,5 +1169,320 @@ extern "C" vdamp_status vdamp_kernel_times(vdamp_plan* p, double* ms, int* count
     }
     p->ev_used.clear();
     p->ev_next = 0;
+    return VDAMP_OK;
+}
+
+// ------------------------------------------------------------- tuning ---
+namespace {
+
+bool tuning_valid(const vdamp_plan* p, const int* t) {
+    const int cb = t[0], rpc = t[1], ito = t[2], dto = t[3];
+    if (cb < 2 || cb > 16 || (cb & (cb - 1)) || p->nx % cb) return false;
+    if (vdamp::col_pass_smem(p->ny, cb, 2 * p->levels) > p->smem_col) return false;
+    if (rpc < 1 || rpc > 8 || 2 * (size_t)rpc * p->nx * sizeof(float2) > p->smem_rows) return false;
+    if (ito != 16 && ito != 32 && ito != 64) return false;
+    if (dto != 16 && dto != 32) return false;
+    if (vdamp::idwt_tile_smem(ito, p->filt.L) > p->smem_dwt ||
+        vdamp::dwt_tile_smem(dto, p->filt.L) > p->smem_dwt)
+        return false;
+    int r[VDAMP_MAX_STAGES], ns = 0;
+    for (int ax = 0; ax < 2; ++ax)
+        if (t[4 + ax] < 0 || t[4 + ax] > 2 || !fft_radices(ax ? p->nx : p->ny, r, &ns, t[4 + ax]))
+            return false;
+    return true;
+}
+
+void get_tuning(const vdamp_plan* p, int* t) {
+    t[0] = p->cb;
+    t[1] = p->rpc;
+    t[2] = p->idwt_to;
+    t[3] = p->dwt_to;
+    t[4] = p->radix_var[0];
+    t[5] = p->radix_var[1];
+}
+
+void apply_tuning(vdamp_plan* p, const int* t) {
+    p->cb = t[0];
+    p->nparts = p->nx / p->cb;
+    p->rpc = t[1];
+    p->idwt_to = t[2];
+    p->dwt_to = t[3];
+    p->radix_var[0] = t[4];
+    p->radix_var[1] = t[5];
+    fft_radices(p->ny, p->axy.radix, &p->axy.nstages, t[4]);
+    fft_radices(p->nx, p->axx.radix, &p->axx.nstages, t[5]);
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);  // they hold the old launch shapes
+    p->graphs.clear();
+    purge_group_graphs(p);
+}
+
+// Synthetic problem for timing trials: pseudo-random measurements on a
+// 30% mask with p = 0.3 and a pseudo-random r~ (a hash of the index).
+__global__ void tune_fill_kernel(float2* y, uint8_t* m, float* d, float2* rt, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 2654435761u ^ (uint32_t)(i >> 32) * 40503u;
+        h ^= h >> 15;
+        h *= 2246822519u;
+        h ^= h >> 13;
+        const float u0 = (float)(h & 0xffff) / 65536.f, u1 = (float)(h >> 16) / 65536.f;
+        m[i] = u0 < 0.3f;
+        d[i] = 0.3f;
+        y[i] = make_float2(u0 - 0.5f, u1 - 0.5f);
+        rt[i] = make_float2(0.1f * (u1 - 0.5f), 0.1f * (u0 - 0.5f));
+    }
+}
+
+}  // namespace
+
+extern "C" vdamp_status vdamp_plan_get_tuning(const vdamp_plan* p, int* tuning) {
+    if (!p || !tuning) return fail(VDAMP_EINVAL, "vdamp_plan_get_tuning: NULL");
+    get_tuning(p, tuning);
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_plan_set_tuning(vdamp_plan* p, const int* tuning) {
+    if (!p || !tuning) return fail(VDAMP_EINVAL, "vdamp_plan_set_tuning: NULL");
+    if (!tuning_valid(p, tuning)) return fail(VDAMP_EINVAL, "vdamp_plan_set_tuning: invalid tuning");
+    apply_tuning(p, tuning);
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_plan_autotune(vdamp_plan* p, int batch, int trials, int* tuning,
+                                            void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_plan_autotune");
+    if (st != VDAMP_OK) return st;
+    if (trials < 1 || trials > 1000) return fail(VDAMP_EINVAL, "vdamp_plan_autotune: trials");
+    cudaStream_t us = (cudaStream_t)stream;
+    const size_t n = (size_t)batch * p->N, nb = (size_t)batch * p->B;
+    float2 *y = nullptr, *rt = nullptr, *r = nullptr, *rn = nullptr;
+    uint8_t* m = nullptr;
+    float* d = nullptr;
+    double* outs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+    };
+    A(cudaMalloc(&y, n * sizeof(float2)));
+    A(cudaMalloc(&rt, n * sizeof(float2)));
+    A(cudaMalloc(&r, n * sizeof(float2)));
+    A(cudaMalloc(&rn, n * sizeof(float2)));
+    A(cudaMalloc(&m, n));
+    A(cudaMalloc(&d, n * sizeof(float)));
+    A(cudaMalloc(&outs, 3 * nb * sizeof(double)));
+    A(cudaEventCreate(&e0));
+    A(cudaEventCreate(&e1));
+    auto cleanup = [&]() {
+        cudaFree(y); cudaFree(rt); cudaFree(r); cudaFree(rn); cudaFree(m); cudaFree(d);
+        cudaFree(outs);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(VDAMP_ENOMEM, std::string("vdamp_plan_autotune: ") + cudaGetErrorString(e));
+    }
+    tune_fill_kernel<<<std::min<size_t>((n + 255) / 256, 4096), 256, 0, us>>>(y, m, d, rt, n);
+    std::vector<float> sig(batch, 0.01f);
+    int launches = 0;
+    if ((st = set_sigma(p, sig.data(), batch, us, &launches)) != VDAMP_OK) {
+        cleanup();
+        return st;
+    }
+    // one timing trial: an iteration (lines 3-8) `trials` times after two warm-ups
+    auto trial = [&](const int* t, float* ms) -> cudaError_t {
+        apply_tuning(p, t);
+        Ctx c{p, batch, us};
+        const SrcSpec src = make_src(p, vdamp::SRC_EXPLICIT, rt);
+        auto once = [&]() {
+            enq_psi_h(c, src, p->u);
+            enq_kspace_iter(c, false, y, m, d);
+            enq_psi(c, p->u, r, src);
+            enq_sure(c, r, 1, 0, outs, outs + nb, outs + 2 * nb);
+            enq_line8(c, r, rn);
+        };
+        once();
+        once();
+        cudaEventRecord(e0, us);
+        for (int i = 0; i < trials; ++i) once();
+        cudaEventRecord(e1, us);
+        cudaError_t x = cudaEventSynchronize(e1);
+        if (c.err != cudaSuccess) return c.err;
+        if (x != cudaSuccess) return x;
+        return cudaEventElapsedTime(ms, e0, e1);
+    };
+    // coordinate descent over (cb, rpc, idwt tile, dwt tile, radix plan y, radix plan x)
+    static const int choices[6][4] = {{2, 4, 8, 16}, {1, 2, 4, 8}, {16, 32, 64, 0},
+                                      {16, 32, 0, 0}, {0, 1, 2, -1}, {0, 1, 2, -1}};
+    int best[6];
+    get_tuning(p, best);
+    float best_ms = 0.f;
+    A(trial(best, &best_ms));
+    for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
+        for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+            int cand[6];
+            std::memcpy(cand, best, sizeof(cand));
+            cand[q] = choices[q][c];
+            if (cand[q] == best[q] || !tuning_valid(p, cand)) continue;
+            float ms = 0.f;
+            A(trial(cand, &ms));
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                std::memcpy(best, cand, sizeof(best));
+            }
+        }
+    }
+    apply_tuning(p, best);
+    cleanup();
+    if (e != cudaSuccess)
+        return fail(VDAMP_ECUDA, std::string("vdamp_plan_autotune: ") + cudaGetErrorString(e));
+    if (tuning) get_tuning(p, tuning);
+    return VDAMP_OK;
+}
+
+// ------------------------------------------------------- grouped solve ---
+namespace {
+
+struct GroupGraph {
+    std::vector<vdamp_group> key;
+    cudaGraphExec_t exec;
+    std::vector<int> launches;
+};
+std::mutex g_group_mu;
+std::vector<GroupGraph> g_group_graphs;
+
+bool same_group(const vdamp_group& a, const vdamp_group& b) {
+    return a.plan == b.plan && a.batch == b.batch && a.iters == b.iters && a.y == b.y &&
+           a.mask == b.mask && a.density == b.density && a.x_hat == b.x_hat && a.tau == b.tau &&
+           a.thr == b.thr && a.alpha == b.alpha;
+}
+
+SolveArgs group_args(const vdamp_group& g) {
+    SolveArgs s;
+    s.y = (const float2*)g.y;
+    s.mask = g.mask;
+    s.density = g.density;
+    s.iters = g.iters;
+    s.r_tilde0 = nullptr;
+    s.x_hat = (float2*)g.x_hat;
+    s.tau = g.tau;
+    s.thr = g.thr;
+    s.alpha = g.alpha;
+    s.r_tilde_out = nullptr;
+    s.x_hat_iters = nullptr;
+    return s;
+}
+
+}  // namespace
+
+static void purge_group_graphs(const vdamp_plan* p) {
+    std::lock_guard<std::mutex> lk(g_group_mu);
+    for (size_t i = 0; i < g_group_graphs.size();) {
+        bool uses = false;
+        for (auto& g : g_group_graphs[i].key) uses = uses || g.plan == p;
+        if (uses) {
+            cudaGraphExecDestroy(g_group_graphs[i].exec);
+            g_group_graphs.erase(g_group_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+extern "C" vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count, void* stream) {
+    if (!groups || count < 1 || count > 64)
+        return fail(VDAMP_EINVAL, "vdamp_solve_groups: count outside [1, 64]");
+    for (int i = 0; i < count; ++i) {
+        const vdamp_group& g = groups[i];
+        vdamp_status st = check_common(g.plan, g.batch, "vdamp_solve_groups");
+        if (st != VDAMP_OK) return st;
+        if (!g.y || !g.mask || !g.density || !g.x_hat || !g.tau || !g.thr || !g.alpha)
+            return fail(VDAMP_EINVAL, "vdamp_solve_groups: a required pointer is NULL");
+        if (g.iters < 1) return fail(VDAMP_EINVAL, "vdamp_solve_groups: iters must be >= 1");
+        if ((st = check_sigma(g.sigma, g.batch, "vdamp_solve_groups")) != VDAMP_OK) return st;
+        for (int j = 0; j < i; ++j)
+            if (groups[j].plan == g.plan)
+                return fail(VDAMP_EINVAL, "vdamp_solve_groups: a plan appears in two groups");
+    }
+    cudaStream_t us = (cudaStream_t)stream;
+    std::vector<int> launches(count, 0);
+    for (int i = 0; i < count; ++i) {
+        vdamp_status st = set_sigma(groups[i].plan, groups[i].sigma, groups[i].batch, us,
+                                    &launches[i]);
+        if (st != VDAMP_OK) return st;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(us, &cs));
+    vdamp_plan* p0 = groups[0].plan;
+    bool direct = !p0->use_graph || cs != cudaStreamCaptureStatusNone;
+    for (int i = 0; i < count; ++i) direct = direct || groups[i].plan->timing || groups[i].plan->use_fused;
+    if (direct) {   // one group after another on the caller's stream
+        for (int i = 0; i < count; ++i) {
+            Ctx c{groups[i].plan, groups[i].batch, us};
+            c.timed = groups[i].plan->timing != 0;
+            enq_solve(c, group_args(groups[i]));
+            groups[i].plan->last_launches = launches[i] + c.launches;
+            if (c.err != cudaSuccess)
+                return fail(VDAMP_ECUDA, std::string("vdamp_solve_groups: ") +
+                                             cudaGetErrorString(c.err));
+        }
+        return VDAMP_OK;
+    }
+    std::lock_guard<std::mutex> lk(g_group_mu);
+    GroupGraph* hit = nullptr;
+    for (auto& gg : g_group_graphs) {
+        if ((int)gg.key.size() != count) continue;
+        bool same = true;
+        for (int i = 0; i < count && same; ++i) same = same_group(gg.key[i], groups[i]);
+        if (same) hit = &gg;
+    }
+    if (!hit) {
+        // One graph: a fork from the first plan's capture stream into every
+        // group's own stream, each group's solve there, and a join back.
+        std::vector<cudaEvent_t> ev(count + 1, nullptr);
+        cudaError_t e = cudaSuccess;
+        for (auto& x : ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+        std::vector<int> lc(count, 0);
+        cudaGraph_t graph = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(p0->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t ce = cudaEventRecord(ev[count], p0->cap);
+            for (int i = 1; i < count && ce == cudaSuccess; ++i)
+                ce = cudaStreamWaitEvent(groups[i].plan->cap, ev[count], 0);
+            for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+                Ctx c{groups[i].plan, groups[i].batch, groups[i].plan->cap};
+                enq_solve(c, group_args(groups[i]));
+                lc[i] = c.launches;
+                ce = c.err;
+                if (ce == cudaSuccess && i > 0) ce = cudaEventRecord(ev[i], groups[i].plan->cap);
+            }
+            for (int i = 1; i < count && ce == cudaSuccess; ++i)
+                ce = cudaStreamWaitEvent(p0->cap, ev[i], 0);
+            cudaError_t ee = cudaStreamEndCapture(p0->cap, &graph);
+            e = ce != cudaSuccess ? ce : ee;
+        }
+        for (auto& x : ev)
+            if (x) cudaEventDestroy(x);
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return fail(VDAMP_ECUDA, std::string("vdamp_solve_groups capture: ") +
+                                         cudaGetErrorString(e));
+        if (g_group_graphs.size() >= 16) {
+            cudaGraphExecDestroy(g_group_graphs.front().exec);
+            g_group_graphs.erase(g_group_graphs.begin());
+        }
+        GroupGraph gg;
+        gg.key.assign(groups, groups + count);
+        gg.exec = exec;
+        gg.launches = lc;
+        g_group_graphs.push_back(gg);
+        hit = &g_group_graphs.back();
+    }
+    CUDA_TRY(cudaGraphLaunch(hit->exec, us));
+    for (int i = 0; i < count; ++i) groups[i].plan->last_launches = launches[i] + hit->launches[i];
     return VDAMP_OK;
 }

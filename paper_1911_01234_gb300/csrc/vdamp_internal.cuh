@@ -239,6 +239,7 @@ cudaError_t launch_line8(const Line8Args& a, int batch, cudaStream_t st);
 cudaError_t configure_col_pass(size_t smem_bytes);
 cudaError_t configure_fft_rows(size_t smem_bytes);
 cudaError_t configure_sure(size_t smem_bytes);
+cudaError_t configure_dwt(size_t smem_bytes);
 void set_last_error(const char* msg);  // text returned by vdamp_last_error()
 
 }  // namespace vdamp

@@ -1,0 +1,182 @@
+"""Mixed-size batched solve, launch-shape tuning and the autotuner (CUDA path).
+
+* vdamp_solve_groups runs several plans' solves as one graph launch; its
+  results must equal the per-plan vdamp_solve results bit for bit (same
+  kernels, same arguments, separate workspaces).
+* Sampled slices of a mixed batch (sizes of the 96-slice mixed workload:
+  128x128, 256x256, 384x320, db4 s=4, per-slice R and SNR) are checked against
+  the FP64 oracle with the solve tolerances (x_hat and the tau vector within
+  1e-4 relative L2, thresholds within 1e-3 or a certified SURE tie).
+* Every tuning computes the same method: each launch shape is checked against
+  the oracle, and unsupported shapes are refused.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import vdamp_oracle as O
+from paper_1911_01234_gb300 import binding as vb
+from paper_1911_01234_gb300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    vb.load()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _stack(prs, key):
+    return torch.from_numpy(np.ascontiguousarray(np.stack([getattr(p, key) for p in prs]))).cuda()
+
+
+def _groups(counts):
+    out = []
+    for wl, n in zip(synth.mixed_batch_workloads(), counts):
+        prs = [synth.make_problem(wl, i) for i in range(n)]
+        plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=n)
+        out.append((wl, prs, plan))
+    return out
+
+
+def test_groups_equal_separate_solves():
+    iters = 6
+    groups = _groups((3, 2, 2))
+    args = [(plan, _stack(prs, "y"), _stack(prs, "mask"), _stack(prs, "density"),
+             [p.sigma for p in prs]) for _, prs, plan in groups]
+    outs = vb.solve_groups(args, iters)
+    again = vb.solve_groups(args, iters)   # replay of the cached graph
+    torch.cuda.synchronize()
+    for (wl, prs, plan), (_, y, m, d, sig), o, o2 in zip(groups, args, outs, again):
+        ref = plan.solve(y, m, d, sig, iters)
+        torch.cuda.synchronize()
+        assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+        for k in ("x_hat", "tau", "thr", "alpha"):
+            assert torch.equal(o[k], ref[k]), (wl.name, k)
+            assert torch.equal(o2[k], ref[k]), (wl.name, k)
+        plan.close()
+
+
+def _tie(r, sbs, tau, th_gpu, th_orc):
+    """Thresholds agree within 1e-3, or the oracle's SURE at the two differs by at most
+    1e-6 of the scale of its terms (a near-tie that FP32-level changes of r_k can flip)."""
+    for sb in sbs:
+        a, b = th_gpu[sb.index], th_orc[sb.index]
+        if abs(a - b) <= 1e-3 * abs(b):
+            continue
+        mag = np.abs(r[sb.offset:sb.offset + sb.size])
+        t = float(tau[sb.index])
+        scale = float(np.sum(mag ** 2)) + sb.size * t
+        if abs(O.sure_value(mag, a, t) - O.sure_value(mag, b, t)) > 1e-6 * scale:
+            return False
+    return True
+
+
+def test_groups_match_oracle_on_sampled_slices():
+    iters = 5
+    groups = _groups((2, 2, 2))
+    args = [(plan, _stack(prs, "y"), _stack(prs, "mask"), _stack(prs, "density"),
+             [p.sigma for p in prs]) for _, prs, plan in groups]
+    outs = vb.solve_groups(args, iters)
+    torch.cuda.synchronize()
+    for (wl, prs, plan), o in zip(groups, outs):
+        i = 1   # second slice of each group: its own R and SNR
+        pr = prs[i]
+        ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+        res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, iters, ops=ops)
+        tau = o["tau"].cpu().numpy()[i]
+        thr = o["thr"].cpu().numpy()[i]
+        parted = None
+        for k, rec in enumerate(res.records):
+            assert rel(tau[k], rec.tau) < 1e-4, (wl.name, k)
+            if not np.allclose(thr[k], rec.theta, rtol=1e-3, atol=0):
+                # from here the runs follow different (equally valid) trajectories
+                assert _tie(rec.r, ops.sbs, rec.tau, thr[k], rec.theta), (wl.name, k)
+                parted = k
+                break
+        xg = o["x_hat"].cpu().numpy()[i]
+        if parted is None:
+            assert rel(xg, res.x_hat) < 1e-4, wl.name
+        else:
+            assert abs(O.nmse_db(xg, pr.x0) - O.nmse_db(res.x_hat, pr.x0)) < 0.1, wl.name
+        plan.close()
+
+
+def test_groups_reject_bad_arguments():
+    (wl, prs, plan), = _groups((1,))
+    y, m, d = _stack(prs, "y"), _stack(prs, "mask"), _stack(prs, "density")
+    x = torch.empty((1, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+    t = torch.empty((1, 3, plan.B), dtype=torch.float64, device="cuda")
+    g = {"plan": plan.handle, "batch": 1, "y": y, "mask": m, "density": d, "sigma": [prs[0].sigma],
+         "iters": 3, "x_hat": x, "tau": t, "thr": t.clone(), "alpha": t.clone()}
+    with pytest.raises(vb.VdampError) as e:
+        vb.vdamp_solve_groups([g, dict(g)])   # the same plan twice would share a workspace
+    assert e.value.status == vb.VDAMP_EINVAL
+    with pytest.raises(vb.VdampError):
+        vb.vdamp_solve_groups([dict(g, batch=2, sigma=[prs[0].sigma] * 2)])  # max_batch is 1
+    with pytest.raises(vb.VdampError):
+        vb.vdamp_solve_groups([dict(g, iters=0)])
+    plan.close()
+
+
+TUNINGS = [[2, 1, 16, 16, 0, 0], [4, 2, 32, 32, 1, 1], [8, 4, 64, 16, 2, 2],
+           [16, 8, 32, 32, 0, 1], [2, 2, 64, 32, 1, 2]]
+
+
+@pytest.mark.parametrize("ny,nx,wav,s", [(64, 64, "haar", 3), (48, 80, "db4", 2),
+                                         (96, 160, "db4", 3)])
+def test_every_tuning_matches_oracle(ny, nx, wav, s):
+    wl = synth.Workload("t", 91, ny, nx, 10, True, wav, s, 4.0, 4.0, 8, 30.0, 30.0, 4, 1)
+    pr = synth.make_problem(wl)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, wav, s, wl.iters)
+    plan = vb.Plan(ny, nx, wav, s)
+    y, m, d = (torch.from_numpy(np.ascontiguousarray(a[None])).cuda()
+               for a in (pr.y, pr.mask, pr.density))
+    tried = 0
+    for t in TUNINGS:
+        if nx % t[0]:
+            with pytest.raises(vb.VdampError):
+                vb.vdamp_plan_set_tuning(plan.handle, t)
+            continue
+        vb.vdamp_plan_set_tuning(plan.handle, t)
+        assert vb.vdamp_plan_get_tuning(plan.handle) == t
+        o = plan.solve(y, m, d, [pr.sigma], wl.iters)
+        torch.cuda.synchronize()
+        assert rel(o["x_hat"].cpu().numpy()[0], res.x_hat) < 1e-4, t
+        for k, rec in enumerate(res.records):
+            assert rel(o["tau"].cpu().numpy()[0, k], rec.tau) < 1e-4, (t, k)
+        tried += 1
+    assert tried >= 3
+    for bad in ([3, 1, 16, 16, 0, 0], [8, 0, 16, 16, 0, 0], [8, 1, 24, 16, 0, 0],
+                [8, 1, 16, 64, 0, 0], [8, 1, 16, 16, 3, 0]):
+        with pytest.raises(vb.VdampError) as e:
+            vb.vdamp_plan_set_tuning(plan.handle, bad)
+        assert e.value.status == vb.VDAMP_EINVAL
+    plan.close()
+
+
+def test_autotune_picks_a_valid_tuning_that_still_matches():
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=4)
+    chosen = vb.vdamp_plan_autotune(plan.handle, 4, trials=2)
+    torch.cuda.synchronize()
+    assert chosen == vb.vdamp_plan_get_tuning(plan.handle)
+    assert chosen[0] in (2, 4, 8, 16) and chosen[2] in (16, 32, 64) and chosen[3] in (16, 32)
+    iters = 6
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, iters)
+    y, m, d = (torch.from_numpy(np.ascontiguousarray(a[None])).cuda()
+               for a in (pr.y, pr.mask, pr.density))
+    o = plan.solve(y, m, d, [pr.sigma], iters)
+    torch.cuda.synchronize()
+    assert rel(o["x_hat"].cpu().numpy()[0], res.x_hat) < 1e-4
+    plan.close()
