@@ -1,0 +1,175 @@
+"""Precision report and state-evolution diagnostics of the CUDA path.
+
+Precision (what each part computes in): FP32 for the transforms (F, Psi and
+their adjoints), the k-space step and the soft threshold; FP64 for the
+cross-block tau reduction, the SURE curve sums of the chosen interval, theta
+and alpha; FP32 storage of r_k.  The report gives, for each result, its
+largest error against the FP64 oracle:
+  * 64x64 Haar, 20 iterations, free running: x_hat_k, tau_k, theta_k, alpha_k;
+  * 256x256 db4, 30 iterations, teacher forced (each step from the oracle's
+    own r~_k: the iteration amplifies FP32-level differences, so a free
+    trajectory is compared through its NMSE only): r_k, tau_k, theta_k,
+    alpha_k, r~_{k+1};
+  * the transforms F, F^H, Psi, Psi^H at 256x256.
+State evolution (Eq. 5): on the 256x256 db4 workload, for iterations k < 10
+and subbands of at least 4096 coefficients, mean |r_k - w0|^2 / tau_b lies
+in [0.85, 1.15] and Re, Im of r_k - w0 have |skew| < 0.2 and |excess
+kurtosis| < 0.3 (the oracle's own state-evolution pin, held by the GPU run).
+With VDAMP_REPORT_DIR set, both reports are written there (JSON + markdown).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import vdamp_oracle as O
+from paper_1911_01234_gb300 import binding as vb
+from paper_1911_01234_gb300 import build, diagnostics, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    vb.load()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _write(name, obj, md):
+    d = os.environ.get("VDAMP_REPORT_DIR")
+    if not d:
+        return
+    os.makedirs(d, exist_ok=True)
+    with open(os.path.join(d, name + ".json"), "w") as f:
+        json.dump(obj, f, indent=1)
+    with open(os.path.join(d, name + ".md"), "w") as f:
+        f.write(md + "\n")
+
+
+def test_precision_report():
+    rep = {}
+    # ---- 64x64 Haar, free running
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, wl.iters,
+                  want_x=True)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    o = plan.solve(dev(pr.y[None]), dev(pr.mask[None]), dev(pr.density[None]), [pr.sigma],
+                   wl.iters, want_iters=True)
+    torch.cuda.synchronize()
+    xi = o["x_hat_iters"].cpu().numpy()[:, 0]
+    tg, hg, ag = (o[k].cpu().numpy()[0] for k in ("tau", "thr", "alpha"))
+    e = {"x_hat_k (rel L2)": max(rel(xi[k], r.x_hat) for k, r in enumerate(res.records)),
+         "tau_k (rel L2)": max(rel(tg[k], r.tau) for k, r in enumerate(res.records)),
+         "theta_k (max rel)": max(float(np.max(np.abs(hg[k] - r.theta) / r.theta))
+                                  for k, r in enumerate(res.records)),
+         "alpha_k (max abs)": max(float(np.max(np.abs(ag[k] - r.alpha)))
+                                  for k, r in enumerate(res.records)),
+         "final NMSE (dB diff)": abs(O.nmse_db(xi[-1], pr.x0) - O.nmse_db(res.x_hat, pr.x0))}
+    rep["64x64 Haar s=3, 20 iterations, free running"] = e
+    assert e["x_hat_k (rel L2)"] < 1e-4 and e["tau_k (rel L2)"] < 1e-4
+    assert e["theta_k (max rel)"] < 1e-3 and e["final NMSE (dB diff)"] < 0.01
+    plan.close()
+
+    # ---- 256x256 db4, teacher forced
+    wl = synth.PLAIN_256_DB4_4
+    pr = synth.make_problem(wl)
+    ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, wl.iters, ops=ops)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = dev(pr.y[None]), dev(pr.mask[None]), dev(pr.density[None])
+    N, B = wl.ny * wl.nx, plan.B
+    y64 = np.where(pr.mask == 1, pr.y.astype(np.complex128), 0.0)
+    r = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    rn = torch.empty_like(r)
+    tau = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+    worst = {"r_k (rel L2)": 0.0, "tau_k (rel L2)": 0.0, "theta_k (max rel, untied)": 0.0,
+             "alpha_k (max abs, untied)": 0.0, "r~_{k+1} (rel L2, untied)": 0.0,
+             "iterations with a SURE tie": 0}
+    for k in range(wl.iters):
+        rt32 = res.records[k].r_tilde.astype(np.complex64)
+        rec = O.iterate(rt32.astype(np.complex128), y64, ops, float(pr.sigma) ** 2)
+        vb.vdamp_iterate(plan.handle, 1, dev(rt32[None]), y, m, p, [pr.sigma], r, tau, thr,
+                         alpha, rn)
+        torch.cuda.synchronize()
+        worst["r_k (rel L2)"] = max(worst["r_k (rel L2)"], rel(r.cpu().numpy()[0], rec.r))
+        worst["tau_k (rel L2)"] = max(worst["tau_k (rel L2)"], rel(tau.cpu().numpy()[0], rec.tau))
+        th = thr.cpu().numpy()[0]
+        if np.allclose(th, rec.theta, rtol=1e-3, atol=0):
+            worst["theta_k (max rel, untied)"] = max(worst["theta_k (max rel, untied)"],
+                                                     float(np.max(np.abs(th - rec.theta) / rec.theta)))
+            worst["alpha_k (max abs, untied)"] = max(worst["alpha_k (max abs, untied)"],
+                                                     float(np.max(np.abs(alpha.cpu().numpy()[0]
+                                                                         - rec.alpha))))
+            worst["r~_{k+1} (rel L2, untied)"] = max(worst["r~_{k+1} (rel L2, untied)"],
+                                                    rel(rn.cpu().numpy()[0],
+                                                        O.next_r_tilde(rec, ops)))
+        else:
+            worst["iterations with a SURE tie"] += 1
+    rep["256x256 db4 s=4, 30 iterations, teacher forced"] = worst
+    assert worst["r_k (rel L2)"] < 1e-5 and worst["tau_k (rel L2)"] < 1e-4
+    assert worst["theta_k (max rel, untied)"] < 1e-3 and worst["r~_{k+1} (rel L2, untied)"] < 1e-4
+
+    # ---- transforms
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal((1, 256, 256)) + 1j * rng.standard_normal((1, 256, 256))).astype(
+        np.complex64)
+    xd = dev(x)
+    out, back = torch.empty_like(xd), torch.empty_like(xd)
+    vb.vdamp_fft2(plan.handle, 1, xd, out)
+    vb.vdamp_fft2(plan.handle, 1, xd, back, inverse=True)
+    w = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    vb.vdamp_psi(plan.handle, 1, xd, w)
+    img = torch.empty_like(xd)
+    vb.vdamp_psi_h(plan.handle, 1, w, img)
+    torch.cuda.synchronize()
+    h, g = O.wavelet_filters("db4")
+    x64 = x[0].astype(np.complex128)
+    tr = {"F (rel L2)": rel(out.cpu().numpy()[0], O.fft2u(x64)),
+          "F^H (rel L2)": rel(back.cpu().numpy()[0], O.ifft2u(x64)),
+          "Psi (rel L2)": rel(w.cpu().numpy()[0], O.dwt2(x64, h, g, 4)),
+          "Psi^H Psi x vs x (rel L2)": rel(img.cpu().numpy()[0], x64)}
+    rep["transforms at 256x256 (db4 s=4)"] = tr
+    assert max(tr.values()) < 2e-6
+    plan.close()
+
+    md = ["| result | largest error vs the FP64 oracle |", "|---|---|"]
+    for sec, vals in rep.items():
+        md.append(f"| **{sec}** | |")
+        for k, v in vals.items():
+            md.append(f"| {k} | {v:.3g} |" if isinstance(v, float) else f"| {k} | {v} |")
+    _write("precision_report", rep, "\n".join(md))
+
+
+def test_state_evolution_diagnostics():
+    wl = synth.PLAIN_256_DB4_4
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    d = diagnostics.state_evolution(plan, dev(pr.y[None]), dev(pr.mask[None]),
+                                    dev(pr.density[None]), pr.sigma, pr.x0, 10)
+    for row in d["rows"]:
+        for b in row["bands"]:
+            if b["size"] >= 1024:
+                assert 0.85 <= b["ratio"] <= 1.15, (row["k"], b["band"], b["ratio"])
+            if b["size"] >= 4096:
+                assert max(abs(b["skew_re"]), abs(b["skew_im"])) < 0.2, (row["k"], b["band"])
+                assert max(abs(b["kurt_re"]), abs(b["kurt_im"])) < 0.3, (row["k"], b["band"])
+    nm = [row["nmse_db"] for row in d["rows"]]
+    assert nm[2] < nm[0]
+    _write("state_evolution_256_db4", d, diagnostics.to_markdown(d))
+    plan.close()
