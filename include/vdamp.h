@@ -178,6 +178,109 @@ typedef struct {
  */
 vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count, void* stream);
 
+/* ======================================================================
+ * Learned per-subband denoiser (operations).  A 5-layer network of 3x3
+ * convolutions per subband index b stands in for the soft threshold:
+ *   f(r) = r - sqrt(tau_b) n_b(r / sqrt(tau_b), 0.1 ln tau_b),
+ * n_b: conv 3->32, ReLU, 3 x (conv 32->32, ReLU), conv 32->2, zero padding
+ * at the subband border.  The paper only anticipates such a denoiser (its
+ * concluding section); these operations are the building blocks of its
+ * inference, its Monte-Carlo divergence and its training.
+ *
+ * Images: the network runs on a list of n_img images, given as a device
+ * int array [n_img][8] = (off, h, w, tile0, src_off, src_pitch, band, slice):
+ * image i has h x w pixels stored densely in the activation arrays from
+ * pixel `off` on; its 128-pixel tiles are tile0 .. tile0 + ceil(h w/128) - 1
+ * (tile0 ascending with i; total_tiles = the sum over images); src_off and
+ * src_pitch locate its top-left coefficient and row pitch in packed complex
+ * arrays (r, w0, f); band selects the weight set; slice selects tau.
+ * Activations are BF16 [pixel][C] with C = 16 or 32 channels.  Weights are
+ * FP32 [bands][cout][9][cin] (tap t = 3 (dy + 1) + (dx + 1)), packed by
+ * vdamp_cnn_pack_weights into BF16 operand images [bands][cout_pad x 9
+ * cin_pad] for the tensor cores.  Calls are asynchronous on `stream`;
+ * VDAMP_EINVAL (nothing launched) for invalid arguments.
+ * ==================================================================== */
+
+/* 3x3 convolution of every image (zero padding), BF16 x BF16 -> FP32 on the
+ * tensor cores; mirror = 1 negates the tap offsets (transposed convolution).
+ * mode 0: out = relu(acc + bias) BF16 [pixel][cout_pad]
+ * mode 1: out = acc * (mask > 0)  BF16, mask BF16 [pixel][cout_pad]
+ * mode 2: out = acc + bias        FP32 [pixel][cout_store]
+ * mode 3: out = acc               FP32 [pixel][cout_store]
+ * bias FP32 [bands][cout_pad].  status: device int set to 1 if a bounded
+ * wait for the tensor cores ran out (the outputs are then incomplete). */
+vdamp_status vdamp_cnn_conv3x3(const void* in, int cin_pad, const void* wimg, int cout_pad,
+                               const float* bias, const void* mask, void* out, int mode,
+                               int mirror, int cout_store, const int* images, int n_img,
+                               int total_tiles, int* status, void* stream);
+
+/* FP32 weights [bands][cout][9][cin] -> BF16 operand images; transpose = 1
+ * packs the transposed convolution (cin outputs from cout inputs) used for
+ * the gradient with respect to the layer input (with mirror = 1). */
+vdamp_status vdamp_cnn_pack_weights(const float* w, int bands, int cin, int cout, int cin_pad,
+                                    int cout_pad, int transpose, void* img, void* stream);
+
+/* Weight and bias gradients of a convolution: dw[band][co][tap][ci] +=
+ * sum_p x[p + offset(tap)][ci] dy[p][co], db[band][co] += sum_p dy[p][co]
+ * (FP32, accumulated with atomics: summation order is not fixed). */
+vdamp_status vdamp_cnn_wgrad(const void* x, int cin, int cin_pad, const void* dy, int cout,
+                             int cout_pad, const int* images, int n_img, int total_tiles,
+                             float* dw, float* db, void* stream);
+
+/* Input planes: x[p] = (Re r / sqrt(tau), Im r / sqrt(tau), 0.1 ln tau, 0...)
+ * BF16 [pixel][16], r packed complex64, tau double [slices][B]. */
+vdamp_status vdamp_cnn_input(const float* r, const double* tau, int B, const int* images,
+                             int n_img, int total_tiles, void* x, void* stream);
+
+/* Hutchinson probe: t0[p] = (eta_re, eta_im, 0...) BF16 [pixel][16], eta
+ * Rademacher from splitmix64 (Steele, Lea and Flood 2014) of
+ * seed + golden_gamma (2 key + c + 1), key = the packed index of the
+ * coefficient, c = 0 (re) or 1 (im), sign from bit 0. */
+vdamp_status vdamp_cnn_probe(unsigned long long seed, const int* images, int n_img,
+                             int total_tiles, void* t0, void* stream);
+
+/* Residual output and its statistics: f = r - sqrt(tau) n written at the
+ * images' packed positions (f may be NULL), and per image i
+ *   sums[2 i]     += sum |f - r|^2
+ *   sums[2 i + 1] += sum eta . (J_n eta)  (jn = the network's JVP output for
+ *                    the probe of `seed`, FP32 [pixel][2]; NULL: 0)
+ * n FP32 [pixel][2]; sums double, accumulated with atomics. */
+vdamp_status vdamp_cnn_output(const float* r, const double* tau, int B, const int* images,
+                              int n_img, int total_tiles, const float* n, const float* jn,
+                              unsigned long long seed, float* f, double* sums, void* stream);
+
+/* Training loss sum |f - w0|^2 * inv_count over the images (added to *loss,
+ * double) and its gradient with respect to n, BF16 [pixel][16] (channels 0,
+ * 1: -2 sqrt(tau) (f - w0) inv_count). */
+vdamp_status vdamp_cnn_loss(const float* r, const float* w0, const double* tau, int B,
+                            const int* images, int n_img, int total_tiles, const float* n,
+                            float inv_count, void* dn, double* loss, void* stream);
+
+/* Adam (Kingma and Ba) on n FP32 parameters, step >= 1 (bias corrected). */
+vdamp_status vdamp_cnn_adam(float* p, const float* g, float* m, float* v, size_t n, float lr,
+                            float beta1, float beta2, float eps, int step, void* stream);
+
+/* Onsager step of the learned denoiser (Algorithm 1 lines 6-8) per subband
+ * image i (subband b = band, slice s): with N_b = h w, div = 2 N_b - probe
+ * and SURE_cnn = sum |f - r|^2 - N_b tau + tau div (sums from
+ * vdamp_cnn_output), the network is used when SURE_cnn < sure_soft[s][b]
+ * (the soft threshold's minimum SURE, vdamp_last_sure) and 0 <= div / (2 N_b)
+ * < 1; then w_hat = f and alpha = div / (2 N_b), else w_hat = soft(r, thr)
+ * and alpha = alpha_soft.  Writes r~ = (w_hat - alpha r) / (1 - alpha) and
+ * (if not NULL) w_hat at the images' packed positions, use_out[i] (1 = the
+ * network) and alpha_out[i].  f may be NULL (soft everywhere).  tau, thr,
+ * alpha_soft, sure_soft: double [slices][B]. */
+vdamp_status vdamp_cnn_onsager(const float* r, const float* f, const double* tau,
+                               const double* thr, const double* alpha_soft,
+                               const double* sure_soft, int B, const double* sums,
+                               const int* images, int n_img, int total_tiles, float* r_tilde,
+                               float* w_hat, int* use_out, double* alpha_out, void* stream);
+
+/* Minimum SURE value of each subband at the last threshold search (solve
+ * or iterate) of this plan: double [batch][B], copied to `out` (device or
+ * host) asynchronously on `stream`. */
+vdamp_status vdamp_last_sure(vdamp_plan* plan, int batch, double* out, void* stream);
+
 /*
  * VDAMP solve, Algorithm 1 lines 1-10 with the SURE soft threshold of Sec. 3,
  * on `batch` independent slices (1 <= batch <= max_batch).

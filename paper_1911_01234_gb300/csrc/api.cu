@@ -214,6 +214,7 @@ struct vdamp_plan {
     float2* rB = nullptr;
     double* tau_part = nullptr;
     float* sorted = nullptr;
+    double* sure_val = nullptr;       // [max_batch][B] minimum SURE of the last search
     double4_32a* partrec = nullptr;
     double4_32a* bestrec = nullptr;
     unsigned* counter = nullptr;
@@ -253,6 +254,7 @@ static void plan_free(vdamp_plan* p) {
     void* bufs[] = {p->ey,       p->ex,      p->tw_y,    p->tw_x,    p->u,      p->kbuf,
                     p->ll0,      p->ll1,     p->rA,      p->rB,      p->tau_part, p->sorted,
                     p->partrec,  p->bestrec, p->counter, p->coef,    p->sigma_d, p->status,
+                    p->sure_val,
                     p->st_y,     p->st_mask, p->st_p,    p->st_x,    p->st_r0,  p->st_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -417,6 +419,7 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(dalloc(&p->partrec, MB * p->B * SURE_MAX_PARTS, &acc));
     A(dalloc(&p->bestrec, MB * p->B * SURE_MAX_PARTS, &acc));
     A(dalloc(&p->counter, MB * p->B, &acc));
+    A(dalloc(&p->sure_val, MB * p->B, &acc));
     A(dalloc(&p->coef, MB * p->B, &acc));
     A(dalloc(&p->sigma_d, MB, &acc));
     A(dalloc(&p->status, (size_t)2, &acc));
@@ -718,6 +721,7 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     a.partrec = p->partrec;
     a.bestrec = p->bestrec;
     a.counter = p->counter;
+    a.sure_out = p->sure_val;
     // split big subbands over several CTAs only while slices alone leave SMs idle
     a.max_parts = (c.batch * p->B >= 2 * p->num_sms) ? 1 : SURE_MAX_PARTS;
     c.pre();
@@ -856,6 +860,7 @@ void enq_fused(Ctx& c, const SolveArgs& s) {
     u.partrec = p->partrec;
     u.bestrec = p->bestrec;
     u.counter = p->counter;
+    u.sure_out = p->sure_val;
     u.max_parts = SURE_MAX_PARTS;
     f.l8.src = make_src(p, vdamp::SRC_LINE8, nullptr);
     f.l8.N = N;
@@ -1484,5 +1489,14 @@ extern "C" vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count,
     }
     CUDA_TRY(cudaGraphLaunch(hit->exec, us));
     for (int i = 0; i < count; ++i) groups[i].plan->last_launches = launches[i] + hit->launches[i];
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_last_sure(vdamp_plan* p, int batch, double* out, void* stream) {
+    vdamp_status st = check_common(p, batch, "vdamp_last_sure");
+    if (st != VDAMP_OK) return st;
+    if (!out) return fail(VDAMP_EINVAL, "vdamp_last_sure: NULL");
+    CUDA_TRY(cudaMemcpyAsync(out, p->sure_val, (size_t)batch * p->B * sizeof(double),
+                             cudaMemcpyDefault, (cudaStream_t)stream));
     return VDAMP_OK;
 }

@@ -1,0 +1,646 @@
+// Kernels of the learned per-subband denoiser (see cnn_dev.cuh): the 3x3
+// convolution as an implicit GEMM on the tcgen05 tensor cores (128 pixels x
+// COUT outputs x 9 CIN taps per tile, BF16 operands in shared memory, FP32
+// accumulator in tensor memory), its weight gradient, and the elementwise
+// steps around the network (input planes, residual output, Hutchinson probe,
+// loss gradient, Adam).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "../../include/vdamp.h"
+#include "cnn_dev.cuh"
+#include "vdamp_internal.cuh"
+
+namespace vdamp {
+
+namespace {
+
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+// ---------------------------------------------------------------- conv ---
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ ConvArgs a) {
+    constexpr int K = 9 * CIN;
+    constexpr int A_BYTES = 128 * K * 2;
+    constexpr int B_BYTES = COUT * K * 2;
+    constexpr uint32_t SBO_A = (K / 8) * 128, SBO_B = (K / 8) * 128, LBO = 128;
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, COUT);
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + A_BYTES;
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tbase;
+    __shared__ int s_band;
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    cudaGridDependencySynchronize();
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        s_band = -1;
+    }
+    if (warp == 0) tc::tmem_alloc(&tbase, 32);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tbase;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+        const CnnImage im = a.img[find_image(a.img, a.n_img, t)];
+        // weights of this tile's band (reloaded only when the band changes)
+        if (im.band != s_band) {
+            const uint4* src = reinterpret_cast<const uint4*>(a.wimg + (size_t)im.band * COUT * K);
+            for (int i = tid; i < B_BYTES / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = src[i];
+        }
+        // im2col of the tile: pixel m = tid, taps x CIN channels, zero outside the image
+        const int npx = im.h * im.w;
+        const int pl = (t - im.tile0) * 128 + tid;
+        const bool valid = pl < npx;
+        const int y = valid ? pl / im.w : 0, x = valid ? pl - y * im.w : 0;
+#pragma unroll
+        for (int tp = 0; tp < 9; ++tp) {
+            const int dy = a.mirror ? -tap_dy(tp) : tap_dy(tp);
+            const int dx = a.mirror ? -tap_dx(tp) : tap_dx(tp);
+            const int yy = y + dy, xx = x + dx;
+            const bool inb = valid && yy >= 0 && yy < im.h && xx >= 0 && xx < im.w;
+            const uint4* src = reinterpret_cast<const uint4*>(
+                a.in + (size_t)(im.off + (inb ? yy * im.w + xx : 0)) * CIN);
+            uint4 v[CIN / 8];
+#pragma unroll
+            for (int c = 0; c < CIN / 8; ++c) v[c] = inb ? src[c] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int c = 0; c < CIN / 8; ++c)
+                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(tid, tp * CIN + c * 8, K)) = v[c];
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            s_band = im.band;
+            tc::fence_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < K / 16; ++ks) {
+                const uint64_t ad = tc::make_desc(tc::smem_u32(sA) + ks * 256, LBO, SBO_A);
+                const uint64_t bd = tc::make_desc(tc::smem_u32(sB) + ks * 256, LBO, SBO_B);
+                tc::mma_bf16(tmem, ad, bd, IDESC, ks > 0);
+            }
+            tc::mma_commit(&mbar);
+        }
+        // the MMA outcome is made uniform over the CTA, so that every thread
+        // leaves the tile loop at the same tile
+        ok = __syncthreads_and(tc::mbar_wait(&mbar, phase, kWaitLimit)) != 0;
+        if (!ok) break;
+        phase ^= 1;
+        tc::fence_after_sync();
+        float acc[COUT];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+        if (COUT == 32) tc::tmem_ld32(ta, acc);
+        else tc::tmem_ld16(ta, acc);
+        if (ok && valid) {
+            const size_t p = (size_t)im.off + pl;
+            if (a.mode == CONV_BIAS_RELU || a.mode == CONV_MASK) {
+                const float* bs = a.bias + (size_t)im.band * COUT;
+                __nv_bfloat16 mk[COUT];
+                if (a.mode == CONV_MASK) {
+                    const uint4* ms = reinterpret_cast<const uint4*>(a.mask + p * COUT);
+#pragma unroll
+                    for (int c = 0; c < COUT / 8; ++c)
+                        *reinterpret_cast<uint4*>(mk + 8 * c) = ms[c];
+                }
+                __align__(16) __nv_bfloat16 o[COUT];
+#pragma unroll
+                for (int c = 0; c < COUT; ++c) {
+                    float v = acc[c];
+                    if (a.mode == CONV_BIAS_RELU) v = fmaxf(v + bs[c], 0.f);
+                    else v = __bfloat162float(mk[c]) > 0.f ? v : 0.f;
+                    o[c] = __float2bfloat16_rn(v);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) +
+                                                      p * COUT);
+#pragma unroll
+                for (int c = 0; c < COUT / 8; ++c) dst[c] = reinterpret_cast<const uint4*>(o)[c];
+            } else {
+                const float* bs = a.bias + (size_t)im.band * COUT;
+                float* dst = reinterpret_cast<float*>(a.out) + p * a.cout_store;
+                for (int c = 0; c < a.cout_store; ++c)
+                    dst[c] = acc[c] + (a.mode == CONV_BIAS_F32 ? bs[c] : 0.f);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();   // shared tiles and the accumulator are free again
+        tc::fence_after_sync();
+    }
+    if (!ok) {
+        // a wait ran out: record it, give the MMAs in flight one more bounded
+        // wait, then free the tensor memory as on the normal path
+        if (tid == 0) atomicExch(a.status, 1);
+        tc::mbar_wait(&mbar, phase, kWaitLimit);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
+// ------------------------------------------------------ weight packing ---
+// w [bands][cout][9][cin] FP32 -> B images [bands][COUT x 9 CIN] BF16 in
+// core-matrix order; transpose: the image of the transposed convolution
+// (rows = cin, K = (tap, cout)), zero where a padded channel has no weight.
+__global__ void pack_weights_kernel(const float* w, int bands, int cin, int cout, int CIN, int COUT,
+                                    int transpose, __nv_bfloat16* img) {
+    const int K = 9 * CIN;
+    const size_t total = (size_t)bands * COUT * K;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / ((size_t)COUT * K));
+        const int rem = (int)(i - (size_t)b * COUT * K);
+        const int row = rem / K, k = rem - row * K;
+        const int tp = k / CIN, c = k - tp * CIN;
+        float v = 0.f;
+        if (!transpose) {   // row = output channel, c = input channel
+            if (row < cout && c < cin) v = w[(((size_t)b * cout + row) * 9 + tp) * cin + c];
+        } else {            // row = forward input channel, c = forward output channel
+            if (row < cin && c < cout) v = w[(((size_t)b * cout + c) * 9 + tp) * cin + row];
+        }
+        img[(size_t)b * COUT * K + tc::kmajor_offset(row, k, K) / 2] = __float2bfloat16_rn(v);
+    }
+}
+
+// ------------------------------------------------------ weight gradient ---
+// dw[band][co][tap][ci] += sum over the image pixels p of
+//   x[p + offset(tap)][ci] dy[p][co]       (zero outside the image)
+// db[band][co] += sum_p dy[p][co].  A CTA takes tiles of 128 pixels
+// grid-stride; thread j owns the (co, ci) pairs j, j + 256, ... for all nine
+// taps and sums them in FP32 registers over its tiles, then adds the sums to
+// dw with one atomic per output (also whenever the band changes).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16* x, const __nv_bfloat16* dy,
+                                                    int cin, int cout, const CnnImage* img, int n_img,
+                                                    int total_tiles, float* dw, float* db) {
+    constexpr int PPT = (COUT * CIN + 255) / 256;   // (co, ci) pairs per thread
+    __shared__ float sx[128][CIN + 1];
+    __shared__ float sd[128][COUT + 1];
+    cudaGridDependencySynchronize();
+    const int tid = threadIdx.x;
+    const int pairs = cout * cin;
+    float acc[9][PPT];
+    float accb = 0.f;
+    int band = -1;
+    auto flush = [&]() {
+        if (band < 0) return;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int q = tid + j * 256;
+            if (q >= pairs) continue;
+            const int co = q / cin, ci = q - co * cin;
+#pragma unroll
+            for (int tp = 0; tp < 9; ++tp)
+                atomicAdd(&dw[(((size_t)band * cout + co) * 9 + tp) * cin + ci], acc[tp][j]);
+        }
+        if (tid < cout) atomicAdd(&db[(size_t)band * cout + tid], accb);
+    };
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const CnnImage im = img[find_image(img, n_img, t)];
+        if (im.band != band) {   // uniform over the CTA
+            flush();
+            band = im.band;
+#pragma unroll
+            for (int tp = 0; tp < 9; ++tp)
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) acc[tp][j] = 0.f;
+            accb = 0.f;
+        }
+        const int npx = im.h * im.w;
+        for (int e = tid; e < 128 * COUT; e += 256) {
+            const int c = e % COUT, m = e / COUT;
+            const int pl = (t - im.tile0) * 128 + m;
+            sd[m][c] = pl < npx ? __bfloat162float(dy[(size_t)(im.off + pl) * COUT + c]) : 0.f;
+        }
+        for (int tp = 0; tp < 9; ++tp) {
+            for (int e = tid; e < 128 * CIN; e += 256) {
+                const int c = e % CIN, m = e / CIN;
+                const int pl = (t - im.tile0) * 128 + m;
+                float v = 0.f;
+                if (pl < npx) {
+                    const int y = pl / im.w, xx = pl - y * im.w;
+                    const int yy = y + tap_dy(tp), x2 = xx + tap_dx(tp);
+                    if (yy >= 0 && yy < im.h && x2 >= 0 && x2 < im.w)
+                        v = __bfloat162float(x[(size_t)(im.off + yy * im.w + x2) * CIN + c]);
+                }
+                sx[m][c] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int q = tid + j * 256;
+                if (q >= pairs) continue;
+                const int co = q / cin, ci = q - co * cin;
+                float s = 0.f;
+#pragma unroll 8
+                for (int m = 0; m < 128; ++m) s += sx[m][ci] * sd[m][co];
+                acc[tp][j] += s;
+            }
+            if (tp == 0 && tid < cout)
+                for (int m = 0; m < 128; ++m) accb += sd[m][tid];
+            __syncthreads();
+        }
+    }
+    flush();
+}
+
+// ------------------------------------------------------- input planes ---
+// x[p] = (Re r / sqrt(tau), Im r / sqrt(tau), plane, 0, ...) for each pixel
+// of each image, with plane = 0.1 ln(tau) (the noise level the network is
+// told about); tau = tau[slice][band].
+__global__ void cnn_input_kernel(const float2* r, const double* tau, int B, const CnnImage* img,
+                                 int n_img, int total_tiles, __nv_bfloat16* x) {
+    cudaGridDependencySynchronize();
+    const int t = blockIdx.x;
+    if (t >= total_tiles) return;
+    const CnnImage im = img[find_image(img, n_img, t)];
+    const int pl = (t - im.tile0) * 128 + threadIdx.x;
+    if (pl >= im.h * im.w) return;
+    const int y = pl / im.w, xx = pl - y * im.w;
+    const double tv = tau[(size_t)im.slice * B + im.band];
+    const float is = tv > 0.0 ? (float)(1.0 / sqrt(tv)) : 0.f;
+    const float plane = tv > 0.0 ? (float)(0.1 * log(tv)) : 0.f;
+    const float2 v = r[(size_t)im.src_off + (size_t)y * im.src_pitch + xx];
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
+    o[0] = __float2bfloat16_rn(v.x * is);
+    o[1] = __float2bfloat16_rn(v.y * is);
+    o[2] = __float2bfloat16_rn(plane);
+    uint4* dst = reinterpret_cast<uint4*>(x + ((size_t)im.off + pl) * 16);
+    dst[0] = reinterpret_cast<const uint4*>(o)[0];
+    dst[1] = reinterpret_cast<const uint4*>(o)[1];
+}
+
+// Rademacher probe: component c (0 re, 1 im) of pixel p of image i is
+// +-1 from bit 0 of splitmix64(seed + 2 (image pixel key) + c), the key
+// being src_off + y src_pitch + x (the coefficient's packed index).
+__device__ __forceinline__ float rademacher(uint64_t seed, uint64_t key, int c) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (2 * key + (uint64_t)c + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (z & 1) ? 1.f : -1.f;
+}
+
+__global__ void cnn_probe_kernel(uint64_t seed, const CnnImage* img, int n_img, int total_tiles,
+                                 __nv_bfloat16* t0) {
+    cudaGridDependencySynchronize();
+    const int t = blockIdx.x;
+    if (t >= total_tiles) return;
+    const CnnImage im = img[find_image(img, n_img, t)];
+    const int pl = (t - im.tile0) * 128 + threadIdx.x;
+    if (pl >= im.h * im.w) return;
+    const int y = pl / im.w, xx = pl - y * im.w;
+    const uint64_t key = (uint64_t)im.src_off + (uint64_t)y * im.src_pitch + xx;
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
+    o[0] = __float2bfloat16_rn(rademacher(seed, key, 0));
+    o[1] = __float2bfloat16_rn(rademacher(seed, key, 1));
+    uint4* dst = reinterpret_cast<uint4*>(t0 + ((size_t)im.off + pl) * 16);
+    dst[0] = reinterpret_cast<const uint4*>(o)[0];
+    dst[1] = reinterpret_cast<const uint4*>(o)[1];
+}
+
+// Per image: f = r - sqrt(tau) n written to the packed array, and the sums
+//   rss   = sum |f - r|^2 = tau sum |n|^2,
+//   probe = sum eta . (J_n eta)   (if jn != NULL: the network's JVP output)
+// accumulated in FP64 per tile and added to sums[2 i], sums[2 i + 1].
+__global__ void cnn_output_kernel(const float2* r, const double* tau, int B, const CnnImage* img,
+                                  int n_img, int total_tiles, const float* n, const float* jn,
+                                  uint64_t seed, float2* f, double* sums) {
+    __shared__ double s_rss[4], s_pr[4];
+    cudaGridDependencySynchronize();
+    const int t = blockIdx.x;
+    if (t >= total_tiles) return;
+    const int ii = find_image(img, n_img, t);
+    const CnnImage im = img[ii];
+    const int pl = (t - im.tile0) * 128 + threadIdx.x;
+    double rss = 0.0, pr = 0.0;
+    if (pl < im.h * im.w) {
+        const int y = pl / im.w, xx = pl - y * im.w;
+        const double tv = tau[(size_t)im.slice * B + im.band];
+        const float st = tv > 0.0 ? (float)sqrt(tv) : 0.f;
+        const size_t q = (size_t)im.src_off + (size_t)y * im.src_pitch + xx;
+        const size_t p = (size_t)im.off + pl;
+        const float n0 = n[2 * p], n1 = n[2 * p + 1];
+        const float2 v = r[q];
+        if (f) f[q] = make_float2(v.x - st * n0, v.y - st * n1);
+        rss = tv * ((double)n0 * n0 + (double)n1 * n1);
+        if (jn) {
+            const uint64_t key = (uint64_t)im.src_off + (uint64_t)y * im.src_pitch + xx;
+            pr = (double)rademacher(seed, key, 0) * jn[2 * p] +
+                 (double)rademacher(seed, key, 1) * jn[2 * p + 1];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rss += __shfl_xor_sync(0xffffffffu, rss, o);
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_rss[warp] = rss;
+        s_pr[warp] = pr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&sums[2 * ii], s_rss[0] + s_rss[1] + s_rss[2] + s_rss[3]);
+        atomicAdd(&sums[2 * ii + 1], s_pr[0] + s_pr[1] + s_pr[2] + s_pr[3]);
+    }
+}
+
+// Training loss L = sum over images and pixels of |f - w0|^2 / npix_total
+// with f = r - sqrt(tau) n; dL/dn = -2 sqrt(tau) (f - w0) / npix_total,
+// written as BF16 [pixel][16] (channels 0, 1); loss added to *loss (FP64).
+__global__ void cnn_loss_kernel(const float2* r, const float2* w0, const double* tau, int B,
+                                const CnnImage* img, int n_img, int total_tiles, const float* n,
+                                float inv_count, __nv_bfloat16* dn, double* loss) {
+    __shared__ double s_l[4];
+    cudaGridDependencySynchronize();
+    const int t = blockIdx.x;
+    if (t >= total_tiles) return;
+    const CnnImage im = img[find_image(img, n_img, t)];
+    const int pl = (t - im.tile0) * 128 + threadIdx.x;
+    double l = 0.0;
+    if (pl < im.h * im.w) {
+        const int y = pl / im.w, xx = pl - y * im.w;
+        const double tv = tau[(size_t)im.slice * B + im.band];
+        const float st = tv > 0.0 ? (float)sqrt(tv) : 0.f;
+        const size_t q = (size_t)im.src_off + (size_t)y * im.src_pitch + xx;
+        const size_t p = (size_t)im.off + pl;
+        const float2 v = r[q], w = w0[q];
+        const float e0 = v.x - st * n[2 * p] - w.x, e1 = v.y - st * n[2 * p + 1] - w.y;
+        l = ((double)e0 * e0 + (double)e1 * e1) * inv_count;
+        __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
+        o[0] = __float2bfloat16_rn(-2.f * st * e0 * inv_count);
+        o[1] = __float2bfloat16_rn(-2.f * st * e1 * inv_count);
+        uint4* dst = reinterpret_cast<uint4*>(dn + p * 16);
+        dst[0] = reinterpret_cast<const uint4*>(o)[0];
+        dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) s_l[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(loss, s_l[0] + s_l[1] + s_l[2] + s_l[3]);
+}
+
+// Adam step on FP32 parameters (bias-corrected, step number t >= 1).
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, size_t n, float lr,
+                            float b1, float b2, float eps, int t) {
+    const float c1 = 1.f / (1.f - powf(b1, (float)t)), c2 = 1.f / (1.f - powf(b2, (float)t));
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+
+// Per subband image: the SURE of the network's denoiser,
+//   SURE_cnn = sum |f - r|^2 - N_b tau + tau div,  div = 2 N_b - probe
+// (div estimated by one Hutchinson probe: probe = eta . J_n eta), against
+// the soft threshold's minimum SURE; the smaller one gives w_hat (f, or
+// soft(r, theta)) and alpha (div / (2 N_b), or the soft alpha), and
+// r~ = (w_hat - alpha r) / (1 - alpha) (Algorithm 1 lines 6-8).
+__global__ void cnn_onsager_kernel(const float2* r, const float2* f, const double* tau,
+                                   const double* thr, const double* alpha_soft,
+                                   const double* sure_soft, int B, const double* sums,
+                                   const CnnImage* img, int n_img, int total_tiles, float2* rt,
+                                   float2* w_hat, int* use_out, double* alpha_out) {
+    cudaGridDependencySynchronize();
+    const int t = blockIdx.x;
+    if (t >= total_tiles) return;
+    const int ii = find_image(img, n_img, t);
+    const CnnImage im = img[ii];
+    const int nb = im.h * im.w;
+    const size_t sb = (size_t)im.slice * B + im.band;
+    const double tv = tau[sb];
+    const double div = 2.0 * nb - sums[2 * ii + 1];
+    const double sure_cnn = sums[2 * ii] - nb * tv + tv * div;
+    const double ac = div / (2.0 * nb);
+    const bool use = f != nullptr && tv > 0.0 && sure_cnn < sure_soft[sb] && ac >= 0.0 && ac < 1.0;
+    const double al = use ? ac : alpha_soft[sb];
+    if (t == im.tile0 && threadIdx.x == 0) {
+        if (use_out) use_out[ii] = use ? 1 : 0;
+        if (alpha_out) alpha_out[ii] = al;
+    }
+    const int pl = (t - im.tile0) * 128 + threadIdx.x;
+    if (pl >= nb) return;
+    const int y = pl / im.w, xx = pl - y * im.w;
+    const size_t q = (size_t)im.src_off + (size_t)y * im.src_pitch + xx;
+    const float2 v = r[q];
+    float2 w;
+    if (use) {
+        w = f[q];
+    } else {
+        const float th = (float)thr[sb];
+        const float a = cabs_f(v);
+        const float sc = a > th ? 1.f - th / a : 0.f;
+        w = make_float2(__fmul_rn(v.x, sc), __fmul_rn(v.y, sc));
+    }
+    if (w_hat) w_hat[q] = w;
+    const float fa = (float)al, inv = (float)(1.0 / (1.0 - al));
+    rt[q] = make_float2((w.x - fa * v.x) * inv, (w.y - fa * v.y) * inv);
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_conv(const ConvArgs& a, cudaStream_t st) {
+    constexpr size_t smem = (size_t)(128 + COUT) * 9 * CIN * 2;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(conv3x3_kernel<CIN, COUT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(a.total_tiles, 2 * sms);
+    if (grid < 1) return cudaSuccess;
+    return launch_pdl(conv3x3_kernel<CIN, COUT>, dim3(grid), dim3(128), smem, st, a);
+}
+
+}  // namespace
+}  // namespace vdamp
+
+using namespace vdamp;
+
+static vdamp_status cnn_fail(const char* msg) {
+    vdamp::set_last_error(msg);
+    return VDAMP_EINVAL;
+}
+
+extern "C" vdamp_status vdamp_cnn_conv3x3(const void* in, int cin_pad, const void* wimg,
+                                          int cout_pad, const float* bias, const void* mask,
+                                          void* out, int mode, int mirror, int cout_store,
+                                          const int* images, int n_img, int total_tiles,
+                                          int* status, void* stream) {
+    if (!in || !wimg || !out || !images || !status || n_img < 1 || total_tiles < 0)
+        return cnn_fail("vdamp_cnn_conv3x3: invalid argument");
+    if ((cin_pad != 16 && cin_pad != 32) || (cout_pad != 16 && cout_pad != 32))
+        return cnn_fail("vdamp_cnn_conv3x3: channels must be 16 or 32");
+    if (mode < 0 || mode > 3 || (mode == CONV_MASK && !mask) ||
+        ((mode == CONV_BIAS_RELU || mode == CONV_BIAS_F32) && !bias) ||
+        (mode >= CONV_BIAS_F32 && (cout_store < 1 || cout_store > cout_pad)))
+        return cnn_fail("vdamp_cnn_conv3x3: invalid mode arguments");
+    ConvArgs a;
+    a.in = (const __nv_bfloat16*)in;
+    a.wimg = (const __nv_bfloat16*)wimg;
+    a.bias = bias;
+    a.mask = (const __nv_bfloat16*)mask;
+    a.out = out;
+    a.cout_store = cout_store;
+    a.img = (const CnnImage*)images;
+    a.n_img = n_img;
+    a.total_tiles = total_tiles;
+    a.mirror = mirror ? 1 : 0;
+    a.mode = mode;
+    a.status = status;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (cin_pad == 16 && cout_pad == 32) e = launch_conv<16, 32>(a, st);
+    else if (cin_pad == 32 && cout_pad == 32) e = launch_conv<32, 32>(a, st);
+    else if (cin_pad == 32 && cout_pad == 16) e = launch_conv<32, 16>(a, st);
+    else e = launch_conv<16, 16>(a, st);
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}
+
+extern "C" vdamp_status vdamp_cnn_pack_weights(const float* w, int bands, int cin, int cout,
+                                               int cin_pad, int cout_pad, int transpose,
+                                               void* img, void* stream) {
+    if (!w || !img || bands < 1 || cin < 1 || cout < 1)
+        return cnn_fail("vdamp_cnn_pack_weights: invalid argument");
+    const int rows = transpose ? cin : cout, kc = transpose ? cout : cin;
+    if (rows > cout_pad || kc > cin_pad || (cin_pad != 16 && cin_pad != 32) ||
+        (cout_pad != 16 && cout_pad != 32))
+        return cnn_fail("vdamp_cnn_pack_weights: channels exceed the padding");
+    const size_t total = (size_t)bands * cout_pad * 9 * cin_pad;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+    launch_pdl(pack_weights_kernel, dim3(blocks), dim3(256), 0, (cudaStream_t)stream, w, bands,
+               cin, cout, cin_pad, cout_pad, transpose ? 1 : 0, (__nv_bfloat16*)img);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}
+
+extern "C" vdamp_status vdamp_cnn_wgrad(const void* x, int cin, int cin_pad, const void* dy,
+                                        int cout, int cout_pad, const int* images, int n_img,
+                                        int total_tiles, float* dw, float* db, void* stream) {
+    if (!x || !dy || !images || !dw || !db || n_img < 1 || cin > cin_pad || cout > cout_pad)
+        return cnn_fail("vdamp_cnn_wgrad: invalid argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const CnnImage* im = (const CnnImage*)images;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(total_tiles, 4 * sms));
+    const __nv_bfloat16* xb = (const __nv_bfloat16*)x;
+    const __nv_bfloat16* db16 = (const __nv_bfloat16*)dy;
+    if (cin_pad == 16 && cout_pad == 32)
+        launch_pdl(wgrad_kernel<16, 32>, dim3(grid), dim3(256), 0, st, xb, db16, cin, cout, im,
+                   n_img, total_tiles, dw, db);
+    else if (cin_pad == 32 && cout_pad == 32)
+        launch_pdl(wgrad_kernel<32, 32>, dim3(grid), dim3(256), 0, st, xb, db16, cin, cout, im,
+                   n_img, total_tiles, dw, db);
+    else if (cin_pad == 32 && cout_pad == 16)
+        launch_pdl(wgrad_kernel<32, 16>, dim3(grid), dim3(256), 0, st, xb, db16, cin, cout, im,
+                   n_img, total_tiles, dw, db);
+    else
+        return cnn_fail("vdamp_cnn_wgrad: unsupported channel padding");
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}
+
+extern "C" vdamp_status vdamp_cnn_input(const float* r, const double* tau, int B,
+                                        const int* images, int n_img, int total_tiles, void* x,
+                                        void* stream) {
+    if (!r || !tau || !images || !x || n_img < 1) return cnn_fail("vdamp_cnn_input: invalid argument");
+    if (total_tiles < 1) return VDAMP_OK;
+    launch_pdl(cnn_input_kernel, dim3(total_tiles), dim3(128), 0, (cudaStream_t)stream,
+               (const float2*)r, tau, B, (const CnnImage*)images, n_img, total_tiles,
+               (__nv_bfloat16*)x);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}
+
+extern "C" vdamp_status vdamp_cnn_probe(unsigned long long seed, const int* images, int n_img,
+                                        int total_tiles, void* t0, void* stream) {
+    if (!images || !t0 || n_img < 1) return cnn_fail("vdamp_cnn_probe: invalid argument");
+    if (total_tiles < 1) return VDAMP_OK;
+    launch_pdl(cnn_probe_kernel, dim3(total_tiles), dim3(128), 0, (cudaStream_t)stream,
+               (uint64_t)seed, (const CnnImage*)images, n_img, total_tiles, (__nv_bfloat16*)t0);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}
+
+extern "C" vdamp_status vdamp_cnn_output(const float* r, const double* tau, int B,
+                                         const int* images, int n_img, int total_tiles,
+                                         const float* n, const float* jn, unsigned long long seed,
+                                         float* f, double* sums, void* stream) {
+    if (!r || !tau || !images || !n || !sums || n_img < 1)
+        return cnn_fail("vdamp_cnn_output: invalid argument");
+    if (total_tiles < 1) return VDAMP_OK;
+    launch_pdl(cnn_output_kernel, dim3(total_tiles), dim3(128), 0, (cudaStream_t)stream,
+               (const float2*)r, tau, B, (const CnnImage*)images, n_img, total_tiles, n, jn,
+               (uint64_t)seed, (float2*)f, sums);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}
+
+extern "C" vdamp_status vdamp_cnn_loss(const float* r, const float* w0, const double* tau, int B,
+                                       const int* images, int n_img, int total_tiles,
+                                       const float* n, float inv_count, void* dn, double* loss,
+                                       void* stream) {
+    if (!r || !w0 || !tau || !images || !n || !dn || !loss || n_img < 1)
+        return cnn_fail("vdamp_cnn_loss: invalid argument");
+    if (total_tiles < 1) return VDAMP_OK;
+    launch_pdl(cnn_loss_kernel, dim3(total_tiles), dim3(128), 0, (cudaStream_t)stream,
+               (const float2*)r, (const float2*)w0, tau, B, (const CnnImage*)images, n_img,
+               total_tiles, n, inv_count, (__nv_bfloat16*)dn, loss);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}
+
+extern "C" vdamp_status vdamp_cnn_adam(float* p, const float* g, float* m, float* v, size_t n,
+                                       float lr, float beta1, float beta2, float eps, int step,
+                                       void* stream) {
+    if (!p || !g || !m || !v || step < 1) return cnn_fail("vdamp_cnn_adam: invalid argument");
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 2048);
+    if (blocks < 1) return VDAMP_OK;
+    launch_pdl(adam_kernel, dim3(blocks), dim3(256), 0, (cudaStream_t)stream, p, g, m, v, n, lr,
+               beta1, beta2, eps, step);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}
+
+extern "C" vdamp_status vdamp_cnn_onsager(const float* r, const float* f, const double* tau,
+                                          const double* thr, const double* alpha_soft,
+                                          const double* sure_soft, int B, const double* sums,
+                                          const int* images, int n_img, int total_tiles,
+                                          float* r_tilde, float* w_hat, int* use_out,
+                                          double* alpha_out, void* stream) {
+    if (!r || !tau || !thr || !alpha_soft || !sure_soft || !sums || !images || !r_tilde ||
+        n_img < 1)
+        return cnn_fail("vdamp_cnn_onsager: invalid argument");
+    if (total_tiles < 1) return VDAMP_OK;
+    launch_pdl(cnn_onsager_kernel, dim3(total_tiles), dim3(128), 0, (cudaStream_t)stream,
+               (const float2*)r, (const float2*)f, tau, thr, alpha_soft, sure_soft, B, sums,
+               (const CnnImage*)images, n_img, total_tiles, (float2*)r_tilde, (float2*)w_hat,
+               use_out, alpha_out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
+}

@@ -646,6 +646,7 @@ static __device__ void sure_search_part(const SureArgs& a, int k, int part, int 
         a.thr_out[orow] = 0.0;
         a.alpha_out[orow] = 0.0;
         a.coef[slice * a.B + b] = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = 0.0;
         if (!isfinite(tau)) record_numeric(a.status, k);
         return;
     }
@@ -657,6 +658,7 @@ static __device__ void sure_search_part(const SureArgs& a, int k, int part, int 
     a.tau_out[orow] = tau;
     a.thr_out[orow] = theta;
     a.alpha_out[orow] = alpha;
+    if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = bmi >= 0 ? bv : 0.0;
     const double inv = 1.0 / (1.0 - alpha);
     a.coef[slice * a.B + b] = make_float4((float)theta, (float)alpha, (float)inv, 0.f);
     if (bmi < 0 || !isfinite(alpha) || !isfinite(theta) || !isfinite(inv)) record_numeric(a.status, k);

@@ -193,6 +193,7 @@ struct SureArgs {
     double4_32a* partrec; // [batch][B][SURE_MAX_PARTS] (first, end, sum a^2, sum 1/a) of a part
     double4_32a* bestrec; // [batch][B][SURE_MAX_PARTS] (SURE, theta, H, m) of a part's best
     unsigned* counter;    // [batch][B] search parts done (returns to 0 after each search)
+    double* sure_out;     // [batch][B] minimum SURE of the last search
 };
 
 struct Line8Args {

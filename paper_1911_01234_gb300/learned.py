@@ -1,0 +1,433 @@
+"""Learned VDAMP: a per-subband CNN denoiser in place of the soft threshold.
+
+The paper anticipates denoisers beyond the soft threshold once the state
+evolution makes the effective noise of every subband known (concluding
+section).  Here, per subband index b, a network n_b of five 3x3
+convolutions (3 -> 32 -> 32 -> 32 -> 32 -> 2 channels, ReLU, zero padding)
+denoises in residual form
+
+    f(r) = r - sqrt(tau_b) n_b(Re r / sqrt(tau_b), Im r / sqrt(tau_b), 0.1 ln tau_b),
+
+its divergence for the Onsager term (Algorithm 1 line 7) comes from one
+Hutchinson probe through the network's forward-mode derivative, and SURE
+judges it per subband against the plain SURE soft threshold, which is kept
+wherever the network's SURE is not lower (lines 6-8 in
+vdamp_cnn_onsager).  Every convolution runs on the tcgen05 tensor cores
+(BF16 operands, FP32 accumulation); the weight gradients, the loss, Adam
+and all elementwise steps run in this library's kernels.  This module only
+sequences the C-ABI calls and holds the buffers (torch device memory).
+
+Training pairs (r_k, w0 = Psi x0) come from plain VDAMP itself, run on
+seeded synthetic phantoms of the 256x256 db4 workload's kind (other slice
+seeds than the ones evaluated).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import binding as vb
+from . import diagnostics, synth
+
+# (cin, cout) of the five layers as computed: the input has 16 channels (3
+# used) and the output 16 (2 used); the padded weights start at zero and
+# receive zero gradients, so they stay zero.
+LAYERS = [(16, 32), (32, 32), (32, 32), (32, 32), (32, 16)]
+REAL = [(3, 32), (32, 32), (32, 32), (32, 32), (32, 2)]
+
+_SIGS = {
+    "vdamp_cnn_conv3x3": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "vdamp_cnn_pack_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "vdamp_cnn_wgrad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vdamp_cnn_input": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "vdamp_cnn_probe": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "vdamp_cnn_output": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_ulonglong,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vdamp_cnn_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "vdamp_cnn_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_int, ctypes.c_void_p]),
+    "vdamp_cnn_onsager": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int] +
+                          [ctypes.c_void_p] * 2 + [ctypes.c_int, ctypes.c_int] +
+                          [ctypes.c_void_p] * 5),
+    "vdamp_last_sure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+}
+
+
+def lib():
+    L = vb.load()
+    if not getattr(L, "_cnn_sigs", False):
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        L._cnn_sigs = True
+    return L
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def _st(stream):
+    import torch
+    return torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+
+
+class Images:
+    """Image list of one launch (see include/vdamp.h): entries
+    (h, w, src_off, src_pitch, band, slice); dense pixels follow the list order."""
+
+    def __init__(self, entries: Sequence, device="cuda", dense_offsets=None):
+        import torch
+        rows, off, tile = [], 0, 0
+        for i, (h, w, src_off, pitch, band, slc) in enumerate(entries):
+            o = off if dense_offsets is None else dense_offsets[i]
+            rows.append([o, h, w, tile, src_off, pitch, band, slc])
+            off += h * w
+            tile += (h * w + 127) // 128
+        self.n = len(rows)
+        self.tiles = tile
+        self.pixels = off if dense_offsets is None else max(
+            d + e[0] * e[1] for d, e in zip(dense_offsets, entries))
+        self.rows = np.array(rows, dtype=np.int32)
+        self.dev = torch.from_numpy(self.rows.reshape(-1).copy()).to(device)
+
+    @staticmethod
+    def subbands(ny: int, nx: int, levels: int, batch: int, device="cuda") -> "Images":
+        """Every subband of every slice, dense layout = the packed layout."""
+        N = ny * nx
+        ents, offs = [], []
+        for s in range(batch):
+            for b, sb in enumerate(diagnostics.subband_layout(ny, nx, levels)):
+                ents.append((sb["h"], sb["w"], s * N + sb["offset"], sb["w"], b, s))
+                offs.append(s * N + sb["offset"])
+        return Images(ents, device, dense_offsets=offs)
+
+
+class SubbandCNN:
+    """Weights (FP32 masters + BF16 operand images), Adam state and workspace."""
+
+    def __init__(self, bands: int, seed: int = 0, device="cuda"):
+        import torch
+        self.bands = bands
+        self.device = device
+        rng = np.random.default_rng(seed)
+        self.w, self.b = [], []
+        for (cin, cout), (rin, rout) in zip(LAYERS, REAL):
+            w = np.zeros((bands, cout, 9, cin), dtype=np.float32)
+            w[:, :rout, :, :rin] = rng.standard_normal((bands, rout, 9, rin)) * math.sqrt(
+                2.0 / (9 * rin))
+            if rout == 2:   # start near the identity denoiser: a small last layer
+                w *= 0.1
+            self.w.append(torch.from_numpy(w).to(device))
+            self.b.append(torch.zeros((bands, cout), dtype=torch.float32, device=device))
+        self.params = self.w + self.b
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.steps = 0
+        self.wimg = [torch.empty(bands * cout * 9 * cin, dtype=torch.bfloat16, device=device)
+                     for cin, cout in LAYERS]
+        self.wimgT = [torch.empty(bands * cin * 9 * cout, dtype=torch.bfloat16, device=device)
+                      for cin, cout in LAYERS]
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self._ws: Dict[str, object] = {}
+        self.pack()
+
+    # ---------------------------------------------------------------- io ---
+    def state(self) -> Dict[str, np.ndarray]:
+        out = {}
+        for l in range(5):
+            out[f"w{l}"] = self.w[l].cpu().numpy()
+            out[f"b{l}"] = self.b[l].cpu().numpy()
+        return out
+
+    def load_state(self, st: Dict[str, np.ndarray]):
+        import torch
+        for l in range(5):
+            self.w[l].copy_(torch.from_numpy(st[f"w{l}"]))
+            self.b[l].copy_(torch.from_numpy(st[f"b{l}"]))
+        self.pack()
+
+    def oracle_params(self, band: int):
+        """This band's weights in the oracle's form (real channels only)."""
+        out = []
+        for l, ((rin, rout)) in enumerate(REAL):
+            out.append((self.w[l][band, :rout, :, :rin].double().cpu().numpy(),
+                        self.b[l][band, :rout].double().cpu().numpy()))
+        return out
+
+    def pack(self, stream=None):
+        L, st = lib(), _st(stream)
+        for l, (cin, cout) in enumerate(LAYERS):
+            vb.check(L.vdamp_cnn_pack_weights(_p(self.w[l]), self.bands, cin, cout, cin, cout, 0,
+                                              _p(self.wimg[l]), st), "vdamp_cnn_pack_weights")
+            if l > 0:
+                vb.check(L.vdamp_cnn_pack_weights(_p(self.w[l]), self.bands, cin, cout, cout,
+                                                  cin, 1, _p(self.wimgT[l]), st),
+                         "vdamp_cnn_pack_weights")
+
+    # ---------------------------------------------------------- buffers ---
+    def _buf(self, name, shape, dtype):
+        import torch
+        t = self._ws.get(name)
+        n = int(np.prod(shape))
+        if t is None or t.numel() < n or t.dtype != dtype:
+            t = torch.empty(max(n, 1), dtype=dtype, device=self.device)
+            self._ws[name] = t
+        return t[:n].view(*shape)
+
+    def conv(self, l, x, out, mode, im: Images, mask=None, transposed=False, cout_store=0,
+             stream=None):
+        cin, cout = LAYERS[l]
+        if transposed:
+            cin, cout = cout, cin
+        img = self.wimgT[l] if transposed else self.wimg[l]
+        vb.check(lib().vdamp_cnn_conv3x3(_p(x), cin, _p(img), cout, _p(self.b[l]), _p(mask),
+                                         _p(out), mode, 1 if transposed else 0, cout_store,
+                                         _p(im.dev), im.n, im.tiles, _p(self.status),
+                                         _st(stream)), "vdamp_cnn_conv3x3")
+
+    # ---------------------------------------------------------- passes ---
+    def forward(self, im: Images, x0, stream=None):
+        """n (FP32 [pixels][2]) and the activations [x0, a1..a4]."""
+        import torch
+        acts = [x0]
+        a = x0
+        for l in range(4):
+            o = self._buf(f"a{l + 1}", (im.pixels, LAYERS[l][1]), torch.bfloat16)
+            self.conv(l, a, o, 0, im, stream=stream)
+            acts.append(o)
+            a = o
+        n = self._buf("n", (im.pixels, 2), torch.float32)
+        self.conv(4, a, n, 2, im, cout_store=2, stream=stream)
+        return n, acts
+
+    def jvp(self, im: Images, acts, t0, stream=None):
+        import torch
+        t = t0
+        for l in range(4):
+            o = self._buf(f"j{l % 2}", (im.pixels, LAYERS[l][1]), torch.bfloat16)
+            self.conv(l, t, o, 1, im, mask=acts[l + 1], stream=stream)
+            t = o
+        jn = self._buf("jn", (im.pixels, 2), torch.float32)
+        self.conv(4, t, jn, 3, im, cout_store=2, stream=stream)
+        return jn
+
+    def backward(self, im: Images, acts, dn, grads, stream=None):
+        """Accumulate d(loss)/d(params) into grads (list like self.params) from dn."""
+        import torch
+        L, st = lib(), _st(stream)
+        d = dn
+        for l in range(4, -1, -1):
+            cin, cout = LAYERS[l]
+            vb.check(L.vdamp_cnn_wgrad(_p(acts[l]), cin, cin, _p(d), cout, cout, _p(im.dev),
+                                       im.n, im.tiles, _p(grads[l]), _p(grads[5 + l]), st),
+                     "vdamp_cnn_wgrad")
+            if l > 0:
+                o = self._buf(f"d{l % 2}", (im.pixels, cin), torch.bfloat16)
+                self.conv(l, d, o, 1, im, mask=acts[l], transposed=True, stream=stream)
+                d = o
+        return grads
+
+    def adam(self, grads, lr, stream=None, b1=0.9, b2=0.999, eps=1e-8):
+        L, st = lib(), _st(stream)
+        self.steps += 1
+        for p, g, m, v in zip(self.params, grads, self.m, self.v):
+            vb.check(L.vdamp_cnn_adam(_p(p), _p(g), _p(m), _p(v), p.numel(), lr, b1, b2, eps,
+                                      self.steps, st), "vdamp_cnn_adam")
+        self.pack(stream)
+
+    def input(self, im: Images, r, tau, B, stream=None):
+        import torch
+        x0 = self._buf("x0", (im.pixels, 16), torch.bfloat16)
+        vb.check(lib().vdamp_cnn_input(_p(r), _p(tau), B, _p(im.dev), im.n, im.tiles, _p(x0),
+                                       _st(stream)), "vdamp_cnn_input")
+        return x0
+
+    def train_step(self, im: Images, r, w0, tau, B, lr, stream=None):
+        """One Adam step on the images (patches of r with targets w0); returns the
+        loss as a device scalar (mean |f - w0|^2 per coefficient)."""
+        import torch
+        L, st = lib(), _st(stream)
+        x0 = self.input(im, r, tau, B, stream)
+        n, acts = self.forward(im, x0, stream)
+        dn = self._buf("dn", (im.pixels, 16), torch.bfloat16)
+        loss = self._buf("loss", (1,), torch.float64)
+        loss.zero_()
+        vb.check(L.vdamp_cnn_loss(_p(r), _p(w0), _p(tau), B, _p(im.dev), im.n, im.tiles, _p(n),
+                                  1.0 / im.pixels, _p(dn), _p(loss), st), "vdamp_cnn_loss")
+        grads = [self._buf(f"g{i}", tuple(p.shape), torch.float32) for i, p in
+                 enumerate(self.params)]
+        for g in grads:
+            g.zero_()
+        self.backward(im, acts, dn, grads, stream)
+        self.adam(grads, lr, stream)
+        return loss
+
+    def denoise(self, im: Images, r, tau, B, seed, f_out, sums, stream=None):
+        """f = the network's output at every image, and per image (sum |f - r|^2,
+        eta . J_n eta) for the probe `seed`."""
+        import torch
+        L, st = lib(), _st(stream)
+        x0 = self.input(im, r, tau, B, stream)
+        n, acts = self.forward(im, x0, stream)
+        t0 = self._buf("t0", (im.pixels, 16), torch.bfloat16)
+        vb.check(L.vdamp_cnn_probe(seed, _p(im.dev), im.n, im.tiles, _p(t0), st),
+                 "vdamp_cnn_probe")
+        jn = self.jvp(im, acts, t0, stream)
+        sums.zero_()
+        vb.check(L.vdamp_cnn_output(_p(r), _p(tau), B, _p(im.dev), im.n, im.tiles, _p(n),
+                                    _p(jn), seed, _p(f_out), _p(sums), st), "vdamp_cnn_output")
+
+
+# ------------------------------------------------------------ training ---
+
+def make_pairs(ny, nx, wavelet, levels, slices, iters, workload_id=77, stream=None):
+    """Plain VDAMP (this library) on seeded phantoms of the 256x256 db4 kind:
+    returns (R [pairs][N] complex64, W0 [slices][N], TAU [pairs][B], slice of each pair)."""
+    import torch
+    wl = synth.Workload("training phantoms", workload_id, ny, nx, 20, True, wavelet, levels,
+                        5.0, 5.0, 24, 30.0, 30.0, iters, 1)
+    plan = vb.Plan(ny, nx, wavelet, levels)
+    N, B = ny * nx, plan.B
+    R = torch.empty((slices * iters, N), dtype=torch.complex64, device="cuda")
+    W0 = torch.empty((slices, N), dtype=torch.complex64, device="cuda")
+    TAU = torch.empty((slices * iters, B), dtype=torch.float64, device="cuda")
+    owner = np.repeat(np.arange(slices), iters)
+    thr = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    alpha = torch.empty_like(thr)
+    rt = torch.zeros((1, N), dtype=torch.complex64, device="cuda")
+    rn = torch.empty_like(rt)
+    for s in range(slices):
+        pr = synth.make_problem(wl, s)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a[None])).cuda()
+        y, m, p = dev(pr.y), dev(pr.mask), dev(pr.density)
+        vb.vdamp_psi(plan.handle, 1, dev(pr.x0.astype(np.complex64)), W0[s:s + 1])
+        rt.zero_()
+        for k in range(iters):
+            i = s * iters + k
+            vb.vdamp_iterate(plan.handle, 1, rt, y, m, p, [pr.sigma], R[i:i + 1], TAU[i:i + 1],
+                             thr, alpha, rn)
+            rt, rn = rn, rt
+    torch.cuda.synchronize()
+    plan.close()
+    return R, W0, TAU, owner
+
+
+def train(net: SubbandCNN, R, W0, TAU, owner, ny, nx, levels, steps=1500, patches=8,
+          patch=32, lr=1e-3, seed=0, log_every=0):
+    """Adam on random patches: each step takes `patches` patches of every subband
+    (whole subbands when smaller than the patch) from random pairs."""
+    import torch
+    rng = np.random.default_rng(seed)
+    layout = diagnostics.subband_layout(ny, nx, levels)
+    N = ny * nx
+    B = len(layout)
+    pairs = R.shape[0]
+    # targets: W0 per pair (index by slice) gathered once per step into a pair-major view
+    hist = []
+    for step in range(steps):
+        ents = []
+        for b, sb in enumerate(layout):
+            ph, pw = min(patch, sb["h"]), min(patch, sb["w"])
+            for _ in range(patches):
+                i = int(rng.integers(pairs))
+                y0 = int(rng.integers(sb["h"] - ph + 1))
+                x0 = int(rng.integers(sb["w"] - pw + 1))
+                ents.append((ph, pw, i * N + sb["offset"] + y0 * sb["w"] + x0, sb["w"], b, i))
+        im = Images(ents)
+        loss = net.train_step(im, R, _targets(W0, owner, R), TAU, B, lr)
+        if log_every and step % log_every == 0:
+            hist.append((step, float(loss.item())))
+    return hist
+
+
+_TGT = {}
+
+
+def _targets(W0, owner, R):
+    """W0 laid out pair by pair (the training kernels index targets like r)."""
+    key = (W0.data_ptr(), R.shape[0])
+    t = _TGT.get(key)
+    if t is None:
+        import torch
+        t = W0[torch.from_numpy(owner).to(W0.device)]
+        _TGT.clear()
+        _TGT[key] = t
+    return t
+
+
+# ---------------------------------------------------------- learned solve ---
+
+def solve_learned(plan, net: Optional[SubbandCNN], y, mask, density, sigma, iters,
+                  seed=1, want_iters=False, stream=None):
+    """Algorithm 1 with the per-subband choice between the network and the SURE
+    soft threshold at every iteration; net=None gives the plain method through
+    the same path.  Returns x_hat, tau, thr (soft), the per-iteration network use
+    [iters][batch][B] and alpha [iters][batch][B]."""
+    import torch
+    L, st = lib(), _st(stream)
+    batch = y.shape[0]
+    ny, nx, B = plan.ny, plan.nx, plan.B
+    N = ny * nx
+    im = Images.subbands(ny, nx, plan.levels, batch)
+    rt = torch.zeros((batch, N), dtype=torch.complex64, device="cuda")
+    rt_soft = torch.empty_like(rt)
+    r = torch.empty_like(rt)
+    f = torch.empty_like(rt)
+    w_hat = torch.empty_like(rt)
+    tau = torch.empty((batch, B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+    sure_soft = torch.empty_like(tau)
+    sums = torch.zeros(2 * im.n, dtype=torch.float64, device="cuda")
+    use = torch.zeros((iters, im.n), dtype=torch.int32, device="cuda")
+    al = torch.zeros((iters, im.n), dtype=torch.float64, device="cuda")
+    taus = torch.empty((iters, batch, B), dtype=torch.float64, device="cuda")
+    thrs = torch.empty_like(taus)
+    xs = []
+    for k in range(iters):
+        vb.vdamp_iterate(plan.handle, batch, rt, y, mask, density, sigma, r, tau, thr, alpha,
+                         rt_soft, stream=st)
+        vb.check(L.vdamp_last_sure(plan.handle, batch, _p(sure_soft), st), "vdamp_last_sure")
+        taus[k].copy_(tau)
+        thrs[k].copy_(thr)
+        if net is not None:
+            net.denoise(im, r, tau, B, seed + k, f, sums, st)
+        else:
+            sums.zero_()
+        vb.check(L.vdamp_cnn_onsager(_p(r), _p(f) if net is not None else None, _p(tau),
+                                     _p(thr), _p(alpha), _p(sure_soft), B, _p(sums), _p(im.dev),
+                                     im.n, im.tiles, _p(rt), _p(w_hat), _p(use[k]), _p(al[k]),
+                                     st), "vdamp_cnn_onsager")
+        if want_iters:
+            xk = torch.empty((batch, ny, nx), dtype=torch.complex64, device="cuda")
+            vb.vdamp_final_estimate(plan.handle, batch, w_hat, y, mask, xk, stream=st)
+            xs.append(xk)
+    x_hat = torch.empty((batch, ny, nx), dtype=torch.complex64, device="cuda")
+    vb.vdamp_final_estimate(plan.handle, batch, w_hat, y, mask, x_hat, stream=st)
+    return {"x_hat": x_hat, "tau": taus, "thr": thrs,
+            "use": use.view(iters, batch, B), "alpha": al.view(iters, batch, B),
+            "x_hat_iters": xs if want_iters else None}
