@@ -23,7 +23,6 @@ seeds than the ones evaluated).
 """
 from __future__ import annotations
 
-import ctypes
 import math
 from typing import Dict, List, Optional, Sequence
 
@@ -38,53 +37,8 @@ from . import diagnostics, synth
 LAYERS = [(16, 32), (32, 32), (32, 32), (32, 32), (32, 16)]
 REAL = [(3, 32), (32, 32), (32, 32), (32, 32), (32, 2)]
 
-_SIGS = {
-    "vdamp_cnn_conv3x3": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
-                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
-                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
-    "vdamp_cnn_pack_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                              ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
-    "vdamp_cnn_wgrad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
-    "vdamp_cnn_input": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
-                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_void_p, ctypes.c_void_p]),
-    "vdamp_cnn_probe": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_void_p, ctypes.c_int,
-                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
-    "vdamp_cnn_output": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
-                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_ulonglong,
-                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
-    "vdamp_cnn_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                      ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p,
-                                      ctypes.c_void_p, ctypes.c_void_p]),
-    "vdamp_cnn_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_float,
-                                      ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                                      ctypes.c_int, ctypes.c_void_p]),
-    "vdamp_cnn_onsager": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int] +
-                          [ctypes.c_void_p] * 2 + [ctypes.c_int, ctypes.c_int] +
-                          [ctypes.c_void_p] * 5),
-    "vdamp_last_sure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
-                                       ctypes.c_void_p]),
-}
-
-
 def lib():
-    L = vb.load()
-    if not getattr(L, "_cnn_sigs", False):
-        for name, (res, args) in _SIGS.items():
-            fn = getattr(L, name)
-            fn.restype = res
-            fn.argtypes = args
-        L._cnn_sigs = True
-    return L
+    return vb.load()
 
 
 def _p(t):
