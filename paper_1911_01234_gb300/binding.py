@@ -59,40 +59,17 @@ _SIGS = {
     "vdamp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), _P]),
     "vdamp_solve_groups": (_I, [_P, _I, _P]),
     # learned per-subband denoiser
-    "vdamp_cnn_conv3x3": (_I, [_P, _I, _P,
-                                         _I, _P, _P,
-                                         _P, _I, _I,
-                                         _I, _P, _I,
-                                         _I, _P, _P]),
-    "vdamp_cnn_pack_weights": (_I, [_P, _I, _I,
-                                              _I, _I, _I,
-                                              _I, _P, _P]),
-    "vdamp_cnn_wgrad": (_I, [_P, _I, _I,
-                                       _P, _I, _I,
-                                       _P, _I, _I,
-                                       _P, _P, _P]),
-    "vdamp_cnn_input": (_I, [_P, _P, _I,
-                                       _P, _I, _I,
-                                       _P, _P]),
-    "vdamp_cnn_probe": (_I, [ctypes.c_ulonglong, _P, _I,
-                                       _I, _P, _P]),
-    "vdamp_cnn_output": (_I, [_P, _P, _I,
-                                        _P, _I, _I,
-                                        _P, _P, ctypes.c_ulonglong,
-                                        _P, _P, _P]),
-    "vdamp_cnn_loss": (_I, [_P, _P, _P,
-                                      _I, _P, _I, _I,
-                                      _P, ctypes.c_float, _P,
-                                      _P, _P]),
-    "vdamp_cnn_adam": (_I, [_P, _P, _P,
-                                      _P, ctypes.c_size_t, ctypes.c_float,
-                                      ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                                      _I, _P]),
-    "vdamp_cnn_onsager": (_I, [_P] * 6 + [_I] +
-                          [_P] * 2 + [_I, _I] +
-                          [_P] * 5),
-    "vdamp_last_sure": (_I, [_P, _I, _P,
-                                       _P]),
+    "vdamp_cnn_conv3x3": (_I, [_P, _I, _P, _I, _P, _P, _P, _I, _I, _I, _P, _I, _I, _P, _P]),
+    "vdamp_cnn_pack_weights": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _P]),
+    "vdamp_cnn_wgrad": (_I, [_P, _I, _I, _P, _I, _I, _P, _I, _I, _P, _P, _P]),
+    "vdamp_cnn_input": (_I, [_P, _P, _I, _P, _I, _I, _P, _P]),
+    "vdamp_cnn_probe": (_I, [ctypes.c_ulonglong, _P, _I, _I, _P, _P]),
+    "vdamp_cnn_output": (_I, [_P, _P, _I, _P, _I, _I, _P, _P, ctypes.c_ulonglong, _P, _P, _P]),
+    "vdamp_cnn_loss": (_I, [_P, _P, _P, _I, _P, _I, _I, _P, ctypes.c_float, _P, _P, _P]),
+    "vdamp_cnn_adam": (_I, [_P, _P, _P, _P, ctypes.c_size_t, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_float, ctypes.c_float, _I, _P]),
+    "vdamp_cnn_onsager": (_I, [_P] * 6 + [_I] + [_P] * 2 + [_I, _I] + [_P] * 5),
+    "vdamp_last_sure": (_I, [_P, _I, _P, _P]),
 }
 
 VDAMP_TUNING_LEN = 6
