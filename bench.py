@@ -332,6 +332,65 @@ def run_mixed(args, vb, torch, flush_buf, stream):
             "tuning": tunings or None}
 
 
+def run_learned(args, vb, torch, flush_buf, stream):
+    """Learned VDAMP at 256x256 db4 s=4 (per-subband CNN chosen by SURE): time to
+    reach the plain method's 30-iteration NMSE, next to the plain solve."""
+    from oracle import vdamp_oracle as O
+    from paper_1911_01234_gb300 import learned
+    tim = {}
+    net, _ = learned.train_default(steps=1500, timings=tim)
+    wl = WL
+    pr = synth.make_problem(wl, 0)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a[None])).cuda()
+    y, m, p = d(pr.y), d(pr.mask), d(pr.density)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    if not args.no_autotune:
+        plan.autotune(1, trials=3, stream=stream.cuda_stream)
+    K = wl.iters
+    plain = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
+    torch.cuda.synchronize()
+    nm_plain = [O.nmse_db(plain["x_hat_iters"][k, 0].cpu().numpy(), pr.x0) for k in range(K)]
+    solver = learned.LearnedSolver(plan, net, 1, K, want_iters=True)
+    out = solver.run(y, m, p, [pr.sigma])
+    torch.cuda.synchronize()
+    nm_l = [O.nmse_db(out["x_hat_iters"][k, 0].cpu().numpy(), pr.x0) for k in range(K)]
+    target = nm_plain[-1]
+    need = next((k + 1 for k, v in enumerate(nm_l) if v <= target), None)
+
+    def timed(fn, reps=10):
+        for i in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for i in range(reps):
+            flush_buf.fill_(float(i))
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+    ms_plain = timed(lambda: plan.solve(y, m, p, [pr.sigma], K, stream=stream.cuda_stream))
+    full = learned.LearnedSolver(plan, net, 1, K).capture(y, m, p, [pr.sigma])
+    ms_learned = timed(full.replay)
+    ms_need = None
+    if need is not None:
+        short = learned.LearnedSolver(plan, net, 1, need).capture(y, m, p, [pr.sigma])
+        ms_need = timed(short.replay)
+    use = out["use"].cpu().numpy()[:, 0, :].mean(0)
+    plan.close()
+    return {"workload": "learned VDAMP, 256x256 db4 s=4 R=5 30 dB, per-subband 5-layer CNN "
+                        "(32 ch, BF16 tcgen05) chosen by SURE, Hutchinson divergence",
+            "metric": "time to reach the plain method's 30-iteration NMSE", "unit": "ms",
+            "plain_nmse_db_30": target, "learned_nmse_db_30": nm_l[-1],
+            "learned_iters_to_plain_nmse": need, "ms_plain_30": ms_plain,
+            "ms_learned_to_plain_nmse": ms_need, "ms_learned_30": ms_learned,
+            "speedup_to_plain_nmse": (ms_plain / ms_need) if ms_need else None,
+            "network_use_per_subband": [round(float(u), 2) for u in use],
+            "training": tim}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -474,6 +533,8 @@ def run_gpu(args):
         if not args.no_batched:
             line["batched"] = run_batched(args, vb, torch, flush_buf, stream)
             line["mixed"] = run_mixed(args, vb, torch, flush_buf, stream)
+        if not args.no_learned:
+            line["learned"] = run_learned(args, vb, torch, flush_buf, stream)
         if not args.no_cpu_baseline:
             it, el = OracleRunner().run(args.cpu_seconds)
             line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -499,6 +560,8 @@ def main():
                     help="skip the 256 x 320x320 batched measurement")
     ap.add_argument("--batched-slices", type=int, default=256)
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-denoiser measurement (trains for a few seconds)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plans' default launch shapes")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "steps"],

@@ -336,52 +336,116 @@ def _targets(W0, owner, R):
 
 # ---------------------------------------------------------- learned solve ---
 
-def solve_learned(plan, net: Optional[SubbandCNN], y, mask, density, sigma, iters,
-                  seed=1, want_iters=False, stream=None):
+class LearnedSolver:
     """Algorithm 1 with the per-subband choice between the network and the SURE
-    soft threshold at every iteration; net=None gives the plain method through
-    the same path.  Returns x_hat, tau, thr (soft), the per-iteration network use
-    [iters][batch][B] and alpha [iters][batch][B]."""
+    soft threshold at every iteration (net=None: the soft threshold everywhere,
+    i.e. the plain method through the same steps).  Buffers are allocated once;
+    capture() records a whole solve on the given inputs into a CUDA graph that
+    replay() runs again (the inputs' memory and the sigma values are baked in)."""
+
+    def __init__(self, plan, net: Optional[SubbandCNN], batch: int, iters: int, seed: int = 1,
+                 want_iters: bool = False):
+        import torch
+        self.plan, self.net, self.batch, self.iters, self.seed = plan, net, batch, iters, seed
+        ny, nx, B = plan.ny, plan.nx, plan.B
+        N = ny * nx
+        self.im = Images.subbands(ny, nx, plan.levels, batch)
+        z = lambda: torch.zeros((batch, N), dtype=torch.complex64, device="cuda")
+        self.rt, self.rt_soft, self.r, self.f, self.w_hat = z(), z(), z(), z(), z()
+        d = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda")
+        self.tau, self.thr, self.alpha, self.sure_soft = (d(batch, B) for _ in range(4))
+        self.sums = d(2 * self.im.n)
+        self.use = torch.zeros((iters, self.im.n), dtype=torch.int32, device="cuda")
+        self.al = d(iters, self.im.n)
+        self.taus, self.thrs = d(iters, batch, B), d(iters, batch, B)
+        self.x_hat = torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda")
+        self.xs = torch.zeros((iters, batch, ny, nx), dtype=torch.complex64, device="cuda") \
+            if want_iters else None
+        self.graph = None
+
+    def run(self, y, mask, density, sigma, stream=None):
+        L, st = lib(), _st(stream)
+        plan, B = self.plan, self.plan.B
+        self.rt.zero_()
+        for k in range(self.iters):
+            vb.vdamp_iterate(plan.handle, self.batch, self.rt, y, mask, density, sigma, self.r,
+                             self.tau, self.thr, self.alpha, self.rt_soft, stream=st)
+            vb.check(L.vdamp_last_sure(plan.handle, self.batch, _p(self.sure_soft), st),
+                     "vdamp_last_sure")
+            self.taus[k].copy_(self.tau)
+            self.thrs[k].copy_(self.thr)
+            if self.net is not None:
+                self.net.denoise(self.im, self.r, self.tau, B, self.seed + k, self.f, self.sums,
+                                 st)
+            else:
+                self.sums.zero_()
+            vb.check(L.vdamp_cnn_onsager(_p(self.r), _p(self.f) if self.net is not None else None,
+                                         _p(self.tau), _p(self.thr), _p(self.alpha),
+                                         _p(self.sure_soft), B, _p(self.sums), _p(self.im.dev),
+                                         self.im.n, self.im.tiles, _p(self.rt), _p(self.w_hat),
+                                         _p(self.use[k]), _p(self.al[k]), st),
+                     "vdamp_cnn_onsager")
+            if self.xs is not None:
+                vb.vdamp_final_estimate(plan.handle, self.batch, self.w_hat, y, mask, self.xs[k],
+                                        stream=st)
+        vb.vdamp_final_estimate(plan.handle, self.batch, self.w_hat, y, mask, self.x_hat,
+                                stream=st)
+        return self.outputs()
+
+    def capture(self, y, mask, density, sigma):
+        import torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(y, mask, density, sigma, stream=s.cuda_stream)   # warm-up (allocations)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=s):
+            self.run(y, mask, density, sigma, stream=s.cuda_stream)
+        torch.cuda.synchronize()
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return self.outputs()
+
+    def outputs(self):
+        B = self.plan.B
+        return {"x_hat": self.x_hat, "tau": self.taus, "thr": self.thrs,
+                "use": self.use.view(self.iters, self.batch, B),
+                "alpha": self.al.view(self.iters, self.batch, B), "x_hat_iters": self.xs}
+
+
+def solve_learned(plan, net: Optional[SubbandCNN], y, mask, density, sigma, iters, seed=1,
+                  want_iters=False, stream=None):
+    """One learned solve (see LearnedSolver); returns x_hat, tau, thr (soft), the
+    per-iteration network use [iters][batch][B], alpha [iters][batch][B] and, with
+    want_iters, x_hat after every iteration [iters][batch][ny][nx]."""
+    return LearnedSolver(plan, net, y.shape[0], iters, seed, want_iters).run(
+        y, mask, density, sigma, stream)
+
+
+def train_default(slices=52, iters=30, steps=1500, seed=0, log_every=100, timings=None):
+    """The denoiser of the 256x256 db4 s=4 workload: about 20k subband pairs
+    (52 phantoms x 30 iterations x 13 subbands) from plain VDAMP, then Adam on
+    32x32 patches (8 per subband and step).  Returns the network and the
+    loss history."""
+    import time
+
     import torch
-    L, st = lib(), _st(stream)
-    batch = y.shape[0]
-    ny, nx, B = plan.ny, plan.nx, plan.B
-    N = ny * nx
-    im = Images.subbands(ny, nx, plan.levels, batch)
-    rt = torch.zeros((batch, N), dtype=torch.complex64, device="cuda")
-    rt_soft = torch.empty_like(rt)
-    r = torch.empty_like(rt)
-    f = torch.empty_like(rt)
-    w_hat = torch.empty_like(rt)
-    tau = torch.empty((batch, B), dtype=torch.float64, device="cuda")
-    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
-    sure_soft = torch.empty_like(tau)
-    sums = torch.zeros(2 * im.n, dtype=torch.float64, device="cuda")
-    use = torch.zeros((iters, im.n), dtype=torch.int32, device="cuda")
-    al = torch.zeros((iters, im.n), dtype=torch.float64, device="cuda")
-    taus = torch.empty((iters, batch, B), dtype=torch.float64, device="cuda")
-    thrs = torch.empty_like(taus)
-    xs = []
-    for k in range(iters):
-        vb.vdamp_iterate(plan.handle, batch, rt, y, mask, density, sigma, r, tau, thr, alpha,
-                         rt_soft, stream=st)
-        vb.check(L.vdamp_last_sure(plan.handle, batch, _p(sure_soft), st), "vdamp_last_sure")
-        taus[k].copy_(tau)
-        thrs[k].copy_(thr)
-        if net is not None:
-            net.denoise(im, r, tau, B, seed + k, f, sums, st)
-        else:
-            sums.zero_()
-        vb.check(L.vdamp_cnn_onsager(_p(r), _p(f) if net is not None else None, _p(tau),
-                                     _p(thr), _p(alpha), _p(sure_soft), B, _p(sums), _p(im.dev),
-                                     im.n, im.tiles, _p(rt), _p(w_hat), _p(use[k]), _p(al[k]),
-                                     st), "vdamp_cnn_onsager")
-        if want_iters:
-            xk = torch.empty((batch, ny, nx), dtype=torch.complex64, device="cuda")
-            vb.vdamp_final_estimate(plan.handle, batch, w_hat, y, mask, xk, stream=st)
-            xs.append(xk)
-    x_hat = torch.empty((batch, ny, nx), dtype=torch.complex64, device="cuda")
-    vb.vdamp_final_estimate(plan.handle, batch, w_hat, y, mask, x_hat, stream=st)
-    return {"x_hat": x_hat, "tau": taus, "thr": thrs,
-            "use": use.view(iters, batch, B), "alpha": al.view(iters, batch, B),
-            "x_hat_iters": xs if want_iters else None}
+    t0 = time.perf_counter()
+    R, W0, TAU, owner = make_pairs(256, 256, "db4", 4, slices, iters)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = SubbandCNN(bands=13, seed=seed)
+    hist = train(net, R, W0, TAU, owner, 256, 256, 4, steps=steps, seed=seed,
+                 log_every=log_every)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    if timings is not None:
+        timings.update({"pairs_s": t1 - t0, "train_s": t2 - t1,
+                        "pairs": int(R.shape[0]) * 13, "steps": steps})
+    _TGT.clear()
+    del R, W0, TAU
+    return net, hist
