@@ -424,7 +424,12 @@ def run_gpu(args):
     tau = torch.empty((1, K, plan.B), dtype=torch.float64, device="cuda")
     thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
     stream = torch.cuda.current_stream()
-    tuning = None if args.no_autotune else plan.autotune(1, trials=5, stream=stream.cuda_stream)
+    if args.tuning:
+        plan.set_tuning([int(v) for v in args.tuning.split(",")])
+        tuning = plan.tuning()
+    else:
+        tuning = None if args.no_autotune else plan.autotune(1, trials=5,
+                                                             stream=stream.cuda_stream)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -562,6 +567,9 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=5)
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-denoiser measurement (trains for a few seconds)")
+    ap.add_argument("--tuning", default="",
+                    help="explicit launch shapes for the 256x256 plan (comma-separated, "
+                         "vdamp_plan_set_tuning order) instead of autotuning it")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plans' default launch shapes")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "steps"],
