@@ -188,10 +188,13 @@ vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count, void* stre
  * inference, its Monte-Carlo divergence and its training.
  *
  * Images: the network runs on a list of n_img images, given as a device
- * int array [n_img][8] = (off, h, w, tile0, src_off, src_pitch, band, slice):
- * image i has h x w pixels stored densely in the activation arrays from
- * pixel `off` on; its 128-pixel tiles are tile0 .. tile0 + ceil(h w/128) - 1
- * (tile0 ascending with i; total_tiles = the sum over images); src_off and
+ * int array [n_img][9] = (off, h, w, tile0, src_off, src_pitch, band, slice,
+ * ctile0): image i has h x w pixels stored densely in the activation arrays
+ * from pixel `off` on; its 128-pixel tiles (elementwise operations) are
+ * tile0 .. tile0 + ceil(h w / 128) - 1 and its convolution tiles ctile0 ..
+ * ctile0 + ceil(w / Wb) ceil(h / R) - 1 (blocks of R = floor(128 / (Wb + 2))
+ * rows and Wb = min(w, 30) columns; both ascending with i; total_tiles /
+ * conv_tiles_total = the sums over images); src_off and
  * src_pitch locate its top-left coefficient and row pitch in packed complex
  * arrays (r, w0, f); band selects the weight set; slice selects tau.
  * Activations are BF16 [pixel][C] with C = 16 or 32 channels.  Weights are
@@ -203,6 +206,7 @@ vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count, void* stre
 
 /* 3x3 convolution of every image (zero padding), BF16 x BF16 -> FP32 on the
  * tensor cores; mirror = 1 negates the tap offsets (transposed convolution).
+ * max_w: the largest image width (>= 1; it sizes the shared-memory halo). 
  * mode 0: out = relu(acc + bias) BF16 [pixel][cout_pad]
  * mode 1: out = acc * (mask > 0)  BF16, mask BF16 [pixel][cout_pad]
  * mode 2: out = acc + bias        FP32 [pixel][cout_store]
@@ -212,7 +216,7 @@ vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count, void* stre
 vdamp_status vdamp_cnn_conv3x3(const void* in, int cin_pad, const void* wimg, int cout_pad,
                                const float* bias, const void* mask, void* out, int mode,
                                int mirror, int cout_store, const int* images, int n_img,
-                               int total_tiles, int* status, void* stream);
+                               int conv_tiles_total, int max_w, int* status, void* stream);
 
 /* FP32 weights [bands][cout][9][cin] -> BF16 operand images; transpose = 1
  * packs the transposed convolution (cin outputs from cout inputs) used for

@@ -59,7 +59,7 @@ _SIGS = {
     "vdamp_plan_autotune": (_I, [_P, _I, _I, ctypes.POINTER(_I), _P]),
     "vdamp_solve_groups": (_I, [_P, _I, _P]),
     # learned per-subband denoiser
-    "vdamp_cnn_conv3x3": (_I, [_P, _I, _P, _I, _P, _P, _P, _I, _I, _I, _P, _I, _I, _P, _P]),
+    "vdamp_cnn_conv3x3": (_I, [_P, _I, _P, _I, _P, _P, _P, _I, _I, _I, _P, _I, _I, _I, _P, _P]),
     "vdamp_cnn_pack_weights": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _P]),
     "vdamp_cnn_wgrad": (_I, [_P, _I, _I, _P, _I, _I, _P, _I, _I, _P, _P, _P]),
     "vdamp_cnn_input": (_I, [_P, _P, _I, _P, _I, _I, _P, _P]),

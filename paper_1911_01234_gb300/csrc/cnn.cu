@@ -17,130 +17,227 @@ namespace vdamp {
 namespace {
 
 constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr int CONV_STAGES = 4;   // halo buffers: the current tile and three in flight
 
 // ---------------------------------------------------------------- conv ---
+// Implicit GEMM without an im2col copy.  A tile is a block of the image
+// (conv_block: R rows x Wb columns); its zero-padded halo of pitch P = Wb + 2
+// lives in shared memory as CIN/8 chunk planes [chunk][position][8 channels]
+// (16 bytes per position), so that for tap (dy, dx) the A operand of the MMA
+// is the same buffer read from position P + 1 + m + dy P + dx: a descriptor
+// whose start moves by 16 bytes per position, 8-row groups 128 bytes apart
+// (SBO), and the two chunks of a K step one chunk plane apart (LBO).  The halo (and, for the masked
+// modes, the mask rows) of the next tile arrive by cp.async (zero-filled
+// outside the image) while the current tile's MMAs and epilogue run; weights
+// and bias are staged once per band.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ ConvArgs a) {
     constexpr int K = 9 * CIN;
-    constexpr int A_BYTES = 128 * K * 2;
+    constexpr int NCH = CIN / 8;
+    constexpr int KPT = CIN / 16;   // K steps per tap
     constexpr int B_BYTES = COUT * K * 2;
-    constexpr uint32_t SBO_A = (K / 8) * 128, SBO_B = (K / 8) * 128, LBO = 128;
+    constexpr int M_BYTES = 128 * COUT * 2;
+    constexpr uint32_t SBO_B = (K / 8) * 128, LBO_B = 128;
     constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, COUT);
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + A_BYTES;
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t mbar[2];   // one per TMEM accumulator
     __shared__ uint32_t tbase;
-    __shared__ int s_band;
+    __shared__ float s_bias[2][COUT];   // bias of the current band and of the next one
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int nq = a.nq;
+    const uint32_t CS = (uint32_t)nq * 16;
+    const uint32_t A_BYTES = NCH * CS;
+    uint8_t* const sA0 = smem;                       // STAGES stages
+    uint8_t* const sB = smem + CONV_STAGES * A_BYTES;
+    uint8_t* const sM0 = sB + B_BYTES;               // STAGES stages (masked mode)
+    const bool masked = a.mode == CONV_MASK;
+
+    // a contiguous range of tiles per CTA: weight bands change rarely
+    const int per = (a.total_tiles + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per;
+    const int t_end = min(a.total_tiles, t_begin + per);
+    if (t_begin >= t_end) return;   // uniform over the CTA
 
     cudaGridDependencySynchronize();
     if (tid == 0) {
-        tc::mbar_init(&mbar, 1);
-        s_band = -1;
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
     }
-    if (warp == 0) tc::tmem_alloc(&tbase, 32);
+    if (warp == 0) tc::tmem_alloc(&tbase, 64);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tbase;
-    uint32_t phase = 0;
-    bool ok = true;
 
-    for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
-        const CnnImage im = a.img[find_image(a.img, a.n_img, t)];
-        // weights of this tile's band (reloaded only when the band changes)
-        if (im.band != s_band) {
-            const uint4* src = reinterpret_cast<const uint4*>(a.wimg + (size_t)im.band * COUT * K);
-            for (int i = tid; i < B_BYTES / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = src[i];
+    // asynchronous loads of tile t into stage st (one commit group); tiles come
+    // in increasing order, so the image is found by stepping from the last one
+    // (one binary search per CTA, not one per tile)
+    int load_idx = find_conv_image(a.img, a.n_img, t_begin);
+    auto issue_loads = [&](int t, int st) -> CnnImage {
+        while (load_idx + 1 < a.n_img && a.img[load_idx + 1].ctile0 <= t) ++load_idx;
+        const CnnImage im = a.img[load_idx];
+        uint8_t* sA = sA0 + st * A_BYTES;
+        const ConvBlock cb = conv_block(im.h, im.w);
+        const int ti = t - im.ctile0, by = ti / cb.nbx, bx = ti - by * cb.nbx;
+        const int y0 = by * cb.rows - 1, x0 = bx * cb.wb - 1;   // image pixel of halo (0, 0)
+        const int P = cb.pitch, nqi = conv_halo(P);
+        const __nv_bfloat16* base = a.in + (size_t)im.off * CIN;
+        for (int q = tid; q < nqi; q += 128) {
+            const int i = q / P, j = q - i * P;
+            const int y = y0 + i, x = x0 + j;
+            const bool inb = y >= 0 && y < im.h && x >= 0 && x < im.w;
+            const __nv_bfloat16* src = inb ? base + (size_t)(y * im.w + x) * CIN : base;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                tc::cp_async16(sA + c * CS + (uint32_t)q * 16, src + 8 * c, inb ? 16u : 0u);
         }
-        // im2col of the tile: pixel m = tid, taps x CIN channels, zero outside the image
-        const int npx = im.h * im.w;
-        const int pl = (t - im.tile0) * 128 + tid;
-        const bool valid = pl < npx;
-        const int y = valid ? pl / im.w : 0, x = valid ? pl - y * im.w : 0;
+        if (masked) {
+            const int q = P + 1 + tid, i = q / P, j = q - i * P;
+            const int y = y0 + i, x = x0 + j;
+            const bool ok = i <= cb.rows && j >= 1 && j <= cb.wb && y < im.h && x < im.w;
+            const __nv_bfloat16* src =
+                ok ? a.mask + ((size_t)im.off + (size_t)y * im.w + x) * COUT : a.mask;
+            uint8_t* dst = sM0 + st * M_BYTES + tid * COUT * 2;
 #pragma unroll
-        for (int tp = 0; tp < 9; ++tp) {
-            const int dy = a.mirror ? -tap_dy(tp) : tap_dy(tp);
-            const int dx = a.mirror ? -tap_dx(tp) : tap_dx(tp);
-            const int yy = y + dy, xx = x + dx;
-            const bool inb = valid && yy >= 0 && yy < im.h && xx >= 0 && xx < im.w;
-            const uint4* src = reinterpret_cast<const uint4*>(
-                a.in + (size_t)(im.off + (inb ? yy * im.w + xx : 0)) * CIN);
-            uint4 v[CIN / 8];
+            for (int c = 0; c < COUT / 8; ++c) tc::cp_async16(dst + 16 * c, src + 8 * c, ok ? 16u : 0u);
+        }
+        tc::cp_async_commit();
+        return im;
+    };
+    auto load_band = [&](int band, int slot) {   // synchronous: no MMA may be in flight
+        const uint4* src = reinterpret_cast<const uint4*>(a.wimg + (size_t)band * COUT * K);
+        for (int i = tid; i < B_BYTES / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = src[i];
+        if (tid < COUT) s_bias[slot][tid] = a.bias ? a.bias[(size_t)band * COUT + tid] : 0.f;
+    };
+    auto issue_mma = [&](const CnnImage& im, int st, int acc) {   // one thread
+        const int W2 = conv_block(im.h, im.w).pitch;
+        const uint32_t abase = tc::smem_u32(sA0 + st * A_BYTES);
+        const uint32_t bbase = tc::smem_u32(sB);
 #pragma unroll
-            for (int c = 0; c < CIN / 8; ++c) v[c] = inb ? src[c] : make_uint4(0, 0, 0, 0);
+        for (int ks = 0; ks < 9 * KPT; ++ks) {
+            const int tp = ks / KPT, j = ks - tp * KPT;
+            int sh = tap_dy(tp) * W2 + tap_dx(tp);
+            if (a.mirror) sh = -sh;
+            const uint32_t aaddr = abase + (uint32_t)(W2 + 1 + sh) * 16 + (uint32_t)(2 * j) * CS;
+            tc::mma_bf16(tmem + acc * 32, tc::make_desc(aaddr, CS, 128),
+                         tc::make_desc(bbase + ks * 256, LBO_B, SBO_B), IDESC, ks > 0);
+        }
+        tc::mma_commit(&mbar[acc]);
+    };
+
+    constexpr int D = CONV_STAGES - 1;   // tiles in flight ahead of the current one
+    uint32_t phase[2] = {0, 0};
+    bool ok = true, pending[2] = {false, false};
+    // tiles t_begin .. t_begin + D - 1 into stages 0 .. D - 1; every iteration t
+    // then refills the stage of tile t - 1 with tile t + D
+    CnnImage cur = issue_loads(t_begin, 0);
+    CnnImage ahead[D - 1];               // at iteration t: images of tiles t + 1 .. t + D - 1
 #pragma unroll
-            for (int c = 0; c < CIN / 8; ++c)
-                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(tid, tp * CIN + c * 8, K)) = v[c];
+    for (int d = 1; d < D; ++d) {
+        ahead[d - 1] = cur;              // defined even past the range (then never used)
+        if (t_begin + d < t_end) ahead[d - 1] = issue_loads(t_begin + d, d);
+        else tc::cp_async_commit();      // empty group: the group count stays aligned
+    }
+    int band = cur.band, bslot = 0;
+    load_band(band, 0);
+    tc::cp_async_wait<D - 1>();          // tile t_begin has landed
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+        tc::fence_after_sync();
+        issue_mma(cur, 0, 0);
+    }
+    pending[0] = true;
+    // Iteration t: MMAs of tile t are in flight in accumulator t & 1.  Issue
+    // the MMAs of tile t + 1 into the other accumulator (free since the
+    // epilogue of tile t - 1), then wait for tile t and run its epilogue.
+    for (int t = t_begin; t < t_end; ++t) {
+        const int k = t - t_begin, ac = k & 1;
+        const int st = k % CONV_STAGES;
+        const bool more = t + 1 < t_end;
+        // the stage of tile t - 1 is free (its MMAs and epilogue are done): refill it
+        CnnImage fresh = cur;
+        if (t + D < t_end) fresh = issue_loads(t + D, (k + D) % CONV_STAGES);
+        else tc::cp_async_commit();
+        const CnnImage nxt = ahead[0];
+#pragma unroll
+        for (int d = 0; d + 2 < D; ++d) ahead[d] = ahead[d + 1];
+        ahead[D - 2] = fresh;
+        tc::cp_async_wait<D - 1>();   // tile t + 1 has landed (t + 2 .. t + D may still fly)
+        const bool new_band = more && nxt.band != band;
+        if (new_band) {
+            // the weights change: the tensor cores must be done with tile t first
+            ok = __syncthreads_and(tc::mbar_wait(&mbar[ac], phase[ac], kWaitLimit)) != 0;
+            if (!ok) break;
+            band = nxt.band;
+            load_band(band, bslot ^ 1);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
-            s_band = im.band;
-            tc::fence_after_sync();
-#pragma unroll
-            for (int ks = 0; ks < K / 16; ++ks) {
-                const uint64_t ad = tc::make_desc(tc::smem_u32(sA) + ks * 256, LBO, SBO_A);
-                const uint64_t bd = tc::make_desc(tc::smem_u32(sB) + ks * 256, LBO, SBO_B);
-                tc::mma_bf16(tmem, ad, bd, IDESC, ks > 0);
+        if (more) {
+            if (tid == 0) {
+                tc::fence_after_sync();
+                issue_mma(nxt, (k + 1) % CONV_STAGES, ac ^ 1);
             }
-            tc::mma_commit(&mbar);
+            pending[ac ^ 1] = true;
         }
-        // the MMA outcome is made uniform over the CTA, so that every thread
-        // leaves the tile loop at the same tile
-        ok = __syncthreads_and(tc::mbar_wait(&mbar, phase, kWaitLimit)) != 0;
-        if (!ok) break;
-        phase ^= 1;
+        if (!new_band) {
+            ok = __syncthreads_and(tc::mbar_wait(&mbar[ac], phase[ac], kWaitLimit)) != 0;
+            if (!ok) break;
+        }
+        phase[ac] ^= 1;
+        pending[ac] = false;
         tc::fence_after_sync();
         float acc[COUT];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t ta = tmem + ac * 32 + ((uint32_t)(warp * 32) << 16);
         if (COUT == 32) tc::tmem_ld32(ta, acc);
         else tc::tmem_ld16(ta, acc);
-        if (ok && valid) {
-            const size_t p = (size_t)im.off + pl;
-            if (a.mode == CONV_BIAS_RELU || a.mode == CONV_MASK) {
-                const float* bs = a.bias + (size_t)im.band * COUT;
-                __nv_bfloat16 mk[COUT];
-                if (a.mode == CONV_MASK) {
-                    const uint4* ms = reinterpret_cast<const uint4*>(a.mask + p * COUT);
-#pragma unroll
-                    for (int c = 0; c < COUT / 8; ++c)
-                        *reinterpret_cast<uint4*>(mk + 8 * c) = ms[c];
-                }
-                __align__(16) __nv_bfloat16 o[COUT];
+        const ConvBlock cb = conv_block(cur.h, cur.w);
+        const int ti = t - cur.ctile0, by = ti / cb.nbx, bx = ti - by * cb.nbx;
+        const int q = cb.pitch + 1 + tid, bi = q / cb.pitch, bj = q - bi * cb.pitch;
+        const int oy = by * cb.rows - 1 + bi, ox = bx * cb.wb - 1 + bj;
+        if (bi <= cb.rows && bj >= 1 && bj <= cb.wb && oy < cur.h && ox < cur.w) {
+            const size_t p = (size_t)cur.off + (size_t)oy * cur.w + ox;
+            if (a.mode == CONV_BIAS_RELU || masked) {
+                const __nv_bfloat16* mk =
+                    reinterpret_cast<const __nv_bfloat16*>(sM0 + st * M_BYTES + tid * COUT * 2);
+                uint4 ov[COUT / 8];
+                __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ov);
 #pragma unroll
                 for (int c = 0; c < COUT; ++c) {
                     float v = acc[c];
-                    if (a.mode == CONV_BIAS_RELU) v = fmaxf(v + bs[c], 0.f);
+                    if (!masked) v = fmaxf(v + s_bias[bslot][c], 0.f);
                     else v = __bfloat162float(mk[c]) > 0.f ? v : 0.f;
                     o[c] = __float2bfloat16_rn(v);
                 }
                 uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) +
                                                       p * COUT);
 #pragma unroll
-                for (int c = 0; c < COUT / 8; ++c) dst[c] = reinterpret_cast<const uint4*>(o)[c];
+                for (int c = 0; c < COUT / 8; ++c) dst[c] = ov[c];
             } else {
-                const float* bs = a.bias + (size_t)im.band * COUT;
                 float* dst = reinterpret_cast<float*>(a.out) + p * a.cout_store;
                 for (int c = 0; c < a.cout_store; ++c)
-                    dst[c] = acc[c] + (a.mode == CONV_BIAS_F32 ? bs[c] : 0.f);
+                    dst[c] = acc[c] + (a.mode == CONV_BIAS_F32 ? s_bias[bslot][c] : 0.f);
             }
         }
         tc::fence_before_sync();
-        __syncthreads();   // shared tiles and the accumulator are free again
-        tc::fence_after_sync();
+        __syncthreads();   // accumulator ac and this tile's stage are free again
+        if (new_band) bslot ^= 1;
+        cur = nxt;
     }
     if (!ok) {
         // a wait ran out: record it, give the MMAs in flight one more bounded
         // wait, then free the tensor memory as on the normal path
         if (tid == 0) atomicExch(a.status, 1);
-        tc::mbar_wait(&mbar, phase, kWaitLimit);
+        for (int i = 0; i < 2; ++i)
+            if (pending[i]) tc::mbar_wait(&mbar[i], phase[i], kWaitLimit);
     }
+    tc::cp_async_wait_all();
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
 // ------------------------------------------------------ weight packing ---
@@ -262,9 +359,9 @@ __global__ void cnn_input_kernel(const float2* r, const double* tau, int B, cons
     const int pl = (t - im.tile0) * 128 + threadIdx.x;
     if (pl >= im.h * im.w) return;
     const int y = pl / im.w, xx = pl - y * im.w;
-    const double tv = tau[(size_t)im.slice * B + im.band];
-    const float is = tv > 0.0 ? (float)(1.0 / sqrt(tv)) : 0.f;
-    const float plane = tv > 0.0 ? (float)(0.1 * log(tv)) : 0.f;
+    const float tv = (float)tau[(size_t)im.slice * B + im.band];   // per-image constants in FP32
+    const float is = tv > 0.f ? 1.f / sqrtf(tv) : 0.f;
+    const float plane = tv > 0.f ? 0.1f * logf(tv) : 0.f;
     const float2 v = r[(size_t)im.src_off + (size_t)y * im.src_pitch + xx];
     __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
@@ -325,18 +422,20 @@ __global__ void cnn_output_kernel(const float2* r, const double* tau, int B, con
     double rss = 0.0, pr = 0.0;
     if (pl < im.h * im.w) {
         const int y = pl / im.w, xx = pl - y * im.w;
-        const double tv = tau[(size_t)im.slice * B + im.band];
-        const float st = tv > 0.0 ? (float)sqrt(tv) : 0.f;
+        const float tv = (float)tau[(size_t)im.slice * B + im.band];
+        const float st = tv > 0.f ? sqrtf(tv) : 0.f;
         const size_t q = (size_t)im.src_off + (size_t)y * im.src_pitch + xx;
         const size_t p = (size_t)im.off + pl;
         const float n0 = n[2 * p], n1 = n[2 * p + 1];
         const float2 v = r[q];
-        if (f) f[q] = make_float2(v.x - st * n0, v.y - st * n1);
-        rss = tv * ((double)n0 * n0 + (double)n1 * n1);
+        const float2 fv = make_float2(v.x - st * n0, v.y - st * n1);
+        if (f) f[q] = fv;
+        const float e0 = fv.x - v.x, e1 = fv.y - v.y;
+        rss = (double)(e0 * e0 + e1 * e1);
         if (jn) {
             const uint64_t key = (uint64_t)im.src_off + (uint64_t)y * im.src_pitch + xx;
-            pr = (double)rademacher(seed, key, 0) * jn[2 * p] +
-                 (double)rademacher(seed, key, 1) * jn[2 * p + 1];
+            pr = (double)(rademacher(seed, key, 0) * jn[2 * p] +
+                          rademacher(seed, key, 1) * jn[2 * p + 1]);
         }
     }
 #pragma unroll
@@ -371,8 +470,8 @@ __global__ void cnn_loss_kernel(const float2* r, const float2* w0, const double*
     double l = 0.0;
     if (pl < im.h * im.w) {
         const int y = pl / im.w, xx = pl - y * im.w;
-        const double tv = tau[(size_t)im.slice * B + im.band];
-        const float st = tv > 0.0 ? (float)sqrt(tv) : 0.f;
+        const float tv = (float)tau[(size_t)im.slice * B + im.band];
+        const float st = tv > 0.f ? sqrtf(tv) : 0.f;
         const size_t q = (size_t)im.src_off + (size_t)y * im.src_pitch + xx;
         const size_t p = (size_t)im.off + pl;
         const float2 v = r[q], w = w0[q];
@@ -421,6 +520,8 @@ __global__ void cnn_onsager_kernel(const float2* r, const float2* f, const doubl
                                    const double* sure_soft, int B, const double* sums,
                                    const CnnImage* img, int n_img, int total_tiles, float2* rt,
                                    float2* w_hat, int* use_out, double* alpha_out) {
+    __shared__ int s_use;
+    __shared__ float s_fa, s_inv, s_th;
     cudaGridDependencySynchronize();
     const int t = blockIdx.x;
     if (t >= total_tiles) return;
@@ -428,16 +529,25 @@ __global__ void cnn_onsager_kernel(const float2* r, const float2* f, const doubl
     const CnnImage im = img[ii];
     const int nb = im.h * im.w;
     const size_t sb = (size_t)im.slice * B + im.band;
-    const double tv = tau[sb];
-    const double div = 2.0 * nb - sums[2 * ii + 1];
-    const double sure_cnn = sums[2 * ii] - nb * tv + tv * div;
-    const double ac = div / (2.0 * nb);
-    const bool use = f != nullptr && tv > 0.0 && sure_cnn < sure_soft[sb] && ac >= 0.0 && ac < 1.0;
-    const double al = use ? ac : alpha_soft[sb];
-    if (t == im.tile0 && threadIdx.x == 0) {
-        if (use_out) use_out[ii] = use ? 1 : 0;
-        if (alpha_out) alpha_out[ii] = al;
+    if (threadIdx.x == 0) {   // the per-subband decision, in FP64, once per block
+        const double tv = tau[sb];
+        const double div = 2.0 * nb - sums[2 * ii + 1];
+        const double sure_cnn = sums[2 * ii] - nb * tv + tv * div;
+        const double ac = div / (2.0 * nb);
+        const bool use = f != nullptr && tv > 0.0 && sure_cnn < sure_soft[sb] && ac >= 0.0 &&
+                         ac < 1.0;
+        const double al = use ? ac : alpha_soft[sb];
+        s_use = use ? 1 : 0;
+        s_fa = (float)al;
+        s_inv = (float)(1.0 / (1.0 - al));
+        s_th = (float)thr[sb];
+        if (t == im.tile0) {
+            if (use_out) use_out[ii] = use ? 1 : 0;
+            if (alpha_out) alpha_out[ii] = al;
+        }
     }
+    __syncthreads();
+    const bool use = s_use != 0;
     const int pl = (t - im.tile0) * 128 + threadIdx.x;
     if (pl >= nb) return;
     const int y = pl / im.w, xx = pl - y * im.w;
@@ -447,25 +557,26 @@ __global__ void cnn_onsager_kernel(const float2* r, const float2* f, const doubl
     if (use) {
         w = f[q];
     } else {
-        const float th = (float)thr[sb];
         const float a = cabs_f(v);
-        const float sc = a > th ? 1.f - th / a : 0.f;
+        const float sc = a > s_th ? 1.f - s_th / a : 0.f;
         w = make_float2(__fmul_rn(v.x, sc), __fmul_rn(v.y, sc));
     }
     if (w_hat) w_hat[q] = w;
-    const float fa = (float)al, inv = (float)(1.0 / (1.0 - al));
-    rt[q] = make_float2((w.x - fa * v.x) * inv, (w.y - fa * v.y) * inv);
+    rt[q] = make_float2((w.x - s_fa * v.x) * s_inv, (w.y - s_fa * v.y) * s_inv);
 }
 
 template <int CIN, int COUT>
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t st) {
-    constexpr size_t smem = (size_t)(128 + COUT) * 9 * CIN * 2;
-    static bool configured = false;
-    if (!configured) {
+    const size_t smem = CONV_STAGES * (size_t)(CIN / 8) * a.nq * 16 + (size_t)COUT * 9 * CIN * 2 +
+                        (a.mode == CONV_MASK ? CONV_STAGES * (size_t)128 * COUT * 2 : 0);
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    static size_t raised = 48 * 1024;   // the attribute only ever grows (process-wide)
+    if (smem > raised) {
         cudaError_t e = cudaFuncSetAttribute(conv3x3_kernel<CIN, COUT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        raised = smem;
     }
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -488,9 +599,10 @@ static vdamp_status cnn_fail(const char* msg) {
 extern "C" vdamp_status vdamp_cnn_conv3x3(const void* in, int cin_pad, const void* wimg,
                                           int cout_pad, const float* bias, const void* mask,
                                           void* out, int mode, int mirror, int cout_store,
-                                          const int* images, int n_img, int total_tiles,
-                                          int* status, void* stream) {
-    if (!in || !wimg || !out || !images || !status || n_img < 1 || total_tiles < 0)
+                                          const int* images, int n_img, int conv_tiles_total,
+                                          int max_w, int* status, void* stream) {
+    if (!in || !wimg || !out || !images || !status || n_img < 1 || conv_tiles_total < 0 ||
+        max_w < 1)
         return cnn_fail("vdamp_cnn_conv3x3: invalid argument");
     if ((cin_pad != 16 && cin_pad != 32) || (cout_pad != 16 && cout_pad != 32))
         return cnn_fail("vdamp_cnn_conv3x3: channels must be 16 or 32");
@@ -507,7 +619,8 @@ extern "C" vdamp_status vdamp_cnn_conv3x3(const void* in, int cin_pad, const voi
     a.cout_store = cout_store;
     a.img = (const CnnImage*)images;
     a.n_img = n_img;
-    a.total_tiles = total_tiles;
+    a.total_tiles = conv_tiles_total;
+    a.nq = conv_halo(conv_block(1, max_w).pitch);
     a.mirror = mirror ? 1 : 0;
     a.mode = mode;
     a.status = status;

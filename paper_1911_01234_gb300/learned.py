@@ -52,18 +52,23 @@ def _st(stream):
 
 class Images:
     """Image list of one launch (see include/vdamp.h): entries
-    (h, w, src_off, src_pitch, band, slice); dense pixels follow the list order."""
+    (h, w, src_off, src_pitch, band, slice); dense pixels follow the list order;
+    tiles / ctiles count the elementwise and the convolution tiles."""
 
     def __init__(self, entries: Sequence, device="cuda", dense_offsets=None):
         import torch
-        rows, off, tile = [], 0, 0
+        rows, off, tile, ctile = [], 0, 0, 0
         for i, (h, w, src_off, pitch, band, slc) in enumerate(entries):
             o = off if dense_offsets is None else dense_offsets[i]
-            rows.append([o, h, w, tile, src_off, pitch, band, slc])
+            rows.append([o, h, w, tile, src_off, pitch, band, slc, ctile])
             off += h * w
             tile += (h * w + 127) // 128
+            wb = min(w, 30)   # convolution blocks: wb columns x floor(128 / (wb + 2)) rows
+            ctile += ((w + wb - 1) // wb) * ((h + 128 // (wb + 2) - 1) // (128 // (wb + 2)))
         self.n = len(rows)
         self.tiles = tile
+        self.ctiles = ctile
+        self.max_w = max(e[1] for e in entries)
         self.pixels = off if dense_offsets is None else max(
             d + e[0] * e[1] for d, e in zip(dense_offsets, entries))
         self.rows = np.array(rows, dtype=np.int32)
@@ -161,7 +166,7 @@ class SubbandCNN:
         img = self.wimgT[l] if transposed else self.wimg[l]
         vb.check(lib().vdamp_cnn_conv3x3(_p(x), cin, _p(img), cout, _p(self.b[l]), _p(mask),
                                          _p(out), mode, 1 if transposed else 0, cout_store,
-                                         _p(im.dev), im.n, im.tiles, _p(self.status),
+                                         _p(im.dev), im.n, im.ctiles, im.max_w, _p(self.status),
                                          _st(stream)), "vdamp_cnn_conv3x3")
 
     # ---------------------------------------------------------- passes ---
@@ -449,3 +454,40 @@ def train_default(slices=52, iters=30, steps=1500, seed=0, log_every=100, timing
     _TGT.clear()
     del R, W0, TAU
     return net, hist
+
+
+def time_denoiser(batch: int = 64, reps: int = 10, seed: int = 0):
+    """Times one denoiser application (input planes, the 5 convolutions, the
+    probe, the 5 JVP convolutions, the output sums) on `batch` synthetic
+    256x256 db4 s=4 slices; returns (ms, TFLOP/s of the convolutions)."""
+    import torch
+    net = SubbandCNN(13, seed=seed)
+    im = Images.subbands(256, 256, 4, batch)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    r = torch.randn((batch, 65536), dtype=torch.complex64, device="cuda", generator=g)
+    tau = torch.full((batch, 13), 0.5, dtype=torch.float64, device="cuda")
+    f = torch.empty_like(r)
+    sums = torch.zeros(2 * im.n, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        net.denoise(im, r, tau, 13, 7, f, sums)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        net.denoise(im, r, tau, 13, 7, f, sums)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flop = batch * 65536 * 2 * sum(9 * ci * co for ci, co in LAYERS) * 2
+    return ms, flop / ms / 1e9
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="time the learned denoiser on synthetic slices")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--reps", type=int, default=10)
+    args = ap.parse_args()
+    vb.load()
+    ms, tf = time_denoiser(args.batch, args.reps)
+    print(f"batch {args.batch}: denoise {ms:.3f} ms, {tf:.1f} TFLOP/s of convolution")

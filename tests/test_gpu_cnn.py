@@ -31,7 +31,10 @@ def _lib():
     vb.load()
 
 
-SIZES = [(13, 9), (16, 16), (5, 40), (1, 1), (32, 24)]
+# small and ragged images, and two large ones so that every CTA of a launch
+# (at most 2 per SM) runs several tiles through the load pipeline
+SIZES = [(13, 9), (16, 16), (5, 40), (1, 1), (32, 24), (3, 200), (40, 3), (256, 240),
+         (200, 200)]
 
 
 def rel(a, b):
@@ -81,7 +84,8 @@ def test_conv_matches_oracle(cin, cout, mode, mirror):
     xt = _bf(x)   # kept alive until the kernel has run
     vb.check(L.vdamp_cnn_conv3x3(xt.data_ptr(), cin, img.data_ptr(), cout, bt.data_ptr(),
                                  mt.data_ptr(), out.data_ptr(), mode, mirror, store,
-                                 im.dev.data_ptr(), im.n, im.tiles, st.data_ptr(), None), "conv")
+                                 im.dev.data_ptr(), im.n, im.ctiles, im.max_w, st.data_ptr(),
+                                 None), "conv")
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     got = out.float().cpu().numpy()

@@ -47,6 +47,21 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def mag32(r):
+    """|r| as the kernels form it: FP32 sqrt of an FP32 fused x*x + (y*y rounded)."""
+    r = np.asarray(r).astype(np.complex64)
+    x = r.real.astype(np.float64)
+    y2 = (r.imag.astype(np.float32) * r.imag.astype(np.float32)).astype(np.float64)
+    return np.sqrt((x * x + y2).astype(np.float32).astype(np.float64)).astype(np.float32)
+
+
+def soft32(r, theta):
+    """Soft threshold with the kernels' above/below decision (FP32 magnitudes): theta
+    often equals one of them, where an FP64 magnitude could fall on the other side."""
+    a = mag32(r).astype(np.float64)
+    return np.where(a > theta, 1.0 - theta / np.where(a > 0, a, 1.0), 0.0) * r
+
+
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
@@ -72,10 +87,7 @@ def test_soft_onsager_equals_plain_line8_and_sure_value():
     # the magnitudes as the kernels key them (FP32 sqrt of an FP32 fused x^2 + y^2): the
     # threshold often sits exactly on one of them, so a one-ulp difference in a
     # magnitude would move that coefficient across theta and change SURE by tau
-    rr = r.cpu().numpy()[0]
-    x = rr.real.astype(np.float64)
-    y2 = (rr.imag.astype(np.float32) * rr.imag.astype(np.float32)).astype(np.float64)
-    a32 = np.sqrt((x * x + y2).astype(np.float32).astype(np.float64)).astype(np.float32)
+    a32 = mag32(r.cpu().numpy()[0])
     for b, sb in enumerate(diagnostics.subband_layout(wl.ny, wl.nx, wl.levels)):
         a = a32[sb["offset"]:sb["offset"] + sb["h"] * sb["w"]].astype(np.float64)
         t, th = float(tau[0, b]), float(thr[0, b])
@@ -138,7 +150,7 @@ def test_learned_iteration_matches_oracle(trained):
             assert rel(rt[o:o + h * w].reshape(h, w), ref) < 3e-2, b
         else:
             a_s = float(alpha[b])
-            ref = (O.soft(rb, float(thr[b])) - a_s * rb) / (1 - a_s)
+            ref = (soft32(rb, float(thr[b])) - a_s * rb) / (1 - a_s)
             assert rel(rt[o:o + h * w].reshape(h, w), ref) < 1e-5, b
     assert agree >= plan.B - 1
     assert int(use.sum()) >= 1        # the trained network is used somewhere
