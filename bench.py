@@ -332,6 +332,71 @@ def run_mixed(args, vb, torch, flush_buf, stream):
             "tuning": tunings or None}
 
 
+def run_learned_batched(args, vb, torch, flush_buf, stream):
+    """Learned VDAMP at scale: 256 slices of 320x320 db4 s=5 R=6 (a 16-subband
+    network trained on pairs of that kind), time to reach the plain method's
+    30-iteration mean NMSE, next to plain batched VDAMP (20 and 30 iterations)."""
+    from oracle import vdamp_oracle as O
+    from paper_1911_01234_gb300 import learned
+    wl = synth.BATCH_320_DB4_5
+    nb = args.batched_slices
+    tim = {}
+    net, _ = learned.train_for(wl.ny, wl.nx, wl.wavelet, wl.levels, wl.rate, 63, wl.iters,
+                               steps=1500, workload_id=78, timings=tim)
+    probs = [synth.make_problem(wl, i) for i in range(nb)]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
+    y, m, p = dev([q.y for q in probs]), dev([q.mask for q in probs]), dev([q.density for q in probs])
+    sig = [q.sigma for q in probs]
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
+    if not args.no_autotune:
+        plan.autotune(nb, trials=3, stream=stream.cuda_stream)
+
+    def mean_nmse(x):
+        xs = x.cpu().numpy()
+        return float(np.mean([O.nmse_db(xs[i], probs[i].x0) for i in range(nb)]))
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for i in range(reps):
+            flush_buf.fill_(float(i))
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+    plain30 = plan.solve(y, m, p, sig, 30)
+    torch.cuda.synchronize()
+    target = mean_nmse(plain30["x_hat"])
+    ms_plain30 = timed(lambda: plan.solve(y, m, p, sig, 30, stream=stream.cuda_stream))
+    ms_plain20 = timed(lambda: plan.solve(y, m, p, sig, wl.iters, stream=stream.cuda_stream))
+    nm_plain20 = mean_nmse(plan.solve(y, m, p, sig, wl.iters)["x_hat"])
+    full = learned.LearnedSolver(plan, net, nb, wl.iters, want_iters=True)
+    out = full.run(y, m, p, sig)
+    torch.cuda.synchronize()
+    curve = [mean_nmse(out["x_hat_iters"][k]) for k in range(wl.iters)]
+    use = out["use"].float().mean(dim=(0, 1)).cpu().numpy()
+    del full, out
+    need = next((k + 1 for k, v in enumerate(curve) if v <= target), None)
+    ms_need = None
+    if need is not None:
+        solver = learned.LearnedSolver(plan, net, nb, need).capture(y, m, p, sig)
+        ms_need = timed(solver.replay)
+    plan.close()
+    return {"workload": wl.name + ", learned per-subband CNN (16 networks) chosen by SURE",
+            "metric": "time to reach the plain method's 30-iteration mean NMSE", "unit": "ms",
+            "plain_mean_nmse_db_30": target, "plain_mean_nmse_db_20": nm_plain20,
+            "ms_plain_30": ms_plain30, "ms_plain_20": ms_plain20,
+            "learned_mean_nmse_db_by_iter": [round(v, 3) for v in curve],
+            "learned_iters_to_plain_nmse": need, "ms_learned_to_plain_nmse": ms_need,
+            "speedup_to_plain_nmse": (ms_plain30 / ms_need) if ms_need else None,
+            "network_use_per_subband": [round(float(u), 2) for u in use],
+            "training": tim}
+
+
 def run_learned(args, vb, torch, flush_buf, stream):
     """Learned VDAMP at 256x256 db4 s=4 (per-subband CNN chosen by SURE): time to
     reach the plain method's 30-iteration NMSE, next to the plain solve."""
@@ -540,6 +605,8 @@ def run_gpu(args):
             line["mixed"] = run_mixed(args, vb, torch, flush_buf, stream)
         if not args.no_learned:
             line["learned"] = run_learned(args, vb, torch, flush_buf, stream)
+            if not args.no_batched:
+                line["learned_batched"] = run_learned_batched(args, vb, torch, flush_buf, stream)
         if not args.no_cpu_baseline:
             it, el = OracleRunner().run(args.cpu_seconds)
             line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",

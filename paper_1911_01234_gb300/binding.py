@@ -72,8 +72,9 @@ _SIGS = {
     "vdamp_last_sure": (_I, [_P, _I, _P, _P]),
 }
 
-VDAMP_TUNING_LEN = 6
-TUNING_FIELDS = ("col_block", "rows_per_cta", "idwt_tile", "dwt_tile", "radix_y", "radix_x")
+VDAMP_TUNING_LEN = 7
+TUNING_FIELDS = ("col_block", "rows_per_cta", "idwt_tile", "dwt_tile", "radix_y", "radix_x",
+                 "wavelet_cluster")
 
 
 class vdamp_group(ctypes.Structure):

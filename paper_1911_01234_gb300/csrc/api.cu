@@ -201,6 +201,8 @@ struct vdamp_plan {
     int idwt_to = 32, dwt_to = 16;     // wavelet tile sides
     size_t smem_col = 0, smem_rows = 0, smem_dwt = 0;  // attributes raised for the tuner's choices
     int radix_var[2] = {0, 0};         // radix plan variant along y, x
+    int wcluster = 0;                  // CTAs of the one-launch wavelet cluster (0: unavailable)
+    int use_wcluster = 0;              // tuning: all scales in one cluster launch (small batches)
     int num_sms = 152;
     float* ey = nullptr;
     float* ex = nullptr;
@@ -483,6 +485,15 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
             cudaGetLastError();  // clear a refusal before trying the smaller cluster
         }
     }
+    // one cluster per slice for all wavelet scales (16 CTAs, else 8)
+    for (int C : {16, 8}) {
+        int nclus = 0;
+        if (vdamp::configure_wavelet_cluster(C, p->smem_dwt, &nclus) == cudaSuccess && nclus > 0) {
+            p->wcluster = C;
+            break;
+        }
+        cudaGetLastError();
+    }
     *out = p;
     return VDAMP_OK;
 }
@@ -566,11 +577,23 @@ SrcSpec make_src(const vdamp_plan* p, int mode, const float2* r) {
     return s;
 }
 
+// The one-launch cluster path: while one cluster per slice leaves SMs free.
+bool wavelet_cluster(const Ctx& c) {
+    const vdamp_plan* p = c.p;
+    return p->wcluster > 0 && p->use_wcluster && c.batch * p->wcluster <= p->num_sms;
+}
+
 // x = Psi^H (src), levels s .. 1
 void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
     vdamp_plan* p = c.p;
     const int s = p->levels;
     const float2* ll_in = nullptr;
+    const bool cl = wavelet_cluster(c);
+    vdamp::WaveletArgs w;
+    if (cl) {
+        memset(&w, 0, sizeof(w));
+        w.levels = s;
+    }
     for (int j = s; j >= 1; --j) {
         vdamp::IdwtArgs a;
         a.ll_in = ll_in;
@@ -593,9 +616,18 @@ void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
         a.src = src;
         a.f = p->filt;
         a.to = p->idwt_to;
+        ll_in = a.out;
+        if (cl) {
+            w.idwt[j - 1] = a;
+            continue;
+        }
         c.pre();
         c.chk(vdamp::launch_idwt_level(a, c.batch, c.st), VDAMP_KERNEL_IDWT);
-        ll_in = a.out;
+    }
+    if (cl) {
+        c.pre();
+        c.chk(vdamp::launch_psi_h_cluster(w, c.batch, p->wcluster, p->smem_dwt, c.st),
+              VDAMP_KERNEL_IDWT);
     }
 }
 
@@ -605,6 +637,12 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
     const int s = p->levels;
     const float2* in = img;
     size_t in_stride = p->N;
+    const bool cl = wavelet_cluster(c);
+    vdamp::WaveletArgs w;
+    if (cl) {
+        memset(&w, 0, sizeof(w));
+        w.levels = s;
+    }
     for (int j = 1; j <= s; ++j) {
         vdamp::DwtArgs a;
         a.in = in;
@@ -628,10 +666,19 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
         a.src = src;
         a.f = p->filt;
         a.to = p->dwt_to;
-        c.pre();
-        c.chk(vdamp::launch_dwt_level(a, c.batch, c.st), VDAMP_KERNEL_DWT);
         in = a.ll_out;
         in_stride = p->N / 4;
+        if (cl) {
+            w.dwt[j - 1] = a;
+            continue;
+        }
+        c.pre();
+        c.chk(vdamp::launch_dwt_level(a, c.batch, c.st), VDAMP_KERNEL_DWT);
+    }
+    if (cl) {
+        c.pre();
+        c.chk(vdamp::launch_psi_cluster(w, c.batch, p->wcluster, p->smem_dwt, c.st),
+              VDAMP_KERNEL_DWT);
     }
 }
 
@@ -1187,6 +1234,7 @@ bool tuning_valid(const vdamp_plan* p, const int* t) {
     if (rpc < 1 || rpc > 8 || 2 * (size_t)rpc * p->nx * sizeof(float2) > p->smem_rows) return false;
     if (ito != 16 && ito != 32 && ito != 64) return false;
     if (dto != 16 && dto != 32) return false;
+    if (t[6] != 0 && t[6] != 1) return false;
     if (vdamp::idwt_tile_smem(ito, p->filt.L) > p->smem_dwt ||
         vdamp::dwt_tile_smem(dto, p->filt.L) > p->smem_dwt)
         return false;
@@ -1204,6 +1252,7 @@ void get_tuning(const vdamp_plan* p, int* t) {
     t[3] = p->dwt_to;
     t[4] = p->radix_var[0];
     t[5] = p->radix_var[1];
+    t[6] = p->use_wcluster;
 }
 
 void apply_tuning(vdamp_plan* p, const int* t) {
@@ -1214,6 +1263,7 @@ void apply_tuning(vdamp_plan* p, const int* t) {
     p->dwt_to = t[3];
     p->radix_var[0] = t[4];
     p->radix_var[1] = t[5];
+    p->use_wcluster = t[6];
     fft_radices(p->ny, p->axy.radix, &p->axy.nstages, t[4]);
     fft_radices(p->nx, p->axx.radix, &p->axx.nstages, t[5]);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);  // they hold the old launch shapes
@@ -1318,15 +1368,16 @@ extern "C" vdamp_status vdamp_plan_autotune(vdamp_plan* p, int batch, int trials
         return cudaEventElapsedTime(ms, e0, e1);
     };
     // coordinate descent over (cb, rpc, idwt tile, dwt tile, radix plan y, radix plan x)
-    static const int choices[6][4] = {{2, 4, 8, 16}, {1, 2, 4, 8}, {16, 32, 64, 0},
-                                      {16, 32, 0, 0}, {0, 1, 2, -1}, {0, 1, 2, -1}};
-    int best[6];
+    static const int choices[7][4] = {{2, 4, 8, 16}, {1, 2, 4, 8}, {16, 32, 64, 0},
+                                      {16, 32, 0, 0}, {0, 1, 2, -1}, {0, 1, 2, -1},
+                                      {0, 1, -1, -1}};
+    int best[7];
     get_tuning(p, best);
     float best_ms = 0.f;
     A(trial(best, &best_ms));
-    for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
+    for (int q = 0; q < 7 && e == cudaSuccess; ++q) {
         for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
-            int cand[6];
+            int cand[7];
             std::memcpy(cand, best, sizeof(cand));
             cand[q] = choices[q][c];
             if (cand[q] == best[q] || !tuning_valid(p, cand)) continue;

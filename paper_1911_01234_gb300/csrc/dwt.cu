@@ -1,6 +1,10 @@
 // Orthonormal periodic 2D wavelet transform Psi and its adjoint Psi^H
 // (Sec. 1, Eq. 5-6), one scale per launch; the tile code is in dwt_dev.cuh.
+#include <cooperative_groups.h>
+
 #include "dwt_dev.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace vdamp {
 
@@ -46,6 +50,97 @@ cudaError_t launch_line8(const Line8Args& a, int batch, cudaStream_t st) {
     int blocks = (int)((a.N + 255) / 256);
     if (blocks > 1024) blocks = 1024;
     return launch_pdl(line8_kernel, dim3(blocks, batch), dim3(256), 0, st, a);
+}
+
+// ------------------------------------------------ one launch for all scales ---
+// Every CTA of a cluster runs the same scale loop and the same number of
+// cluster barriers (the control flow depends only on launch arguments).
+__global__ void __launch_bounds__(256) psi_h_cluster_kernel(const __grid_constant__ WaveletArgs w) {
+    extern __shared__ float2 sm[];
+    cudaGridDependencySynchronize();
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks(), slice = blockIdx.y;
+    for (int j = w.levels; j >= 1; --j) {
+        const IdwtArgs& a = w.idwt[j - 1];
+        const int ntx = (2 * a.w + a.to - 1) / a.to, nty = (2 * a.h + a.to - 1) / a.to;
+        for (int t = rank; t < ntx * nty; t += C) {
+            idwt_tile(a, a.out, a.src, t % ntx, t / ntx, slice, sm);
+            __syncthreads();
+        }
+        if (j > 1) cl.sync();   // the next scale reads this scale's LL image
+    }
+}
+
+__global__ void __launch_bounds__(256) psi_cluster_kernel(const __grid_constant__ WaveletArgs w) {
+    extern __shared__ float2 sm[];
+    cudaGridDependencySynchronize();
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks(), slice = blockIdx.y;
+    for (int j = 1; j <= w.levels; ++j) {
+        const DwtArgs& a = w.dwt[j - 1];
+        const int Ho = a.H >> 1, Wo = a.W >> 1;
+        const int ntx = (Wo + a.to - 1) / a.to, nty = (Ho + a.to - 1) / a.to;
+        for (int t = rank; t < ntx * nty; t += C) {
+            dwt_tile(a, a.in, a.packed, a.src, t % ntx, t / ntx, slice, sm);
+            __syncthreads();
+        }
+        if (j < w.levels) cl.sync();   // the next scale reads this scale's LL image
+    }
+}
+
+template <typename K>
+static cudaError_t launch_cluster(K kern, const WaveletArgs& w, int batch, int cluster,
+                                  size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster, batch, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, w);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_psi_h_cluster(const WaveletArgs& w, int batch, int cluster, size_t smem,
+                                 cudaStream_t st) {
+    return launch_cluster(psi_h_cluster_kernel, w, batch, cluster, smem, st);
+}
+
+cudaError_t launch_psi_cluster(const WaveletArgs& w, int batch, int cluster, size_t smem,
+                               cudaStream_t st) {
+    return launch_cluster(psi_cluster_kernel, w, batch, cluster, smem, st);
+}
+
+cudaError_t configure_wavelet_cluster(int cluster, size_t smem, int* max_clusters) {
+    for (auto k : {psi_h_cluster_kernel, psi_cluster_kernel}) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        if (cluster > 8) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(max_clusters, psi_h_cluster_kernel, &cfg);
 }
 
 cudaError_t configure_dwt(size_t smem_bytes) {

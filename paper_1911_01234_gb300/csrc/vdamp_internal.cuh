@@ -241,6 +241,20 @@ cudaError_t configure_col_pass(size_t smem_bytes);
 cudaError_t configure_fft_rows(size_t smem_bytes);
 cudaError_t configure_sure(size_t smem_bytes);
 cudaError_t configure_dwt(size_t smem_bytes);
+
+// All scales of Psi^H (levels s .. 1) or of Psi (1 .. s) in one launch: one
+// thread-block cluster of `cluster` CTAs per slice, the tiles of a scale
+// spread over the cluster, a cluster barrier between scales.
+struct WaveletArgs {
+    IdwtArgs idwt[VDAMP_MAX_LEVELS];   // level j at [j - 1]
+    DwtArgs dwt[VDAMP_MAX_LEVELS];
+    int levels;
+};
+cudaError_t configure_wavelet_cluster(int cluster, size_t smem, int* max_clusters);
+cudaError_t launch_psi_h_cluster(const WaveletArgs& w, int batch, int cluster, size_t smem,
+                                 cudaStream_t st);
+cudaError_t launch_psi_cluster(const WaveletArgs& w, int batch, int cluster, size_t smem,
+                               cudaStream_t st);
 void set_last_error(const char* msg);  // text returned by vdamp_last_error()
 
 }  // namespace vdamp

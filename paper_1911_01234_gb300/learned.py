@@ -264,12 +264,13 @@ class SubbandCNN:
 
 # ------------------------------------------------------------ training ---
 
-def make_pairs(ny, nx, wavelet, levels, slices, iters, workload_id=77, stream=None):
-    """Plain VDAMP (this library) on seeded phantoms of the 256x256 db4 kind:
-    returns (R [pairs][N] complex64, W0 [slices][N], TAU [pairs][B], slice of each pair)."""
+def make_pairs(ny, nx, wavelet, levels, slices, iters, workload_id=77, rate=5.0, stream=None):
+    """Plain VDAMP (this library) on seeded phantoms of the given kind (20 textured
+    ellipses, 24x24 centre, 30 dB, undersampling `rate`): returns (R [pairs][N]
+    complex64, W0 [slices][N], TAU [pairs][B], slice of each pair)."""
     import torch
     wl = synth.Workload("training phantoms", workload_id, ny, nx, 20, True, wavelet, levels,
-                        5.0, 5.0, 24, 30.0, 30.0, iters, 1)
+                        rate, rate, 24, 30.0, 30.0, iters, 1)
     plan = vb.Plan(ny, nx, wavelet, levels)
     N, B = ny * nx, plan.B
     R = torch.empty((slices * iters, N), dtype=torch.complex64, device="cuda")
@@ -436,21 +437,29 @@ def train_default(slices=52, iters=30, steps=1500, seed=0, log_every=100, timing
     (52 phantoms x 30 iterations x 13 subbands) from plain VDAMP, then Adam on
     32x32 patches (8 per subband and step).  Returns the network and the
     loss history."""
+    return train_for(256, 256, "db4", 4, 5.0, slices, iters, steps, 77, seed, log_every,
+                     timings)
+
+
+def train_for(ny, nx, wavelet, levels, rate, slices, iters, steps=1500, workload_id=77, seed=0,
+              log_every=100, timings=None):
+    """A denoiser for slices of one kind: slices x iters x (1 + 3 levels) subband
+    pairs from plain VDAMP on seeded phantoms (seed `workload_id`), then Adam."""
     import time
 
     import torch
     t0 = time.perf_counter()
-    R, W0, TAU, owner = make_pairs(256, 256, "db4", 4, slices, iters)
+    R, W0, TAU, owner = make_pairs(ny, nx, wavelet, levels, slices, iters, workload_id, rate)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    net = SubbandCNN(bands=13, seed=seed)
-    hist = train(net, R, W0, TAU, owner, 256, 256, 4, steps=steps, seed=seed,
+    net = SubbandCNN(bands=1 + 3 * levels, seed=seed)
+    hist = train(net, R, W0, TAU, owner, ny, nx, levels, steps=steps, seed=seed,
                  log_every=log_every)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     if timings is not None:
         timings.update({"pairs_s": t1 - t0, "train_s": t2 - t1,
-                        "pairs": int(R.shape[0]) * 13, "steps": steps})
+                        "pairs": int(R.shape[0]) * (1 + 3 * levels), "steps": steps})
     _TGT.clear()
     del R, W0, TAU
     return net, hist
