@@ -189,9 +189,16 @@ def algorithmic_bytes(kind, N, n, levels):
     return 0.0
 
 
-# Measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum per launch)
-# on the kernel build named by its source hash; None when the source changed.
-MEASURED_TRAFFIC = {}
+# Measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum per launch,
+# mean over the launches of one iteration of the 256x256 db4 s=4 workload:
+# 4 scales for idwt and dwt, the sort + search pair for sure) on the kernel
+# build named by its source hash; ignored (traffic null) once the source changed.
+# ncu replays each launch with cold caches, and a launch's writes stay in L2.
+MEASURED_TRAFFIC = {
+    "idwt": {"bytes_per_launch": 270848, "source": "79f5458322d9b998"},
+    "dwt": {"bytes_per_launch": 376384, "source": "79f5458322d9b998"},
+    "sure": {"bytes_per_launch": 951808, "source": "79f5458322d9b998"},
+}
 
 
 def slowest_rank_ms(local_ms, world, device=None):

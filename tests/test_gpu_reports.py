@@ -25,9 +25,10 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import cnn_oracle as C
 from oracle import vdamp_oracle as O
 from paper_1911_01234_gb300 import binding as vb
-from paper_1911_01234_gb300 import build, diagnostics, synth
+from paper_1911_01234_gb300 import build, diagnostics, learned, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -147,6 +148,56 @@ def test_precision_report():
     rep["transforms at 256x256 (db4 s=4)"] = tr
     assert max(tr.values()) < 2e-6
     plan.close()
+
+    # ---- the learned denoiser (BF16 weights and activations, FP32 accumulation):
+    # its output n, the residual denoiser f and the JVP on the subbands of one
+    # 256x256 slice's r_k, against the FP64 oracle with the same weights, both
+    # as plain FP64 (the whole BF16 error) and with BF16 storage reproduced
+    # (the kernels' own error)
+    rng = np.random.default_rng(11)
+    net = learned.SubbandCNN(13, seed=3)
+    with torch.no_grad():
+        for l in range(5):
+            net.b[l].copy_(torch.from_numpy(
+                (rng.standard_normal(net.b[l].shape) * 0.05).astype(np.float32)))
+        net.w[4].mul_(10.0)
+        net.w[4][:, 2:] = 0
+        net.b[4][:, 2:] = 0
+    net.pack()
+    im = learned.Images.subbands(256, 256, 4, 1)
+    rk = dev(res.records[5].r.astype(np.complex64)[None])
+    tk = dev(res.records[5].tau[None])
+    f = torch.zeros_like(rk)
+    sums = torch.zeros(2 * im.n, dtype=torch.float64, device="cuda")
+    net.denoise(im, rk, tk, 13, 5, f, sums)
+    n_g = net._ws["n"].cpu().numpy()[:2 * 65536].reshape(-1, 2)     # [pixel][2]
+    jn_g = net._ws["jn"].cpu().numpy()[:2 * 65536].reshape(-1, 2)
+    f_g = f.cpu().numpy()[0]
+    err = {"n (rel L2, vs FP64)": 0.0, "n (rel L2, vs BF16-storage oracle)": 0.0,
+           "f (rel L2, vs FP64)": 0.0, "J_n eta (rel L2, vs BF16-storage oracle)": 0.0}
+    r64 = res.records[5].r
+    for b, sb in enumerate(diagnostics.subband_layout(256, 256, 4)):
+        h, w, o = sb["h"], sb["w"], sb["offset"]
+        rb = r64[o:o + h * w].astype(np.complex64).astype(np.complex128).reshape(h, w)
+        t = float(res.records[5].tau[b])
+        params = net.oracle_params(b)
+        f64, n64, _ = C.denoise(params, rb, t)
+        f16, n16, a16 = C.denoise(params, rb, t, bf16=True)
+        ng = n_g[o:o + h * w].reshape(h, w, 2)
+        err["n (rel L2, vs FP64)"] = max(err["n (rel L2, vs FP64)"], rel(ng, n64))
+        err["n (rel L2, vs BF16-storage oracle)"] = max(err["n (rel L2, vs BF16-storage oracle)"],
+                                                       rel(ng, n16))
+        err["f (rel L2, vs FP64)"] = max(err["f (rel L2, vs FP64)"],
+                                         rel(f_g[o:o + h * w].reshape(h, w), f64))
+        keys = np.arange(o, o + h * w).reshape(h, w)
+        eta = np.stack([C.rademacher(5, keys, 0), C.rademacher(5, keys, 1)], -1)
+        t0 = np.concatenate([eta, np.zeros((h, w, 1))], -1)
+        err["J_n eta (rel L2, vs BF16-storage oracle)"] = max(
+            err["J_n eta (rel L2, vs BF16-storage oracle)"],
+            rel(jn_g[o:o + h * w].reshape(h, w, 2), C.jvp(params, a16, t0, bf16=True)))
+    rep["learned denoiser on the 13 subbands of r_5 (256x256 db4), BF16 network"] = err
+    assert err["n (rel L2, vs BF16-storage oracle)"] < 2e-2
+    assert err["f (rel L2, vs FP64)"] < 1e-2
 
     md = ["| result | largest error vs the FP64 oracle |", "|---|---|"]
     for sec, vals in rep.items():
