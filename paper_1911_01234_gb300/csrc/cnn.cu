@@ -30,11 +30,20 @@ constexpr int CONV_STAGES = 4;   // halo buffers: the current tile and three in 
 // modes, the mask rows) of the next tile arrive by cp.async (zero-filled
 // outside the image) while the current tile's MMAs and epilogue run; weights
 // and bias are staged once per band.
+// Where a tile sits: its image (dense offset, size, band) and its block
+// (pitch, width, rows, the image pixel of halo position (0, 0)).
+struct ConvTile {
+    int off, h, w, band, pitch, wb, rows, y0, x0;
+};
+
+constexpr int CONV_THREADS = 256;   // 128 output rows x 2 halves of the output channels
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ ConvArgs a) {
+__global__ void __launch_bounds__(CONV_THREADS) conv3x3_kernel(const __grid_constant__ ConvArgs a) {
     constexpr int K = 9 * CIN;
     constexpr int NCH = CIN / 8;
     constexpr int KPT = CIN / 16;   // K steps per tap
+    constexpr int HC = COUT / 2;    // output channels per thread
     constexpr int B_BYTES = COUT * K * 2;
     constexpr int M_BYTES = 128 * COUT * 2;
     constexpr uint32_t SBO_B = (K / 8) * 128, LBO_B = 128;
@@ -44,6 +53,7 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ Co
     __shared__ uint32_t tbase;
     __shared__ float s_bias[2][COUT];   // bias of the current band and of the next one
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & 127, half = tid >> 7;   // output row m and channel half of this thread
     const int nq = a.nq;
     const uint32_t CS = (uint32_t)nq * 16;
     const uint32_t A_BYTES = NCH * CS;
@@ -69,48 +79,59 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ Co
     tc::fence_after_sync();
     const uint32_t tmem = tbase;
 
-    // asynchronous loads of tile t into stage st (one commit group); tiles come
-    // in increasing order, so the image is found by stepping from the last one
-    // (one binary search per CTA, not one per tile)
+    // Tiles come in increasing order: the image is found by stepping from the
+    // last one (one binary search per CTA) and its block shape is recomputed
+    // only when the image changes.
     int load_idx = find_conv_image(a.img, a.n_img, t_begin);
-    auto issue_loads = [&](int t, int st) -> CnnImage {
-        while (load_idx + 1 < a.n_img && a.img[load_idx + 1].ctile0 <= t) ++load_idx;
-        const CnnImage im = a.img[load_idx];
+    CnnImage lim = a.img[load_idx];
+    ConvBlock lcb = conv_block(lim.h, lim.w);
+    auto locate = [&](int t) -> ConvTile {
+        bool moved = false;
+        while (load_idx + 1 < a.n_img && __ldg(&a.img[load_idx + 1].ctile0) <= t) {
+            ++load_idx;
+            moved = true;
+        }
+        if (moved) {
+            lim = a.img[load_idx];
+            lcb = conv_block(lim.h, lim.w);
+        }
+        const int ti = t - lim.ctile0, by = ti / lcb.nbx, bx = ti - by * lcb.nbx;
+        return ConvTile{lim.off, lim.h, lim.w, lim.band, lcb.pitch, lcb.wb, lcb.rows,
+                        by * lcb.rows - 1, bx * lcb.wb - 1};
+    };
+    // asynchronous loads of a tile's halo (and mask rows) into stage st (one commit group)
+    auto issue_loads = [&](const ConvTile& ct, int st) {
         uint8_t* sA = sA0 + st * A_BYTES;
-        const ConvBlock cb = conv_block(im.h, im.w);
-        const int ti = t - im.ctile0, by = ti / cb.nbx, bx = ti - by * cb.nbx;
-        const int y0 = by * cb.rows - 1, x0 = bx * cb.wb - 1;   // image pixel of halo (0, 0)
-        const int P = cb.pitch, nqi = conv_halo(P);
-        const __nv_bfloat16* base = a.in + (size_t)im.off * CIN;
-        for (int q = tid; q < nqi; q += 128) {
+        const int P = ct.pitch, nqi = conv_halo(P);
+        const __nv_bfloat16* base = a.in + (size_t)ct.off * CIN;
+        for (int q = tid; q < nqi; q += CONV_THREADS) {
             const int i = q / P, j = q - i * P;
-            const int y = y0 + i, x = x0 + j;
-            const bool inb = y >= 0 && y < im.h && x >= 0 && x < im.w;
-            const __nv_bfloat16* src = inb ? base + (size_t)(y * im.w + x) * CIN : base;
+            const int y = ct.y0 + i, x = ct.x0 + j;
+            const bool inb = y >= 0 && y < ct.h && x >= 0 && x < ct.w;
+            const __nv_bfloat16* src = inb ? base + (size_t)(y * ct.w + x) * CIN : base;
 #pragma unroll
             for (int c = 0; c < NCH; ++c)
                 tc::cp_async16(sA + c * CS + (uint32_t)q * 16, src + 8 * c, inb ? 16u : 0u);
         }
-        if (masked) {
-            const int q = P + 1 + tid, i = q / P, j = q - i * P;
-            const int y = y0 + i, x = x0 + j;
-            const bool ok = i <= cb.rows && j >= 1 && j <= cb.wb && y < im.h && x < im.w;
+        if (masked) {   // the mask row of output m: half of it per thread
+            const int q = P + 1 + row, i = q / P, j = q - i * P;
+            const int y = ct.y0 + i, x = ct.x0 + j;
+            const bool ok = i <= ct.rows && j >= 1 && j <= ct.wb && y < ct.h && x < ct.w;
             const __nv_bfloat16* src =
-                ok ? a.mask + ((size_t)im.off + (size_t)y * im.w + x) * COUT : a.mask;
-            uint8_t* dst = sM0 + st * M_BYTES + tid * COUT * 2;
+                ok ? a.mask + ((size_t)ct.off + (size_t)y * ct.w + x) * COUT + half * HC : a.mask;
+            uint8_t* dst = sM0 + st * M_BYTES + row * COUT * 2 + half * HC * 2;
 #pragma unroll
-            for (int c = 0; c < COUT / 8; ++c) tc::cp_async16(dst + 16 * c, src + 8 * c, ok ? 16u : 0u);
+            for (int c = 0; c < HC / 8; ++c) tc::cp_async16(dst + 16 * c, src + 8 * c, ok ? 16u : 0u);
         }
         tc::cp_async_commit();
-        return im;
     };
     auto load_band = [&](int band, int slot) {   // synchronous: no MMA may be in flight
         const uint4* src = reinterpret_cast<const uint4*>(a.wimg + (size_t)band * COUT * K);
-        for (int i = tid; i < B_BYTES / 16; i += 128) reinterpret_cast<uint4*>(sB)[i] = src[i];
+        for (int i = tid; i < B_BYTES / 16; i += CONV_THREADS) reinterpret_cast<uint4*>(sB)[i] = src[i];
         if (tid < COUT) s_bias[slot][tid] = a.bias ? a.bias[(size_t)band * COUT + tid] : 0.f;
     };
-    auto issue_mma = [&](const CnnImage& im, int st, int acc) {   // one thread
-        const int W2 = conv_block(im.h, im.w).pitch;
+    auto issue_mma = [&](const ConvTile& ct, int st, int acc) {   // one thread
+        const int W2 = ct.pitch;
         const uint32_t abase = tc::smem_u32(sA0 + st * A_BYTES);
         const uint32_t bbase = tc::smem_u32(sB);
 #pragma unroll
@@ -128,19 +149,25 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ Co
     constexpr int D = CONV_STAGES - 1;   // tiles in flight ahead of the current one
     uint32_t phase[2] = {0, 0};
     bool ok = true, pending[2] = {false, false};
+    bool timed_out = false;   // this thread's MMA wait ran out (made uniform at the next barrier)
     // tiles t_begin .. t_begin + D - 1 into stages 0 .. D - 1; every iteration t
     // then refills the stage of tile t - 1 with tile t + D
-    CnnImage cur = issue_loads(t_begin, 0);
-    CnnImage ahead[D - 1];               // at iteration t: images of tiles t + 1 .. t + D - 1
+    ConvTile cur = locate(t_begin);
+    issue_loads(cur, 0);
+    ConvTile ahead[D - 1];               // at iteration t: tiles t + 1 .. t + D - 1
 #pragma unroll
     for (int d = 1; d < D; ++d) {
         ahead[d - 1] = cur;              // defined even past the range (then never used)
-        if (t_begin + d < t_end) ahead[d - 1] = issue_loads(t_begin + d, d);
-        else tc::cp_async_commit();      // empty group: the group count stays aligned
+        if (t_begin + d < t_end) {
+            ahead[d - 1] = locate(t_begin + d);
+            issue_loads(ahead[d - 1], d);
+        } else {
+            tc::cp_async_commit();       // empty group: the group count stays aligned
+        }
     }
     int band = cur.band, bslot = 0;
     load_band(band, 0);
-    tc::cp_async_wait<D - 1>();          // tile t_begin has landed
+    tc::cp_async_wait<D - 2>();          // tile t_begin has landed
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -156,15 +183,9 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ Co
         const int k = t - t_begin, ac = k & 1;
         const int st = k % CONV_STAGES;
         const bool more = t + 1 < t_end;
-        // the stage of tile t - 1 is free (its MMAs and epilogue are done): refill it
-        CnnImage fresh = cur;
-        if (t + D < t_end) fresh = issue_loads(t + D, (k + D) % CONV_STAGES);
-        else tc::cp_async_commit();
-        const CnnImage nxt = ahead[0];
-#pragma unroll
-        for (int d = 0; d + 2 < D; ++d) ahead[d] = ahead[d + 1];
-        ahead[D - 2] = fresh;
-        tc::cp_async_wait<D - 1>();   // tile t + 1 has landed (t + 2 .. t + D may still fly)
+        const ConvTile nxt = ahead[0];
+        // tile t + 1 has landed (t + 2 .. t + D - 1 may still fly; t + D is issued below)
+        tc::cp_async_wait<D - 2>();
         const bool new_band = more && nxt.band != band;
         if (new_band) {
             // the weights change: the tensor cores must be done with tile t first
@@ -175,7 +196,11 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ Co
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
-        __syncthreads();
+        // every thread is past the epilogue of tile t - 1; a wait that ran out stops all
+        if (__syncthreads_or(timed_out)) {
+            ok = false;
+            break;
+        }
         if (more) {
             if (tid == 0) {
                 tc::fence_after_sync();
@@ -183,50 +208,84 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __grid_constant__ Co
             }
             pending[ac ^ 1] = true;
         }
-        if (!new_band) {
-            ok = __syncthreads_and(tc::mbar_wait(&mbar[ac], phase[ac], kWaitLimit)) != 0;
-            if (!ok) break;
+        // the stage of tile t - 1 is free (its MMAs and epilogue are done): refill it
+        ConvTile fresh = cur;
+        if (t + D < t_end) {
+            fresh = locate(t + D);
+            issue_loads(fresh, (k + D) % CONV_STAGES);
+        } else {
+            tc::cp_async_commit();
+        }
+#pragma unroll
+        for (int d = 0; d + 2 < D; ++d) ahead[d] = ahead[d + 1];
+        ahead[D - 2] = fresh;
+        if (!new_band && !tc::mbar_wait(&mbar[ac], phase[ac], kWaitLimit)) {
+            timed_out = true;   // each warp waits on its own; the outcome meets at the next barrier
+            continue;
         }
         phase[ac] ^= 1;
         pending[ac] = false;
         tc::fence_after_sync();
-        float acc[COUT];
-        const uint32_t ta = tmem + ac * 32 + ((uint32_t)(warp * 32) << 16);
-        if (COUT == 32) tc::tmem_ld32(ta, acc);
-        else tc::tmem_ld16(ta, acc);
-        const ConvBlock cb = conv_block(cur.h, cur.w);
-        const int ti = t - cur.ctile0, by = ti / cb.nbx, bx = ti - by * cb.nbx;
-        const int q = cb.pitch + 1 + tid, bi = q / cb.pitch, bj = q - bi * cb.pitch;
-        const int oy = by * cb.rows - 1 + bi, ox = bx * cb.wb - 1 + bj;
-        if (bi <= cb.rows && bj >= 1 && bj <= cb.wb && oy < cur.h && ox < cur.w) {
+        // epilogue: this thread's row m = row, channels [half HC, half HC + HC)
+        float acc[HC];
+        const uint32_t ta = tmem + ac * 32 + half * HC + ((uint32_t)((warp & 3) * 32) << 16);
+        if (HC == 16) tc::tmem_ld16(ta, acc);
+        else tc::tmem_ld8(ta, acc);
+        const int q = cur.pitch + 1 + row, bi = q / cur.pitch, bj = q - bi * cur.pitch;
+        const int oy = cur.y0 + bi, ox = cur.x0 + bj;
+        if (bi <= cur.rows && bj >= 1 && bj <= cur.wb && oy < cur.h && ox < cur.w) {
             const size_t p = (size_t)cur.off + (size_t)oy * cur.w + ox;
+            const float* bs = s_bias[bslot] + half * HC;
             if (a.mode == CONV_BIAS_RELU || masked) {
-                const __nv_bfloat16* mk =
-                    reinterpret_cast<const __nv_bfloat16*>(sM0 + st * M_BYTES + tid * COUT * 2);
-                uint4 ov[COUT / 8];
-                __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ov);
+                uint32_t mk[HC / 2];
+                if (masked) {
+                    const uint4* ms = reinterpret_cast<const uint4*>(sM0 + st * M_BYTES +
+                                                                     row * COUT * 2 + half * HC * 2);
 #pragma unroll
-                for (int c = 0; c < COUT; ++c) {
-                    float v = acc[c];
-                    if (!masked) v = fmaxf(v + s_bias[bslot][c], 0.f);
-                    else v = __bfloat162float(mk[c]) > 0.f ? v : 0.f;
-                    o[c] = __float2bfloat16_rn(v);
+                    for (int c = 0; c < HC / 8; ++c) {
+                        const uint4 v = ms[c];
+                        mk[4 * c] = v.x;
+                        mk[4 * c + 1] = v.y;
+                        mk[4 * c + 2] = v.z;
+                        mk[4 * c + 3] = v.w;
+                    }
+                }
+                uint32_t pk[HC / 2];
+#pragma unroll
+                for (int c = 0; c < HC / 2; ++c) {
+                    float v0 = acc[2 * c], v1 = acc[2 * c + 1];
+                    if (!masked) {
+                        v0 = fmaxf(v0 + bs[2 * c], 0.f);
+                        v1 = fmaxf(v1 + bs[2 * c + 1], 0.f);
+                    } else {   // keep where the mask's bfloat16 is > 0 (sign bit clear, not zero)
+                        const uint32_t m2 = mk[c];
+                        const uint32_t lo = m2 & 0xFFFFu, hi = m2 >> 16;
+                        v0 = (lo != 0u && !(lo & 0x8000u)) ? v0 : 0.f;
+                        v1 = (hi != 0u && !(hi & 0x8000u)) ? v1 : 0.f;
+                    }
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                    pk[c] = *reinterpret_cast<const uint32_t*>(&b2);
                 }
                 uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) +
-                                                      p * COUT);
+                                                      p * COUT + half * HC);
 #pragma unroll
-                for (int c = 0; c < COUT / 8; ++c) dst[c] = ov[c];
+                for (int c = 0; c < HC / 8; ++c)
+                    dst[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
             } else {
                 float* dst = reinterpret_cast<float*>(a.out) + p * a.cout_store;
-                for (int c = 0; c < a.cout_store; ++c)
-                    dst[c] = acc[c] + (a.mode == CONV_BIAS_F32 ? s_bias[bslot][c] : 0.f);
+#pragma unroll
+                for (int c = 0; c < HC; ++c) {
+                    const int ch = half * HC + c;
+                    if (ch < a.cout_store)
+                        dst[ch] = acc[c] + (a.mode == CONV_BIAS_F32 ? bs[c] : 0.f);
+                }
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();   // accumulator ac and this tile's stage are free again
+        tc::fence_before_sync();   // the accumulator reads happen before the next barrier
         if (new_band) bslot ^= 1;
         cur = nxt;
     }
+    if (ok && __syncthreads_or(timed_out)) ok = false;   // the last tile's wait
     if (!ok) {
         // a wait ran out: record it, give the MMAs in flight one more bounded
         // wait, then free the tensor memory as on the normal path
@@ -583,7 +642,7 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t st) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(a.total_tiles, 2 * sms);
     if (grid < 1) return cudaSuccess;
-    return launch_pdl(conv3x3_kernel<CIN, COUT>, dim3(grid), dim3(128), smem, st, a);
+    return launch_pdl(conv3x3_kernel<CIN, COUT>, dim3(grid), dim3(CONV_THREADS), smem, st, a);
 }
 
 }  // namespace
