@@ -195,9 +195,9 @@ def algorithmic_bytes(kind, N, n, levels):
 # build named by its source hash; ignored (traffic null) once the source changed.
 # ncu replays each launch with cold caches, and a launch's writes stay in L2.
 MEASURED_TRAFFIC = {
-    "idwt": {"bytes_per_launch": 270848, "source": "79f5458322d9b998"},
-    "dwt": {"bytes_per_launch": 376384, "source": "79f5458322d9b998"},
-    "sure": {"bytes_per_launch": 951808, "source": "79f5458322d9b998"},
+    "idwt": {"bytes_per_launch": 270848, "source": "5608ced965739e72"},
+    "dwt": {"bytes_per_launch": 376384, "source": "5608ced965739e72"},
+    "sure": {"bytes_per_launch": 951808, "source": "5608ced965739e72"},
 }
 
 
@@ -218,74 +218,16 @@ def job_throughput(world, steps, iters_per_step, slices_per_rank, max_ms):
 
 
 def source_hash():
+    """Hash of the sources the plain path's kernels are built from (the learned
+    denoiser's files excluded): measured traffic stays valid while they are unchanged."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1911_01234_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in ("api.cu", "dwt.cu", "dwt_dev.cuh", "fft.cu", "fft_dev.cuh", "sure.cu",
+              "sure_dev.cuh", "vdamp_internal.cuh"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
-
-
-def run_batched(args, vb, torch, flush_buf, stream):
-    """Batched workload: 256 slices of 320x320, db4 s=5, R=6, 30 dB, 20 iterations."""
-    wl = synth.BATCH_320_DB4_5
-    nb = args.batched_slices
-    probs = [synth.make_problem(wl, i) for i in range(nb)]
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
-    y, m, p = dev([q.y for q in probs]), dev([q.mask for q in probs]), dev([q.density for q in probs])
-    sig = [q.sigma for q in probs]
-    n_samp = int(sum(int(q.mask.sum()) for q in probs))
-    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
-    if args.path != "auto":
-        vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 1 if args.path == "fused" else 0)
-    tuning = None if args.no_autotune else plan.autotune(nb, trials=3, stream=stream.cuda_stream)
-    K = wl.iters
-    x_hat = torch.empty((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
-    tau = torch.empty((nb, K, plan.B), dtype=torch.float64, device="cuda")
-    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
-
-    def step():
-        vb.vdamp_solve(plan.handle, nb, y, m, p, sig, K, None, x_hat, tau, thr, alpha,
-                       stream=stream.cuda_stream)
-    for i in range(2):
-        flush_buf.fill_(float(i))
-        step()
-    torch.cuda.synchronize()
-    steps = args.batched_steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    for i in range(steps):
-        flush_buf.fill_(float(i))
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if vb.vdamp_device_status(plan.handle)[0] != vb.VDAMP_OK:
-        raise RuntimeError("batched solve reported a non-finite tau or alpha")
-    # dominant kernel over one timed solve
-    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 1)
-    vb.vdamp_kernel_times(plan.handle)
-    step()
-    kt = vb.vdamp_kernel_times(plan.handle)
-    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 0)
-    dom = max((k for k in kt if kt[k][1] > 0 and k != "other"), key=lambda k: kt[k][0])
-    avg_s = kt[dom][0] / kt[dom][1] / 1e3
-    N = wl.ny * wl.nx
-    byt = nb * algorithmic_bytes(dom, N, n_samp / nb, wl.levels) if dom != "fused" else \
-        nb * K * (16 * N + 12 * n_samp / nb + N / 8)
-    hbm, src = peaks()
-    plan.close()
-    return {"workload": wl.name, "slices": nb, "iters": K, "steps": steps,
-            "value": nb * K * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
-            "tuning": tuning,
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": byt / avg_s / 1e9,
-                         "peak": hbm, "peak_source": src, "unit": "GB/s",
-                         "frac": byt / avg_s / 1e9 / hbm, "avg_launch_us": avg_s * 1e6,
-                         "algorithmic_bytes_per_launch": byt,
-                         "time_share": {k: round(v[0] / sum(x[0] for x in kt.values()), 4)
-                                        for k, v in kt.items()}}}
 
 
 def run_mixed(args, vb, torch, flush_buf, stream):
