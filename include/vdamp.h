@@ -126,9 +126,9 @@ int vdamp_last_launch_count(const vdamp_plan* plan);
  *   [3] analysis (Psi) tile side in coefficients: 16 or 32
  *   [4], [5] radix plan of the transform along y and x: 0 = radix 8 first,
  *            1 = radix 4 only, 2 = radix 8 with the radices 3 and 5 first
- *   [6] 1: all scales of Psi (and of Psi^H) in one launch, one thread-block
- *       cluster per slice, while batch x cluster size <= the SM count;
- *       0: one launch per scale
+ *   [6] 1: the scales s .. 2 of Psi (and of Psi^H) in one launch, one
+ *       thread-block cluster per slice, scale 1 in its own launch, while
+ *       batch x cluster size <= the SM count; 0: one launch per scale
  * Every tuning computes the same method; tunings differ in FP32 summation
  * order only (the tau partial sums depend on [0], the DFT on [4], [5]).
  * get copies the current tuning out; set validates and applies one

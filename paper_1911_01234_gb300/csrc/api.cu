@@ -577,10 +577,12 @@ SrcSpec make_src(const vdamp_plan* p, int mode, const float2* r) {
     return s;
 }
 
-// The one-launch cluster path: while one cluster per slice leaves SMs free.
+// The cluster path for the coarse scales s .. 2 (scale 1 keeps its own wide
+// launch): while one cluster per slice leaves SMs free and there are >= 2 scales.
 bool wavelet_cluster(const Ctx& c) {
     const vdamp_plan* p = c.p;
-    return p->wcluster > 0 && p->use_wcluster && c.batch * p->wcluster <= p->num_sms;
+    return p->wcluster > 0 && p->use_wcluster && p->levels >= 2 &&
+           c.batch * p->wcluster <= p->num_sms;
 }
 
 // x = Psi^H (src), levels s .. 1
@@ -593,6 +595,7 @@ void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
     if (cl) {
         memset(&w, 0, sizeof(w));
         w.levels = s;
+        w.lo = 2;
     }
     for (int j = s; j >= 1; --j) {
         vdamp::IdwtArgs a;
@@ -617,17 +620,18 @@ void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
         a.f = p->filt;
         a.to = p->idwt_to;
         ll_in = a.out;
-        if (cl) {
+        if (cl && j >= 2) {
+            a.to = 32;   // one tile pass per CTA and scale up to 128x128 outputs
             w.idwt[j - 1] = a;
+            if (j == 2) {   // the coarse scales in one cluster launch
+                c.pre();
+                c.chk(vdamp::launch_psi_h_cluster(w, c.batch, p->wcluster, p->smem_dwt, c.st),
+                      VDAMP_KERNEL_IDWT);
+            }
             continue;
         }
         c.pre();
         c.chk(vdamp::launch_idwt_level(a, c.batch, c.st), VDAMP_KERNEL_IDWT);
-    }
-    if (cl) {
-        c.pre();
-        c.chk(vdamp::launch_psi_h_cluster(w, c.batch, p->wcluster, p->smem_dwt, c.st),
-              VDAMP_KERNEL_IDWT);
     }
 }
 
@@ -642,6 +646,7 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
     if (cl) {
         memset(&w, 0, sizeof(w));
         w.levels = s;
+        w.lo = 2;
     }
     for (int j = 1; j <= s; ++j) {
         vdamp::DwtArgs a;
@@ -668,14 +673,14 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
         a.to = p->dwt_to;
         in = a.ll_out;
         in_stride = p->N / 4;
-        if (cl) {
+        if (cl && j >= 2) {
             w.dwt[j - 1] = a;
             continue;
         }
         c.pre();
         c.chk(vdamp::launch_dwt_level(a, c.batch, c.st), VDAMP_KERNEL_DWT);
     }
-    if (cl) {
+    if (cl) {   // the coarse scales in one cluster launch
         c.pre();
         c.chk(vdamp::launch_psi_cluster(w, c.batch, p->wcluster, p->smem_dwt, c.st),
               VDAMP_KERNEL_DWT);

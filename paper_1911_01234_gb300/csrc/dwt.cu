@@ -60,14 +60,14 @@ __global__ void __launch_bounds__(256) psi_h_cluster_kernel(const __grid_constan
     cudaGridDependencySynchronize();
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks(), slice = blockIdx.y;
-    for (int j = w.levels; j >= 1; --j) {
+    for (int j = w.levels; j >= w.lo; --j) {
         const IdwtArgs& a = w.idwt[j - 1];
         const int ntx = (2 * a.w + a.to - 1) / a.to, nty = (2 * a.h + a.to - 1) / a.to;
         for (int t = rank; t < ntx * nty; t += C) {
             idwt_tile(a, a.out, a.src, t % ntx, t / ntx, slice, sm);
             __syncthreads();
         }
-        if (j > 1) cl.sync();   // the next scale reads this scale's LL image
+        if (j > w.lo) cl.sync();   // the next scale reads this scale's LL image
     }
 }
 
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) psi_cluster_kernel(const __grid_constant_
     cudaGridDependencySynchronize();
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks(), slice = blockIdx.y;
-    for (int j = 1; j <= w.levels; ++j) {
+    for (int j = w.lo; j <= w.levels; ++j) {
         const DwtArgs& a = w.dwt[j - 1];
         const int Ho = a.H >> 1, Wo = a.W >> 1;
         const int ntx = (Wo + a.to - 1) / a.to, nty = (Ho + a.to - 1) / a.to;

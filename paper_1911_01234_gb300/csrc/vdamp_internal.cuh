@@ -242,13 +242,14 @@ cudaError_t configure_fft_rows(size_t smem_bytes);
 cudaError_t configure_sure(size_t smem_bytes);
 cudaError_t configure_dwt(size_t smem_bytes);
 
-// All scales of Psi^H (levels s .. 1) or of Psi (1 .. s) in one launch: one
-// thread-block cluster of `cluster` CTAs per slice, the tiles of a scale
-// spread over the cluster, a cluster barrier between scales.
+// Scales lo .. s of Psi^H (coarse to fine) or of Psi (fine to coarse) in one
+// launch: one thread-block cluster of `cluster` CTAs per slice, the tiles of a
+// scale spread over the cluster, a cluster barrier between scales.
 struct WaveletArgs {
     IdwtArgs idwt[VDAMP_MAX_LEVELS];   // level j at [j - 1]
     DwtArgs dwt[VDAMP_MAX_LEVELS];
-    int levels;
+    int levels;                        // scales lo .. levels in this launch
+    int lo;
 };
 cudaError_t configure_wavelet_cluster(int cluster, size_t smem, int* max_clusters);
 cudaError_t launch_psi_h_cluster(const WaveletArgs& w, int batch, int cluster, size_t smem,
