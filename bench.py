@@ -230,6 +230,67 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def run_batched(args, vb, torch, flush_buf, stream):
+    """Batched workload: 256 slices of 320x320, db4 s=5, R=6, 30 dB, 20 iterations."""
+    wl = synth.BATCH_320_DB4_5
+    nb = args.batched_slices
+    probs = [synth.make_problem(wl, i) for i in range(nb)]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
+    y, m, p = dev([q.y for q in probs]), dev([q.mask for q in probs]), dev([q.density for q in probs])
+    sig = [q.sigma for q in probs]
+    n_samp = int(sum(int(q.mask.sum()) for q in probs))
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
+    if args.path != "auto":
+        vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 1 if args.path == "fused" else 0)
+    tuning = None if args.no_autotune else plan.autotune(nb, trials=3, stream=stream.cuda_stream)
+    K = wl.iters
+    x_hat = torch.empty((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+    tau = torch.empty((nb, K, plan.B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+
+    def step():
+        vb.vdamp_solve(plan.handle, nb, y, m, p, sig, K, None, x_hat, tau, thr, alpha,
+                       stream=stream.cuda_stream)
+    for i in range(2):
+        flush_buf.fill_(float(i))
+        step()
+    torch.cuda.synchronize()
+    steps = args.batched_steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush_buf.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if vb.vdamp_device_status(plan.handle)[0] != vb.VDAMP_OK:
+        raise RuntimeError("batched solve reported a non-finite tau or alpha")
+    # dominant kernel over one timed solve
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 1)
+    vb.vdamp_kernel_times(plan.handle)
+    step()
+    kt = vb.vdamp_kernel_times(plan.handle)
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 0)
+    dom = max((k for k in kt if kt[k][1] > 0 and k != "other"), key=lambda k: kt[k][0])
+    avg_s = kt[dom][0] / kt[dom][1] / 1e3
+    N = wl.ny * wl.nx
+    byt = nb * algorithmic_bytes(dom, N, n_samp / nb, wl.levels) if dom != "fused" else \
+        nb * K * (16 * N + 12 * n_samp / nb + N / 8)
+    hbm, src = peaks()
+    plan.close()
+    return {"workload": wl.name, "slices": nb, "iters": K, "steps": steps,
+            "value": nb * K * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "tuning": tuning,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": byt / avg_s / 1e9,
+                         "peak": hbm, "peak_source": src, "unit": "GB/s",
+                         "frac": byt / avg_s / 1e9 / hbm, "avg_launch_us": avg_s * 1e6,
+                         "algorithmic_bytes_per_launch": byt,
+                         "time_share": {k: round(v[0] / sum(x[0] for x in kt.values()), 4)
+                                        for k, v in kt.items()}}}
+
+
 def run_mixed(args, vb, torch, flush_buf, stream):
     """Mixed-size batch: 32 slices each of 128x128, 256x256 and 384x320 (db4 s=4,
     per-slice R ~ U[3, 8] and SNR ~ U[25, 40] dB, 30 iterations) as one grouped
