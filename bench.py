@@ -610,6 +610,10 @@ def run_gpu(args):
                         "d2h_bytes_per_step": d2h},
                 "roofline": roofline,
                 "wall_s_timed": wall}
+        # the batched, mixed and learned measurements are single-GPU blocks: at
+        # N > 1 the line holds the replicated solve only
+        if world > 1:
+            args.no_batched = args.no_learned = True
         if not args.no_batched:
             line["batched"] = run_batched(args, vb, torch, flush_buf, stream)
             line["mixed"] = run_mixed(args, vb, torch, flush_buf, stream)
