@@ -553,9 +553,9 @@ struct Ctx {
         cudaEvent_t e = ev(ev_start);
         if (e) cudaEventRecord(e, st);
     }
-    // call after a launch with its status and kind
-    void chk(cudaError_t e, int kind) {
-        ++launches;
+    // call after `n` launches of one kind with their status
+    void chk(cudaError_t e, int kind, int n = 1) {
+        launches += n;
         if (err == cudaSuccess) err = e;
         if (timed && ev_start >= 0) {
             cudaEvent_t f = ev(ev_start + 1);
@@ -777,7 +777,9 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     // split big subbands over several CTAs only while slices alone leave SMs idle
     a.max_parts = (c.batch * p->B >= 2 * p->num_sms) ? 1 : SURE_MAX_PARTS;
     c.pre();
-    c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), c.st), VDAMP_KERNEL_SURE);
+    // one kernel (sort and search in one CTA) when every subband is one part, else two
+    c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), c.st), VDAMP_KERNEL_SURE,
+          a.max_parts == 1 ? 1 : 2);
 }
 
 void enq_line8(Ctx& c, const float2* r, float2* out) {

@@ -580,7 +580,7 @@ __global__ void cnn_onsager_kernel(const float2* r, const float2* f, const doubl
                                    const CnnImage* img, int n_img, int total_tiles, float2* rt,
                                    float2* w_hat, int* use_out, double* alpha_out) {
     __shared__ int s_use;
-    __shared__ float s_fa, s_inv, s_th;
+    __shared__ float s_fa, s_inv, s_th, s_c1, s_c2;
     cudaGridDependencySynchronize();
     const int t = blockIdx.x;
     if (t >= total_tiles) return;
@@ -598,8 +598,11 @@ __global__ void cnn_onsager_kernel(const float2* r, const float2* f, const doubl
         const double al = use ? ac : alpha_soft[sb];
         s_use = use ? 1 : 0;
         s_fa = (float)al;
-        s_inv = (float)(1.0 / (1.0 - al));
+        const double inv = 1.0 / (1.0 - al);
+        s_inv = (float)inv;
         s_th = (float)thr[sb];
+        s_c1 = (float)(thr[sb] * inv);   // the soft threshold's line 8 as the plain path
+        s_c2 = (float)(al * inv);        // forms it: r (1 - c1 / |r|) above theta, -c2 r below
         if (t == im.tile0) {
             if (use_out) use_out[ii] = use ? 1 : 0;
             if (alpha_out) alpha_out[ii] = al;
@@ -615,13 +618,15 @@ __global__ void cnn_onsager_kernel(const float2* r, const float2* f, const doubl
     float2 w;
     if (use) {
         w = f[q];
+        rt[q] = make_float2((w.x - s_fa * v.x) * s_inv, (w.y - s_fa * v.y) * s_inv);
     } else {
         const float a = cabs_f(v);
         const float sc = a > s_th ? 1.f - s_th / a : 0.f;
         w = make_float2(__fmul_rn(v.x, sc), __fmul_rn(v.y, sc));
+        const float g = a > s_th ? 1.f - s_c1 / a : -s_c2;
+        rt[q] = make_float2(__fmul_rn(v.x, g), __fmul_rn(v.y, g));
     }
     if (w_hat) w_hat[q] = w;
-    rt[q] = make_float2((w.x - s_fa * v.x) * s_inv, (w.y - s_fa * v.y) * s_inv);
 }
 
 template <int CIN, int COUT>

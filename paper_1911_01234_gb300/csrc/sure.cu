@@ -1,6 +1,8 @@
 // SURE threshold step of the VDAMP iteration (Algorithm 1 lines 5-7) as two
 // kernels: the parallel sort of the subband magnitudes, then the parallel
-// exact minimiser search, both split into parts per subband.  The arithmetic is in sure_dev.cuh.
+// exact minimiser search, both split into parts per subband; or, when the
+// slices alone fill the GPU (one part per subband), as one kernel doing both
+// in the same CTA.  The arithmetic is in sure_dev.cuh.
 #include "sure_dev.cuh"
 
 namespace vdamp {
@@ -18,9 +20,23 @@ __global__ void __launch_bounds__(SURE_THREADS) sure_search_kernel(const __grid_
     sure_search_part(a, a.k, blockIdx.x, a.B - 1 - (int)blockIdx.y, blockIdx.z, sm_keys);
 }
 
+// One CTA per subband (max_parts == 1): sort, then search the keys the sort
+// left in shared memory.
+__global__ void __launch_bounds__(SURE_THREADS) sure_one_cta_kernel(const __grid_constant__ SureArgs a) {
+    extern __shared__ float sm_keys[];
+    cudaGridDependencySynchronize();
+    const int b = a.B - 1 - (int)blockIdx.y;
+    sure_sort_part_f<true>(a, a.r, 0, b, blockIdx.z, sm_keys);
+    __syncthreads();
+    sure_search_part_t<true>(a, a.k, 0, b, blockIdx.z, sm_keys);
+}
+
 size_t sure_smem(int max_band) { return sure_smem_bytes(max_band); }
 
 cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, cudaStream_t st) {
+    if (a.max_parts == 1)
+        return launch_pdl(sure_one_cta_kernel, dim3(1, a.B, batch), dim3(SURE_THREADS),
+                          sure_smem_bytes(max_band), st, a);
     cudaError_t e = launch_pdl(sure_sort_kernel, dim3(a.max_parts, a.B, batch),
                                dim3(SURE_THREADS), sure_smem_bytes(max_band), st, a);
     if (e != cudaSuccess) return e;
@@ -35,6 +51,9 @@ cudaError_t configure_sure(size_t smem_bytes) {
     raised = smem_bytes;
     cudaError_t e = cudaFuncSetAttribute(sure_sort_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sure_one_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sure_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes);

@@ -11,7 +11,9 @@
 // gives the constant C_N - N_b tau.  The global minimum over all intervals is
 // the threshold; ties go to the smaller theta.  alpha = (K - theta H_m / 2) / N_b.
 //
-// Two steps, each run by one 1024-thread CTA per work item:
+// Two steps, each run by one 1024-thread CTA per work item (or, when every
+// subband is a single part, both in one CTA with the sorted keys kept in
+// shared memory between them):
 //   sure_sort_part   : part q of subband b sorts its share of the magnitudes,
 //                      writes them to their final places in `sorted` and
 //                      publishes its position range with the sums of a^2 and
@@ -26,8 +28,8 @@
 // buckets per octave growing with the subband size; smaller magnitudes share
 // bucket 0) are exactly ordered.  Each
 // bucket belongs to the part in which its first position falls, and is
-// sorted in registers by a bitonic network (up to 32 keys) or in shared
-// memory.  A bucket above SORT_MAX_BUCKET keys (ties, or a degenerate subband)
+// sorted in registers by a bitonic network of 2, 4, 8, 16 or 32 keys (the
+// smallest that holds it) or, above 32 keys, in shared memory.  A bucket above SORT_MAX_BUCKET keys (ties, or a degenerate subband)
 // sends the whole subband to a bitonic sort done by part 0.
 //
 // Precision: magnitudes, keys and per-thread partial sums are FP32; the
@@ -68,11 +70,12 @@ inline size_t sure_search_smem_bytes(int max_band) {
 }
 
 // Shared memory of the sort (and an upper bound for the search): keys padded
-// to a power of two, then the bucket counters.
+// to a power of two, four spare slots (the one-CTA sort + search keeps its
+// keys one slot up), then the bucket counters.
 inline size_t sure_smem_bytes(int max_band) {
     int np = 2;
     while (np < max_band) np <<= 1;
-    return (size_t)np * sizeof(float) + SORT_HIST_WORDS * sizeof(int);
+    return ((size_t)np + 4) * sizeof(float) + SORT_HIST_WORDS * sizeof(int);
 }
 
 __device__ __forceinline__ void record_numeric(int* status, int k) {
@@ -120,6 +123,32 @@ __device__ __forceinline__ void block_bitonic(float* keys, int np) {
             __syncthreads();
         }
     }
+}
+
+// Sorts bucket keys[s0, s0 + n), 0 < n <= NR, in registers by a bitonic
+// network of NR keys and writes it to out (adding each key's a^2 and 1/a, in
+// sorted order, to ps2 and ph), or back in place (FUSED).  The network is
+// the smallest power of two that holds the bucket: a bucket of a few keys
+// costs a few compare-exchanges.
+template <int NR, bool FUSED>
+__device__ __forceinline__ void sort_bucket_regs(float* keys, float* out, int s0, int n,
+                                                 float& ps2, float& ph) {
+    if (FUSED && n == 1) return;
+    float v[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) v[i] = i < n ? keys[s0 + i] : INFINITY;
+    if (n > 1) sort_regs<NR>(v);
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+        if (i < n) {
+            if (FUSED) {
+                keys[s0 + i] = v[i];
+            } else {
+                out[s0 + i] = v[i];
+                ps2 += v[i] * v[i];
+                ph += v[i] > 0.f ? __frcp_rn(v[i]) : 0.f;
+            }
+        }
 }
 
 // Publishes the position range [p0, p1) a part sorted and the FP64 sums of a^2
@@ -192,9 +221,13 @@ __device__ __forceinline__ void part_record_sums(const SureArgs& a, int part, in
 // Part `part` of subband b of slice `slice`: sort and write its share of |r|.
 // Called by all threads of a CTA of SURE_THREADS threads; `keys` is dynamic
 // shared memory of sure_smem_bytes(max band) bytes.
-template <int EMAX>
+// FUSED (one part per subband, the search follows in the same CTA): the
+// sorted subband stays in shared memory at keys[1 .. nb] (keys[0] is left
+// for the search's predecessor entry), nothing is written to global memory
+// and no part record is published.
+template <int EMAX, bool FUSED>
 __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2* rk, int part,
-                                                 int b, int slice, float* keys) {
+                                                 int b, int slice, float* keys_base) {
     __shared__ unsigned s_max_bits;
     __shared__ int s_big;
     __shared__ int wsum[32];
@@ -210,7 +243,8 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
     __shared__ int s_qa, s_qb;
     int np = 2;
     while (np < nb) np <<= 1;
-    int* hist = reinterpret_cast<int*>(keys + np);
+    float* keys = FUSED ? keys_base + 1 : keys_base;
+    int* hist = reinterpret_cast<int*>(keys_base + np + (FUSED ? 4 : 0));
     float* out = a.sorted + (size_t)slice * a.N + off;
 
     if (tid == 0) {
@@ -298,7 +332,7 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
     __syncthreads();
     if (s_big) {
         // degenerate subband: part 0 sorts everything, the other parts are empty
-        if (part != 0) {
+        if (part != 0) {   // never with FUSED (one part)
             if (tid == 0)
                 a.partrec[((size_t)slice * a.B + b) * SURE_MAX_PARTS + part] =
                     make_double4_32a(-1.0, -1.0, 0.0, 0.0);
@@ -310,6 +344,7 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
         for (int i = nb + tid; i < np; i += nthr) keys[i] = INFINITY;
         __syncthreads();
         block_bitonic(keys, np);
+        if (FUSED) return;
         for (int i = tid; i < nb; i += nthr) out[i] = keys[i];
         __syncthreads();
         part_record_range(a, part, b, slice, 0, nb, out);
@@ -326,30 +361,16 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
         const int s0 = q > 0 ? hist[HIX(q - 1)] : 0, s1 = hist[HIX(q)];
         const int n = s1 - s0;
         if (n <= 0) continue;
-        if (n <= 16) {
-            float v[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = i < n ? keys[s0 + i] : INFINITY;
-            if (n > 1) sort_regs<16>(v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-                if (i < n) {
-                    out[s0 + i] = v[i];
-                    ps2 += v[i] * v[i];
-                    ph += v[i] > 0.f ? __frcp_rn(v[i]) : 0.f;
-                }
+        if (n <= 2) {
+            sort_bucket_regs<2, FUSED>(keys, out, s0, n, ps2, ph);
+        } else if (n <= 4) {
+            sort_bucket_regs<4, FUSED>(keys, out, s0, n, ps2, ph);
+        } else if (n <= 8) {
+            sort_bucket_regs<8, FUSED>(keys, out, s0, n, ps2, ph);
+        } else if (n <= 16) {
+            sort_bucket_regs<16, FUSED>(keys, out, s0, n, ps2, ph);
         } else if (n <= 32) {
-            float v[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = i < n ? keys[s0 + i] : INFINITY;
-            sort_regs<32>(v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (i < n) {
-                    out[s0 + i] = v[i];
-                    ps2 += v[i] * v[i];
-                    ph += v[i] > 0.f ? __frcp_rn(v[i]) : 0.f;
-                }
+            sort_bucket_regs<32, FUSED>(keys, out, s0, n, ps2, ph);
         } else {
             for (int i = s0 + 1; i < s1; ++i) {
                 const float x = keys[i];
@@ -360,6 +381,7 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
                 }
                 keys[j + 1] = x;
             }
+            if (FUSED) continue;
             for (int i = s0; i < s1; ++i) {
                 const float x = keys[i];
                 out[i] = x;
@@ -368,26 +390,36 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
             }
         }
     }
+    if (FUSED) return;
     const int p0 = qa > 0 ? hist[HIX(qa - 1)] : 0;
     const int p1 = qb > qa ? hist[HIX(qb - 1)] : p0;
     part_record_sums(a, part, b, slice, p0, p1, ps2, ph);
 }
 
-static __device__ void sure_sort_part(const SureArgs& a, const float2* rk, int part, int b,
-                                      int slice, float* keys) {
+template <bool FUSED>
+static __device__ void sure_sort_part_f(const SureArgs& a, const float2* rk, int part, int b,
+                                        int slice, float* keys) {
     const int nb = a.off[b + 1] - a.off[b];
     if (nb <= 16 * SURE_THREADS)
-        sure_sort_part_t<16>(a, rk, part, b, slice, keys);
+        sure_sort_part_t<16, FUSED>(a, rk, part, b, slice, keys);
     else
-        sure_sort_part_t<SORT_MAX_PER_THREAD>(a, rk, part, b, slice, keys);
+        sure_sort_part_t<SORT_MAX_PER_THREAD, FUSED>(a, rk, part, b, slice, keys);
+}
+
+static __device__ void sure_sort_part(const SureArgs& a, const float2* rk, int part, int b,
+                                      int slice, float* keys) {
+    sure_sort_part_f<false>(a, rk, part, b, slice, keys);
 }
 
 // Search part `part` of subband b: the exact minimiser over the intervals whose
 // lower end lies in the part's sorted range, combined across parts by the last
 // part to finish (an atomic counter per subband, returned to zero by that part),
 // which writes tau, theta and alpha.
-static __device__ void sure_search_part(const SureArgs& a, int k, int part, int b, int slice,
-                                        float* keys) {
+// FUSED: the subband is one part whose sorted magnitudes sure_sort_part_t<.., true>
+// left at keys[1 .. nb] of the same CTA.
+template <bool FUSED>
+static __device__ void sure_search_part_t(const SureArgs& a, int k, int part, int b, int slice,
+                                          float* keys) {
     __shared__ double s_tau, s_cbase, s_hafter;
     __shared__ int s_p0, s_p1, s_last;
     __shared__ float wc[32], wh[32];
@@ -410,7 +442,14 @@ static __device__ void sure_search_part(const SureArgs& a, int k, int part, int 
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) s_tau = t;
     }
-    if (warp == 1) {   // this part's range and the sums of the parts below and above it
+    if (FUSED && warp == 1) {   // the whole subband, nothing below or above it
+        if (lane == 0) {
+            s_p0 = 0;
+            s_p1 = nb;
+            s_cbase = 0.0;
+            s_hafter = 0.0;
+        }
+    } else if (warp == 1) {   // this part's range and the sums of the parts below and above it
         const double4_32a me = a.partrec[rec + part];
         const int p0 = (int)me.x, p1 = (int)me.y;
         double cb = 0.0, ha = 0.0;
@@ -440,8 +479,9 @@ static __device__ void sure_search_part(const SureArgs& a, int k, int part, int 
     // keys[0] = the magnitude just below the part (0 for the first), keys[1 + i] = a_(p0 + i)
     const float* srt = a.sorted + (size_t)slice * a.N + off;
     if (tid == 0) keys[0] = p0 > 0 ? srt[p0 - 1] : 0.f;
-    batched_for<16, float>(tid, len, nthr, [&](int i) { return srt[p0 + i]; },
-                           [&](int i, float v) { keys[1 + i] = v; });
+    if (!FUSED)
+        batched_for<16, float>(tid, len, nthr, [&](int i) { return srt[p0 + i]; },
+                               [&](int i, float v) { keys[1 + i] = v; });
     __syncthreads();
 
     // ---- prefix sums of a^2 (from below) and suffix sums of 1/a (from above), local
@@ -645,7 +685,7 @@ static __device__ void sure_search_part(const SureArgs& a, int k, int part, int 
         a.tau_out[orow] = tau;
         a.thr_out[orow] = 0.0;
         a.alpha_out[orow] = 0.0;
-        a.coef[slice * a.B + b] = make_float4(0.f, 0.f, 1.f, 0.f);
+        a.coef[slice * a.B + b] = make_float4(0.f, 0.f, 0.f, 0.f);   // r~ = r
         if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = 0.0;
         if (!isfinite(tau)) record_numeric(a.status, k);
         return;
@@ -659,9 +699,17 @@ static __device__ void sure_search_part(const SureArgs& a, int k, int part, int 
     a.thr_out[orow] = theta;
     a.alpha_out[orow] = alpha;
     if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = bmi >= 0 ? bv : 0.0;
+    // line 8 as r~ = r (1 - c1 / |r|) above theta and -c2 r below, c1 = theta / (1 - alpha),
+    // c2 = alpha / (1 - alpha): no FP32 difference of nearly equal terms when alpha -> 1
     const double inv = 1.0 / (1.0 - alpha);
-    a.coef[slice * a.B + b] = make_float4((float)theta, (float)alpha, (float)inv, 0.f);
+    a.coef[slice * a.B + b] =
+        make_float4((float)theta, (float)(theta * inv), (float)(alpha * inv), 0.f);
     if (bmi < 0 || !isfinite(alpha) || !isfinite(theta) || !isfinite(inv)) record_numeric(a.status, k);
+}
+
+static __device__ void sure_search_part(const SureArgs& a, int k, int part, int b, int slice,
+                                        float* keys) {
+    sure_search_part_t<false>(a, k, part, b, slice, keys);
 }
 
 }  // namespace vdamp

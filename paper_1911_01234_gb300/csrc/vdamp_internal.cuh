@@ -3,8 +3,9 @@
 // Data layout (all per slice, slices contiguous):
 //   image / k-space : float2 [ny][nx], k-space unshifted
 //   packed wavelet  : float2 [ny*nx], subbands A_s, H_s, V_s, D_s, ..., D_1
-//   coef            : float4 [B] per slice = (theta, alpha, 1/(1-alpha), 0):
-//                     what the denoiser of the previous iteration chose
+//   coef            : float4 [B] per slice = (theta, theta/(1-alpha),
+//                     alpha/(1-alpha), 0), from FP64: what the denoiser of
+//                     the previous iteration chose
 #pragma once
 
 #include <cuda_runtime.h>
@@ -95,14 +96,14 @@ __device__ __forceinline__ float2 src_apply(int mode, float2 v, float4 c) {
     if (mode == SRC_ZERO) return make_float2(0.f, 0.f);
     if (mode == SRC_EXPLICIT) return v;
     float a = cabs_f(v);
-    float sc = a > c.x ? 1.f - c.x / a : 0.f;
-    if (mode == SRC_SOFT) return cscale_rn(v, sc);
-    return cscale_rn(v, __fmul_rn(sc - c.y, c.z));
+    if (mode == SRC_SOFT) return cscale_rn(v, a > c.x ? 1.f - c.x / a : 0.f);
+    // (soft(r) - alpha r) / (1 - alpha) = r (1 - c1 / |r|) above theta, -c2 r below
+    return cscale_rn(v, a > c.x ? 1.f - c.y / a : -c.z);
 }
 
 __device__ __forceinline__ float4 src_coef(const SrcSpec& s, int slice, int b) {
     return (s.mode == SRC_LINE8 || s.mode == SRC_SOFT) ? s.coef[slice * s.B + b]
-                                                        : make_float4(0.f, 0.f, 1.f, 0.f);
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __device__ __forceinline__ float2 src_value(const SrcSpec& s, int slice, size_t N, size_t idx,

@@ -81,6 +81,33 @@ def _tie(r, sbs, tau, th_gpu, th_orc):
     return True
 
 
+def _forced_step_ok(plan, pr, ops, r_tilde, where):
+    """One iteration (lines 3-8) of one slice started from the oracle's own r~_k: r, tau,
+    the thresholds (or a certified tie) and, where the thresholds agree, alpha and r~_{k+1}
+    against the oracle's step from the same r~_k."""
+    N, B = pr.y.size, plan.B
+    y64 = np.where(pr.mask == 1, pr.y.astype(np.complex128), 0.0)
+    rt32 = r_tilde.astype(np.complex64)
+    rec = O.iterate(rt32.astype(np.complex128), y64, ops, float(pr.sigma) ** 2)
+    one = lambda a: torch.from_numpy(np.ascontiguousarray(a[None])).cuda()
+    r = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    rn = torch.empty_like(r)
+    tau = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+    vb.vdamp_iterate(plan.handle, 1, one(rt32.reshape(-1)), one(pr.y), one(pr.mask),
+                     one(pr.density), [pr.sigma], r, tau, thr, alpha, rn)
+    torch.cuda.synchronize()
+    assert rel(r.cpu().numpy()[0], rec.r) < 1e-5, where
+    tg = tau.cpu().numpy()[0]
+    assert rel(tg, rec.tau) < 1e-4 and np.max(np.abs(tg - rec.tau) / rec.tau) < 1e-3, where
+    th = thr.cpu().numpy()[0]
+    assert _tie(rec.r, ops.sbs, rec.tau, th, rec.theta), where
+    if np.allclose(th, rec.theta, rtol=1e-3, atol=0):
+        assert np.max(np.abs(alpha.cpu().numpy()[0] - rec.alpha)) < 1e-4, where
+        assert rel(rn.cpu().numpy()[0], O.next_r_tilde(rec, ops)) < 1e-4, where
+    return True
+
+
 def test_groups_match_oracle_on_sampled_slices():
     iters = 5
     groups = _groups((2, 2, 2))
@@ -99,8 +126,12 @@ def test_groups_match_oracle_on_sampled_slices():
         for k, rec in enumerate(res.records):
             assert rel(tau[k], rec.tau) < 1e-4, (wl.name, k)
             if not np.allclose(thr[k], rec.theta, rtol=1e-3, atol=0):
-                # from here the runs follow different (equally valid) trajectories
-                assert _tie(rec.r, ops.sbs, rec.tau, thr[k], rec.theta), (wl.name, k)
+                # The free-running states have drifted apart at the FP32 level (the
+                # iteration amplifies perturbations) and met a SURE near-tie, where a
+                # relative change of 1e-6 in the magnitudes can flip the minimiser.  From
+                # here the runs follow different, equally valid trajectories; the step
+                # itself is held to the tolerances from the oracle's own r~_k.
+                assert _forced_step_ok(plan, pr, ops, rec.r_tilde, (wl.name, k))
                 parted = k
                 break
         xg = o["x_hat"].cpu().numpy()[i]
@@ -180,4 +211,85 @@ def test_autotune_picks_a_valid_tuning_that_still_matches():
     o = plan.solve(y, m, d, [pr.sigma], iters)
     torch.cuda.synchronize()
     assert rel(o["x_hat"].cpu().numpy()[0], res.x_hat) < 1e-4
+    plan.close()
+
+
+def test_full_size_batched_workload_on_sampled_slices():
+    """256 slices of 320x320, db4 s=5, R=6 (the batched workload at full size) in the
+    autotuned launch shape: with 16 subbands x 256 slices every subband's SURE runs as one
+    CTA that sorts and searches (not the split parts of a lone slice).  16 distinct problems
+    are tiled over the batch: replicas must give bit-identical results (no cross-slice
+    effects), and three of them are checked against the FP64 oracle, teacher-forced at
+    iterations 0 and 4 (lines 3-8) and free-running for 3 iterations."""
+    wl = synth.BATCH_320_DB4_5
+    nb, distinct, K = 256, 16, 5
+    prs = [synth.make_problem(wl, i) for i in range(distinct)]
+    pick = [i % distinct for i in range(nb)]
+    sampled = (0, 7, 13)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
+    assert nb * plan.B >= 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    plan.autotune(nb, trials=1)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
+    y = dev([prs[i].y for i in pick])
+    m = dev([prs[i].mask for i in pick])
+    d = dev([prs[i].density for i in pick])
+    sig = [prs[i].sigma for i in pick]
+    ora = {}
+    for j in sampled:
+        pr = prs[j]
+        ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+        ora[j] = (ops, O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, K,
+                               want_x=True, ops=ops))
+    N, B = wl.ny * wl.nx, plan.B
+
+    def same_as_first(t):
+        t = t.reshape(nb, -1)
+        return all(torch.equal(t[i], t[pick[i]]) for i in range(distinct, nb))
+
+    # teacher-forced: the sampled slices start from the oracle's r~_k, the others from 0
+    r = torch.empty((nb, N), dtype=torch.complex64, device="cuda")
+    rn = torch.empty_like(r)
+    tau = torch.empty((nb, B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+    for k in (0, 4):
+        rt = np.zeros((nb, N), dtype=np.complex64)
+        for i in range(nb):
+            if pick[i] in ora:
+                rt[i] = ora[pick[i]][1].records[k].r_tilde.astype(np.complex64)
+        vb.vdamp_iterate(plan.handle, nb, dev(list(rt)), y, m, d, sig, r, tau, thr, alpha, rn)
+        torch.cuda.synchronize()
+        for t in (r, tau, thr, alpha, rn):
+            assert same_as_first(t), k
+        for j in sampled:
+            ops, res = ora[j]
+            pr = prs[j]
+            y64 = np.where(pr.mask == 1, pr.y.astype(np.complex128), 0.0)
+            rt64 = res.records[k].r_tilde.astype(np.complex64).astype(np.complex128)
+            rec = O.iterate(rt64, y64, ops, float(pr.sigma) ** 2)
+            assert rel(r.cpu().numpy()[j], rec.r) < 1e-5, (j, k)
+            tg = tau.cpu().numpy()[j]
+            assert rel(tg, rec.tau) < 1e-4 and np.max(np.abs(tg - rec.tau) / rec.tau) < 1e-3
+            th = thr.cpu().numpy()[j]
+            assert _tie(rec.r, ops.sbs, rec.tau, th, rec.theta), (j, k)
+            if np.allclose(th, rec.theta, rtol=1e-3, atol=0):
+                assert np.max(np.abs(alpha.cpu().numpy()[j] - rec.alpha)) < 1e-4, (j, k)
+                assert rel(rn.cpu().numpy()[j], O.next_r_tilde(rec, ops)) < 1e-4, (j, k)
+
+    # free-running, 3 iterations
+    o = plan.solve(y, m, d, sig, 3, want_iters=True)
+    torch.cuda.synchronize()
+    assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+    for key in ("x_hat", "tau", "thr", "alpha"):
+        assert same_as_first(o[key]), key
+    xi = o["x_hat_iters"].cpu().numpy()
+    for j in sampled:
+        ops, res = ora[j]
+        for k in range(3):
+            rec = res.records[k]
+            assert rel(o["tau"].cpu().numpy()[j, k], rec.tau) < 1e-4, (j, k)
+            if not np.allclose(o["thr"].cpu().numpy()[j, k], rec.theta, rtol=1e-3, atol=0):
+                # a SURE near-tie met by drifted states (see the sampled-slices test)
+                assert _forced_step_ok(plan, prs[j], ops, rec.r_tilde, (j, k))
+                break
+            assert rel(xi[k, j], rec.x_hat) < 1e-4, (j, k)
     plan.close()
