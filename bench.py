@@ -511,7 +511,10 @@ def run_gpu(args):
     thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
     stream = torch.cuda.current_stream()
     if args.tuning:
-        plan.set_tuning([int(v) for v in args.tuning.split(",")])
+        t = [int(v) for v in args.tuning.split(",")]
+        if len(t) == 7:
+            t.append(0)   # no SURE-parts entry given: parts by batch size
+        plan.set_tuning(t)
         tuning = plan.tuning()
     else:
         tuning = None if args.no_autotune else plan.autotune(1, trials=5,

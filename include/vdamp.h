@@ -129,13 +129,20 @@ int vdamp_last_launch_count(const vdamp_plan* plan);
  *   [6] 1: the scales s .. 2 of Psi (and of Psi^H) in one launch, one
  *       thread-block cluster per slice, scale 1 in its own launch, while
  *       batch x cluster size <= the SM count; 0: one launch per scale
+ *   [7] parts per subband of the SURE threshold search (Algorithm 1 lines
+ *       6-7): 1 = one CTA per subband sorts and searches (one launch);
+ *       2, 4 or 8 = subbands above 2048 coefficients split over up to that
+ *       many CTAs (a sort and a search launch); 0 = 8 while the CTAs of the
+ *       split (batch x the parts of all subbands) fit on the SMs at once,
+ *       else 1
  * Every tuning computes the same method; tunings differ in FP32 summation
- * order only (the tau partial sums depend on [0], the DFT on [4], [5]).
+ * order only (the tau partial sums depend on [0], the DFT on [4], [5], the
+ * FP32 candidate sums of the SURE search on [7]).
  * get copies the current tuning out; set validates and applies one
  * (VDAMP_EINVAL for an unsupported value, nothing changed) and drops the
  * plan's cached graphs.
  */
-#define VDAMP_TUNING_LEN 7
+#define VDAMP_TUNING_LEN 8
 vdamp_status vdamp_plan_get_tuning(const vdamp_plan* plan, int* tuning);
 vdamp_status vdamp_plan_set_tuning(vdamp_plan* plan, const int* tuning);
 

@@ -72,9 +72,9 @@ _SIGS = {
     "vdamp_last_sure": (_I, [_P, _I, _P, _P]),
 }
 
-VDAMP_TUNING_LEN = 7
+VDAMP_TUNING_LEN = 8
 TUNING_FIELDS = ("col_block", "rows_per_cta", "idwt_tile", "dwt_tile", "radix_y", "radix_x",
-                 "wavelet_cluster")
+                 "wavelet_cluster", "sure_parts")
 
 
 class vdamp_group(ctypes.Structure):

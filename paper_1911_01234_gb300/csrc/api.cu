@@ -203,6 +203,7 @@ struct vdamp_plan {
     int radix_var[2] = {0, 0};         // radix plan variant along y, x
     int wcluster = 0;                  // CTAs of the one-launch wavelet cluster (0: unavailable)
     int use_wcluster = 0;              // tuning: all scales in one cluster launch (small batches)
+    int sure_parts = 0;                // tuning: SURE parts per subband (0: by batch size)
     int num_sms = 152;
     float* ey = nullptr;
     float* ex = nullptr;
@@ -774,8 +775,14 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     a.bestrec = p->bestrec;
     a.counter = p->counter;
     a.sure_out = p->sure_val;
-    // split big subbands over several CTAs only while slices alone leave SMs idle
-    a.max_parts = (c.batch * p->B >= 2 * p->num_sms) ? 1 : SURE_MAX_PARTS;
+    // Split big subbands over several CTAs only while the split grid fits in one wave
+    // (each part rereads its whole subband: past one wave one CTA per subband is
+    // faster), unless the tuning fixes the number of parts.
+    int split = 0;
+    for (int b = 0; b < p->B; ++b)
+        split += vdamp::sure_parts(p->off[b + 1] - p->off[b], SURE_MAX_PARTS);
+    a.max_parts = p->sure_parts ? p->sure_parts
+                                : ((c.batch * split > p->num_sms) ? 1 : SURE_MAX_PARTS);
     c.pre();
     // one kernel (sort and search in one CTA) when every subband is one part, else two
     c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), c.st), VDAMP_KERNEL_SURE,
@@ -1242,6 +1249,7 @@ bool tuning_valid(const vdamp_plan* p, const int* t) {
     if (ito != 16 && ito != 32 && ito != 64) return false;
     if (dto != 16 && dto != 32) return false;
     if (t[6] != 0 && t[6] != 1) return false;
+    if (t[7] != 0 && t[7] != 1 && t[7] != 2 && t[7] != 4 && t[7] != SURE_MAX_PARTS) return false;
     if (vdamp::idwt_tile_smem(ito, p->filt.L) > p->smem_dwt ||
         vdamp::dwt_tile_smem(dto, p->filt.L) > p->smem_dwt)
         return false;
@@ -1260,6 +1268,7 @@ void get_tuning(const vdamp_plan* p, int* t) {
     t[4] = p->radix_var[0];
     t[5] = p->radix_var[1];
     t[6] = p->use_wcluster;
+    t[7] = p->sure_parts;
 }
 
 void apply_tuning(vdamp_plan* p, const int* t) {
@@ -1271,6 +1280,7 @@ void apply_tuning(vdamp_plan* p, const int* t) {
     p->radix_var[0] = t[4];
     p->radix_var[1] = t[5];
     p->use_wcluster = t[6];
+    p->sure_parts = t[7];
     fft_radices(p->ny, p->axy.radix, &p->axy.nstages, t[4]);
     fft_radices(p->nx, p->axx.radix, &p->axx.nstages, t[5]);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);  // they hold the old launch shapes
@@ -1374,17 +1384,18 @@ extern "C" vdamp_status vdamp_plan_autotune(vdamp_plan* p, int batch, int trials
         if (x != cudaSuccess) return x;
         return cudaEventElapsedTime(ms, e0, e1);
     };
-    // coordinate descent over (cb, rpc, idwt tile, dwt tile, radix plan y, radix plan x)
-    static const int choices[7][4] = {{2, 4, 8, 16}, {1, 2, 4, 8}, {16, 32, 64, 0},
-                                      {16, 32, 0, 0}, {0, 1, 2, -1}, {0, 1, 2, -1},
-                                      {0, 1, -1, -1}};
-    int best[7];
+    // coordinate descent over (cb, rpc, idwt tile, dwt tile, radix plan y, radix plan x,
+    // wavelet cluster, SURE parts)
+    static const int choices[VDAMP_TUNING_LEN][4] = {{2, 4, 8, 16}, {1, 2, 4, 8}, {16, 32, 64, 0},
+                                                     {16, 32, 0, 0}, {0, 1, 2, -1}, {0, 1, 2, -1},
+                                                     {0, 1, -1, -1}, {0, 1, 2, 4}};
+    int best[VDAMP_TUNING_LEN];
     get_tuning(p, best);
     float best_ms = 0.f;
     A(trial(best, &best_ms));
-    for (int q = 0; q < 7 && e == cudaSuccess; ++q) {
+    for (int q = 0; q < VDAMP_TUNING_LEN && e == cudaSuccess; ++q) {
         for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
-            int cand[7];
+            int cand[VDAMP_TUNING_LEN];
             std::memcpy(cand, best, sizeof(cand));
             cand[q] = choices[q][c];
             if (cand[q] == best[q] || !tuning_valid(p, cand)) continue;

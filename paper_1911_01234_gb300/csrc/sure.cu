@@ -1,8 +1,7 @@
 // SURE threshold step of the VDAMP iteration (Algorithm 1 lines 5-7) as two
 // kernels: the parallel sort of the subband magnitudes, then the parallel
-// exact minimiser search, both split into parts per subband; or, when the
-// slices alone fill the GPU (one part per subband), as one kernel doing both
-// in the same CTA.  The arithmetic is in sure_dev.cuh.
+// exact minimiser search, both split into parts per subband; or, with one
+// part per subband (many slices), as one kernel doing both in the same CTA.  The arithmetic is in sure_dev.cuh.
 #include "sure_dev.cuh"
 
 namespace vdamp {

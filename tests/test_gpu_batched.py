@@ -159,8 +159,8 @@ def test_groups_reject_bad_arguments():
     plan.close()
 
 
-TUNINGS = [[2, 1, 16, 16, 0, 0, 1], [4, 2, 32, 32, 1, 1, 0], [8, 4, 64, 16, 2, 2, 1],
-           [16, 8, 32, 32, 0, 1, 0], [2, 2, 64, 32, 1, 2, 1]]
+TUNINGS = [[2, 1, 16, 16, 0, 0, 1, 0], [4, 2, 32, 32, 1, 1, 0, 1], [8, 4, 64, 16, 2, 2, 1, 2],
+           [16, 8, 32, 32, 0, 1, 0, 4], [2, 2, 64, 32, 1, 2, 1, 8]]
 
 
 @pytest.mark.parametrize("ny,nx,wav,s", [(64, 64, "haar", 3), (48, 80, "db4", 2),
@@ -187,8 +187,9 @@ def test_every_tuning_matches_oracle(ny, nx, wav, s):
             assert rel(o["tau"].cpu().numpy()[0, k], rec.tau) < 1e-4, (t, k)
         tried += 1
     assert tried >= 3
-    for bad in ([3, 1, 16, 16, 0, 0, 0], [8, 0, 16, 16, 0, 0, 0], [8, 1, 24, 16, 0, 0, 0],
-                [8, 1, 16, 64, 0, 0, 0], [8, 1, 16, 16, 3, 0, 0], [8, 1, 16, 16, 0, 0, 2]):
+    for bad in ([3, 1, 16, 16, 0, 0, 0, 0], [8, 0, 16, 16, 0, 0, 0, 0], [8, 1, 24, 16, 0, 0, 0, 0],
+                [8, 1, 16, 64, 0, 0, 0, 0], [8, 1, 16, 16, 3, 0, 0, 0], [8, 1, 16, 16, 0, 0, 2, 0],
+                [8, 1, 16, 16, 0, 0, 0, 3], [8, 1, 16, 16, 0, 0, 0, 16]):
         with pytest.raises(vb.VdampError) as e:
             vb.vdamp_plan_set_tuning(plan.handle, bad)
         assert e.value.status == vb.VDAMP_EINVAL
@@ -203,7 +204,7 @@ def test_autotune_picks_a_valid_tuning_that_still_matches():
     torch.cuda.synchronize()
     assert chosen == vb.vdamp_plan_get_tuning(plan.handle)
     assert chosen[0] in (2, 4, 8, 16) and chosen[2] in (16, 32, 64) and chosen[3] in (16, 32)
-    assert chosen[6] in (0, 1)
+    assert chosen[6] in (0, 1) and chosen[7] in (0, 1, 2, 4)
     iters = 6
     res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, iters)
     y, m, d = (torch.from_numpy(np.ascontiguousarray(a[None])).cuda()
@@ -217,7 +218,7 @@ def test_autotune_picks_a_valid_tuning_that_still_matches():
 def test_full_size_batched_workload_on_sampled_slices():
     """256 slices of 320x320, db4 s=5, R=6 (the batched workload at full size) in the
     autotuned launch shape: with 16 subbands x 256 slices every subband's SURE runs as one
-    CTA that sorts and searches (not the split parts of a lone slice).  16 distinct problems
+    CTA that sorts and searches (not the split parts of a few slices).  16 distinct problems
     are tiled over the batch: replicas must give bit-identical results (no cross-slice
     effects), and three of them are checked against the FP64 oracle, teacher-forced at
     iterations 0 and 4 (lines 3-8) and free-running for 3 iterations."""
@@ -227,8 +228,7 @@ def test_full_size_batched_workload_on_sampled_slices():
     pick = [i % distinct for i in range(nb)]
     sampled = (0, 7, 13)
     plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
-    assert nb * plan.B >= 2 * torch.cuda.get_device_properties(0).multi_processor_count
-    plan.autotune(nb, trials=1)
+    assert plan.autotune(nb, trials=1)["sure_parts"] in (0, 1)   # one SURE CTA per subband
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
     y = dev([prs[i].y for i in pick])
     m = dev([prs[i].mask for i in pick])

@@ -130,13 +130,18 @@ def _problem_on_device(pr):
     return dev(pr.y[None]), dev(pr.mask[None]), dev(pr.density[None])
 
 
-@pytest.mark.parametrize("wl,K", [(synth.PLAIN_64_HAAR3, 20), (synth.PLAIN_256_DB4_4, 30)])
-def test_iteration_teacher_forced(wl, K):
-    """Each iteration k from the oracle's own r~_k: lines 3-8 against the oracle."""
+@pytest.mark.parametrize("wl,K,sure_parts", [(synth.PLAIN_64_HAAR3, 20, 0),
+                                              (synth.PLAIN_256_DB4_4, 30, 0),
+                                              (synth.PLAIN_256_DB4_4, 30, 1)])
+def test_iteration_teacher_forced(wl, K, sure_parts):
+    """Each iteration k from the oracle's own r~_k: lines 3-8 against the oracle (the SURE
+    search split into parts per large subband, or one CTA per subband)."""
     pr = synth.make_problem(wl)
     ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
     res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, K, ops=ops)
     plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    if sure_parts:
+        plan.set_tuning(dict(plan.tuning(), sure_parts=sure_parts))
     y, m, p = _problem_on_device(pr)
     N, B = wl.ny * wl.nx, plan.B
     y64 = np.where(pr.mask == 1, pr.y.astype(np.complex128), 0.0)
