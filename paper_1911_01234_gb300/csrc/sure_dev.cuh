@@ -421,6 +421,41 @@ static __device__ void sure_sort_part(const SureArgs& a, const float2* rk, int p
     sure_sort_part_f<false>(a, rk, part, b, slice, keys);
 }
 
+// Writes the results of subband b at iteration k (one thread): tau, theta and
+// alpha of the chosen interval (bmi keys below theta, the sum bh of 1/a above
+// it, SURE value bv; bmi = nb for theta >= max a, bmi < 0 when nothing was
+// found), the minimum SURE, and the per-subband constants of line 8.
+__device__ __forceinline__ void sure_finish(const SureArgs& a, int k, int b, int slice, int nb,
+                                            double tau, int bmi, double btheta, double bh,
+                                            double bv) {
+    const size_t orow = ((size_t)slice * a.iters + k) * a.B + b;
+    if (!(tau > 0.0) || !isfinite(tau)) {
+        // No effective noise (p = 1 and sigma = 0): keep r, no Onsager term.
+        a.tau_out[orow] = tau;
+        a.thr_out[orow] = 0.0;
+        a.alpha_out[orow] = 0.0;
+        a.coef[slice * a.B + b] = make_float4(0.f, 0.f, 0.f, 0.f);   // r~ = r
+        if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = 0.0;
+        if (!isfinite(tau)) record_numeric(a.status, k);
+        return;
+    }
+    double theta = 0.0, alpha = 0.0;
+    if (bmi >= 0) {
+        theta = btheta;
+        alpha = (bmi == nb) ? 0.0 : ((double)(nb - bmi) - 0.5 * theta * bh) / (double)nb;
+    }
+    a.tau_out[orow] = tau;
+    a.thr_out[orow] = theta;
+    a.alpha_out[orow] = alpha;
+    if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = bmi >= 0 ? bv : 0.0;
+    // line 8 as r~ = r (1 - c1 / |r|) above theta and -c2 r below, c1 = theta / (1 - alpha),
+    // c2 = alpha / (1 - alpha): no FP32 difference of nearly equal terms when alpha -> 1
+    const double inv = 1.0 / (1.0 - alpha);
+    a.coef[slice * a.B + b] =
+        make_float4((float)theta, (float)(theta * inv), (float)(alpha * inv), 0.f);
+    if (bmi < 0 || !isfinite(alpha) || !isfinite(theta) || !isfinite(inv)) record_numeric(a.status, k);
+}
+
 // Search part `part` of subband b: the exact minimiser over the intervals whose
 // lower end lies in the part's sorted range, combined across parts by the last
 // part to finish (an atomic counter per subband, returned to zero by that part),
@@ -659,7 +694,6 @@ static __device__ void sure_search_part_t(const SureArgs& a, int k, int part, in
     __syncthreads();
     if (!s_last || warp != 0) return;
     __threadfence();
-    const size_t orow = ((size_t)slice * a.iters + k) * a.B + b;
     // lane q reads part q's best; ties go to the smaller theta, then the smaller m
     double bv = INFINITY, btheta = INFINITY, bh = 0.0;
     int bmi = -1;
@@ -690,31 +724,7 @@ static __device__ void sure_search_part_t(const SureArgs& a, int k, int part, in
     }
     if (lane != 0) return;
     a.counter[(size_t)slice * a.B + b] = 0u;
-    if (!(tau > 0.0) || !isfinite(tau)) {
-        // No effective noise (p = 1 and sigma = 0): keep r, no Onsager term.
-        a.tau_out[orow] = tau;
-        a.thr_out[orow] = 0.0;
-        a.alpha_out[orow] = 0.0;
-        a.coef[slice * a.B + b] = make_float4(0.f, 0.f, 0.f, 0.f);   // r~ = r
-        if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = 0.0;
-        if (!isfinite(tau)) record_numeric(a.status, k);
-        return;
-    }
-    double theta = 0.0, alpha = 0.0;
-    if (bmi >= 0) {
-        theta = btheta;
-        alpha = (bmi == nb) ? 0.0 : ((double)(nb - bmi) - 0.5 * theta * bh) / (double)nb;
-    }
-    a.tau_out[orow] = tau;
-    a.thr_out[orow] = theta;
-    a.alpha_out[orow] = alpha;
-    if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = bmi >= 0 ? bv : 0.0;
-    // line 8 as r~ = r (1 - c1 / |r|) above theta and -c2 r below, c1 = theta / (1 - alpha),
-    // c2 = alpha / (1 - alpha): no FP32 difference of nearly equal terms when alpha -> 1
-    const double inv = 1.0 / (1.0 - alpha);
-    a.coef[slice * a.B + b] =
-        make_float4((float)theta, (float)(theta * inv), (float)(alpha * inv), 0.f);
-    if (bmi < 0 || !isfinite(alpha) || !isfinite(theta) || !isfinite(inv)) record_numeric(a.status, k);
+    sure_finish(a, k, b, slice, nb, tau, bmi, btheta, bh, bv);
 }
 
 static __device__ void sure_search_part(const SureArgs& a, int k, int part, int b, int slice,

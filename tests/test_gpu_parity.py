@@ -131,11 +131,14 @@ def _problem_on_device(pr):
 
 
 @pytest.mark.parametrize("wl,K,sure_parts", [(synth.PLAIN_64_HAAR3, 20, 0),
+                                              (synth.PLAIN_64_HAAR3, 20, 1),
                                               (synth.PLAIN_256_DB4_4, 30, 0),
-                                              (synth.PLAIN_256_DB4_4, 30, 1)])
+                                              (synth.PLAIN_256_DB4_4, 30, 1),
+                                              (synth.PLAIN_256_DB4_4, 30, 8)])
 def test_iteration_teacher_forced(wl, K, sure_parts):
-    """Each iteration k from the oracle's own r~_k: lines 3-8 against the oracle (the SURE
-    search split into parts per large subband, or one CTA per subband)."""
+    """Each iteration k from the oracle's own r~_k: lines 3-8 against the oracle, with each
+    SURE search layout (0: automatic; 1: sort and search in one CTA per subband; 8: large
+    subbands split into parts)."""
     pr = synth.make_problem(wl)
     ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
     res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, K, ops=ops)
