@@ -225,7 +225,7 @@ KERNEL_SOURCES = {
     "dwt": ("dwt.cu", "dwt_dev.cuh", "vdamp_internal.cuh"),
     "sure": ("sure.cu", "sure_dev.cuh", "vdamp_internal.cuh"),
     "fft_rows": ("fft.cu", "fft_dev.cuh", "vdamp_internal.cuh"),
-    "col_pass": ("fft.cu", "fft_dev.cuh", "vdamp_internal.cuh"),
+    "col_pass": ("fft_col.cu", "fft_dev.cuh", "vdamp_internal.cuh"),
 }
 
 
@@ -351,6 +351,42 @@ def run_mixed(args, vb, torch, flush_buf, stream):
             "one_group_after_another": {"value": slices * K * steps / (ms_serial / 1e3),
                                         "ms_per_step": ms_serial / steps},
             "tuning": tunings or None}
+
+
+def run_fft_reference(vb, torch, stream):
+    """The unitary 2D DFT of the library (row and column kernels, `vdamp_fft2`) timed beside
+    cuFFT (torch.fft.fft2, norm="ortho") on the same data: a reference, not on the hot path
+    (the iteration fuses the k-space step into the column transform instead)."""
+    out = {}
+    for ny, nx, batch, reps in ((256, 256, 1, 200), (320, 320, 256, 20)):
+        plan = vb.Plan(ny, nx, "db4", 4, max_batch=batch)
+        g = torch.Generator(device="cuda").manual_seed(7)
+        x = torch.randn((batch, ny, nx), dtype=torch.complex64, device="cuda", generator=g)
+        y_ours = torch.empty_like(x)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e3)
+            return statistics.median(ts)
+        ours = timed(lambda: vb.vdamp_fft2(plan.handle, batch, x, y_ours,
+                                           stream=stream.cuda_stream))
+        cufft = timed(lambda: torch.fft.fft2(x, norm="ortho"))
+        ref = torch.fft.fft2(x, norm="ortho")
+        torch.cuda.synchronize()
+        err = float((torch.linalg.vector_norm(y_ours - ref) / torch.linalg.vector_norm(ref)).item())
+        out[f"{batch}x{ny}x{nx}"] = {"ours_us": round(ours, 2), "cufft_us": round(cufft, 2),
+                                     "rel_l2_vs_cufft": err}
+        plan.close()
+    return out
 
 
 def run_learned_batched(args, vb, torch, flush_buf, stream):
@@ -633,6 +669,7 @@ def run_gpu(args):
         if not args.no_batched:
             line["batched"] = run_batched(args, vb, torch, flush_buf, stream)
             line["mixed"] = run_mixed(args, vb, torch, flush_buf, stream)
+            line["fft_reference"] = run_fft_reference(vb, torch, stream)
         if not args.no_learned:
             line["learned"] = run_learned(args, vb, torch, flush_buf, stream)
             if not args.no_batched:

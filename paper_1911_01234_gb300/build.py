@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvdamp.so")
-SOURCES = ["api.cu", "fft.cu", "dwt.cu", "sure.cu", "fused.cu", "noalloc.cu", "cnn.cu"]
+SOURCES = ["api.cu", "fft.cu", "fft_col.cu", "dwt.cu", "sure.cu", "fused.cu", "noalloc.cu",
+           "cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

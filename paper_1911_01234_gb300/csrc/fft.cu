@@ -1,5 +1,6 @@
-// Unitary 2D DFT (Phi = M_Omega F, Sec. 1) for the VDAMP iteration: row
-// kernel and fused column-pass kernel; the device code is in fft_dev.cuh.
+// Unitary 2D DFT (Phi = M_Omega F, Sec. 1) for the VDAMP iteration: the row
+// kernel (the fused column pass is in fft_col.cu); the device code is in
+// fft_dev.cuh.
 #include "fft_dev.cuh"
 
 namespace vdamp {
@@ -10,7 +11,7 @@ __global__ void fft_rows_kernel(const float2* in, float2* out, int ny, int nx,
     extern __shared__ float2 sm[];
     cudaGridDependencySynchronize();
     const int row0 = blockIdx.x * rpc;
-    fft_rows_block<INV>(in, out, ny, nx, ax, scale, row0, min(rpc, ny - row0), blockIdx.y, sm);
+    fft_rows_dispatch<INV>(in, out, ny, nx, ax, scale, row0, min(rpc, ny - row0), blockIdx.y, sm);
 }
 
 cudaError_t launch_fft_rows(const float2* in, float2* out, int ny, int nx, int batch,
@@ -26,34 +27,6 @@ cudaError_t launch_fft_rows(const float2* in, float2* out, int ny, int nx, int b
                           ax, scale, rpc);
     return launch_pdl(fft_rows_kernel<false>, grid, dim3(threads), smem, st, in, out, ny, nx, ax,
                       scale, rpc);
-}
-
-size_t col_pass_smem(int ny, int cb, int ntypes) { return col_pass_smem_bytes(ny, cb, ntypes); }
-
-__global__ void col_pass_kernel(const __grid_constant__ ColArgs a) {
-    extern __shared__ float2 sm[];
-    cudaGridDependencySynchronize();
-    col_pass_block(a, a.mode, a.u_zero, blockIdx.x, gridDim.x, blockIdx.y, sm);
-}
-
-cudaError_t launch_col_pass(const ColArgs& a, int batch, cudaStream_t st) {
-    dim3 grid(a.nx / a.cb, batch);
-    int threads = a.ny * a.cb / 4;
-    threads = threads < 64 ? 64 : (threads > 512 ? 512 : threads);
-    threads = (threads + 31) / 32 * 32;
-    // every thread keeps one column: blockDim must be a multiple of cb
-    while (threads % a.cb) threads += 32;
-    size_t smem = col_pass_smem(a.ny, a.cb, a.ntypes);
-    return launch_pdl(col_pass_kernel, grid, dim3(threads), smem, st, a);
-}
-
-cudaError_t configure_col_pass(size_t smem_bytes) {
-    // the attribute is per kernel and process-wide: only ever raise it
-    static size_t raised = 48 * 1024;
-    if (smem_bytes <= raised) return cudaSuccess;
-    raised = smem_bytes;
-    return cudaFuncSetAttribute(col_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes);
 }
 
 cudaError_t configure_fft_rows(size_t smem_bytes) {

@@ -213,10 +213,151 @@ static __device__ float2* fft_stages(float2* a, float2* b, const FftAxis& ax, in
     return src;
 }
 
+// ------------------------------------------------- compile-time plans ---
+// For the axis lengths of the workloads the radix plan is fixed at compile
+// time, so that the stage loops, divisions and twiddle strides of fft_stage
+// become constants.  radix_plan builds the same plans as the host (variant
+// 0: radix 8 first; 1: radix 4 only; 2: the radices 3 and 5 first); a kernel
+// uses a compiled plan only when the axis' plan is equal to it, and computes
+// exactly what fft_stages computes with it.
+struct RadixPlan {
+    int ns;
+    int r[VDAMP_MAX_STAGES];
+};
+
+constexpr RadixPlan radix_plan(int n, int variant) {
+    RadixPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    int m = n, a = 0;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++a;
+    }
+    int p2[VDAMP_MAX_STAGES] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int n2 = 0;
+    if (variant == 1) {
+        for (int i = 0; i < a / 2; ++i) p2[n2++] = 4;
+        if (a & 1) p2[n2++] = 2;
+    } else {
+        int e8 = a / 3, rem = a % 3;
+        if (rem == 1 && e8 > 0) {
+            --e8;
+            rem = 4;
+        }
+        for (int i = 0; i < e8; ++i) p2[n2++] = 8;
+        if (rem == 4) {
+            p2[n2++] = 4;
+            p2[n2++] = 4;
+        } else if (rem == 2) {
+            p2[n2++] = 4;
+        } else if (rem == 1) {
+            p2[n2++] = 2;
+        }
+    }
+    int odd[VDAMP_MAX_STAGES] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int no = 0;
+    while (m % 3 == 0 && no < VDAMP_MAX_STAGES) {
+        odd[no++] = 3;
+        m /= 3;
+    }
+    while (m % 5 == 0 && no < VDAMP_MAX_STAGES) {
+        odd[no++] = 5;
+        m /= 5;
+    }
+    if (variant == 2)
+        for (int i = 0; i < no; ++i) p.r[p.ns++] = odd[i];
+    for (int i = 0; i < n2; ++i) p.r[p.ns++] = p2[i];
+    if (variant != 2)
+        for (int i = 0; i < no; ++i) p.r[p.ns++] = odd[i];
+    return p;
+}
+
+constexpr int plan_prefix(RadixPlan p, int s) {
+    int v = 1;
+    for (int i = 0; i < s; ++i) v *= p.r[i];
+    return v;
+}
+
+template <int N, int VAR>
+__device__ __forceinline__ bool axis_has_plan(const FftAxis& ax) {
+    constexpr RadixPlan P = radix_plan(N, VAR);
+    if (ax.n != N || ax.nstages != P.ns) return false;
+    bool same = true;
+#pragma unroll
+    for (int s = 0; s < P.ns; ++s) same &= ax.radix[s] == P.r[s];
+    return same;
+}
+
+// fft_stage with the length N, the radix R and the sub-transform length NS
+// known at compile time (same butterflies, same order of operations).
+template <int R, bool INV, bool ROWS, int CB, int N, int NS>
+__device__ __forceinline__ void fft_stage_ct(const float2* __restrict__ src, float2* __restrict__ dst,
+                                             const float2* __restrict__ tw, int ntrans) {
+    constexpr int NB = N / R;
+    constexpr int STEP = N / (NS * R);
+    constexpr int ES = ROWS ? 1 : CB;
+    const int total = NB * (ROWS ? ntrans : CB);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int t, j;
+        if (ROWS) {
+            t = idx / NB;
+            j = idx - t * NB;
+        } else {
+            t = idx & (CB - 1);
+            j = idx / CB;
+        }
+        const int tbase = ROWS ? t * N : t;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[tbase + (j + r * NB) * ES];
+        const int k = j % NS;
+        if (NS > 1 && k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(&tw[r * k * STEP]);
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        Dft<R, INV>::run(v);
+        const int d = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[tbase + (d + r * NS) * ES] = v[r];
+    }
+}
+
+// All stages of the compiled plan (N, VAR) from stage S on; returns the
+// buffer holding the result.  Each stage ends with a __syncthreads().
+template <int N, int VAR, int S, bool INV, bool ROWS, int CB>
+__device__ __forceinline__ float2* fft_stages_ct(float2* src, float2* dst, const float2* tw,
+                                                 int ntrans) {
+    constexpr RadixPlan P = radix_plan(N, VAR);
+    if constexpr (S >= P.ns) {
+        return src;
+    } else {
+        constexpr int R = P.r[S];
+        constexpr int NS = plan_prefix(P, S);
+        fft_stage_ct<R, INV, ROWS, CB, N, NS>(src, dst, tw, ntrans);
+        __syncthreads();
+        return fft_stages_ct<N, VAR, S + 1, INV, ROWS, CB>(dst, src, tw, ntrans);
+    }
+}
+
+// Stages of an axis: the compiled plan (N > 0) or the axis' own plan.
+template <int N, int VAR, bool INV, bool ROWS, int CB = 1>
+__device__ __forceinline__ float2* axis_stages(float2* a, float2* b, const FftAxis& ax,
+                                               int ntrans, int tstride) {
+    if constexpr (N > 0) {
+        return fft_stages_ct<N, VAR, 0, INV, ROWS, CB>(a, b, ax.tw, ntrans);
+    } else {
+        return fft_stages<INV, ROWS, CB>(a, b, ax, ntrans, tstride);
+    }
+}
+
 // Rows [row0, row0 + rows) of slice `slice`: out = scale * (F or F^H along x) in.
-template <bool INV>
-static __device__ void fft_rows_block(const float2* in, float2* out, int ny, int nx, const FftAxis& ax,
+template <bool INV, int N = 0, int VAR = 0>
+static __device__ void fft_rows_block(const float2* in, float2* out, int ny, int nx_rt, const FftAxis& ax,
                                float scale, int row0, int rows, int slice, float2* sm) {
+    const int nx = N > 0 ? N : nx_rt;
     float2* A = sm;
     float2* Bf = sm + rows * nx;
     const size_t base = (size_t)slice * ny * nx + (size_t)row0 * nx;
@@ -224,8 +365,32 @@ static __device__ void fft_rows_block(const float2* in, float2* out, int ny, int
     batched_for<8, float2>(threadIdx.x, cnt, blockDim.x, [&](int i) { return in[base + i]; },
                            [&](int i, float2 v) { A[i] = v; });
     __syncthreads();
-    float2* res = fft_stages<INV, true>(A, Bf, ax, rows, nx);
+    float2* res = axis_stages<N, VAR, INV, true>(A, Bf, ax, rows, nx);
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[base + i] = cscale(res[i], scale);
+}
+
+// Rows with a compiled plan where the axis has one of the workloads' plans,
+// else the axis' own plan.
+template <bool INV, int N, int VAR>
+__device__ __forceinline__ bool fft_rows_ct(const float2* in, float2* out, int ny, int nx,
+                                            const FftAxis& ax, float scale, int row0, int rows,
+                                            int slice, float2* sm) {
+    if (nx != N || !axis_has_plan<N, VAR>(ax)) return false;
+    fft_rows_block<INV, N, VAR>(in, out, ny, nx, ax, scale, row0, rows, slice, sm);
+    return true;
+}
+
+template <bool INV>
+__device__ __forceinline__ void fft_rows_dispatch(const float2* in, float2* out, int ny, int nx,
+                                                  const FftAxis& ax, float scale, int row0,
+                                                  int rows, int slice, float2* sm) {
+    if (fft_rows_ct<INV, 256, 0>(in, out, ny, nx, ax, scale, row0, rows, slice, sm)) return;
+    if (fft_rows_ct<INV, 256, 1>(in, out, ny, nx, ax, scale, row0, rows, slice, sm)) return;
+    if (fft_rows_ct<INV, 320, 0>(in, out, ny, nx, ax, scale, row0, rows, slice, sm)) return;
+    if (fft_rows_ct<INV, 320, 2>(in, out, ny, nx, ax, scale, row0, rows, slice, sm)) return;
+    if (fft_rows_ct<INV, 128, 0>(in, out, ny, nx, ax, scale, row0, rows, slice, sm)) return;
+    if (fft_rows_ct<INV, 128, 1>(in, out, ny, nx, ax, scale, row0, rows, slice, sm)) return;
+    fft_rows_block<INV>(in, out, ny, nx, ax, scale, row0, rows, slice, sm);
 }
 
 // Shared memory of a column block: two ny x cb work buffers, the per-column
@@ -239,10 +404,10 @@ inline size_t col_pass_smem_bytes(int ny, int cb, int ntypes) {
 // tau partial sums go to tau_part[slice][cblk][B] (nparts blocks per slice).
 // Element idx of the block is row idx / CB, column idx % CB; blockDim.x must
 // be a multiple of 32 (and so of CB), so a thread keeps one column.
-template <int CB>
+template <int CB, int N = 0, int VAR = 0>
 __device__ __forceinline__ void col_pass_block_t(const ColArgs& a, int mode, int u_zero, int cblk,
                                                  int nparts, int slice, float2* sm) {
-    const int ny = a.ny, nx = a.nx;
+    const int ny = N > 0 ? N : a.ny, nx = a.nx;
     const int nt = a.ntypes;
     float2* A = sm;
     float2* Bf = sm + ny * CB;
@@ -264,11 +429,11 @@ __device__ __forceinline__ void col_pass_block_t(const ColArgs& a, int mode, int
                                [&](int idx, float2 v) { A[idx] = v; });
         __syncthreads();
         if (mode == COL_INV) {
-            float2* res = fft_stages<true, false, CB>(A, Bf, a.ax, CB, 0);
+            float2* res = axis_stages<N, VAR, true, false, CB>(A, Bf, a.ax, CB, 0);
             for (int idx = tid; idx < cnt; idx += nthr) a.out[gidx(idx)] = cscale(res[idx], a.scale_inv);
             return;
         }
-        U = fft_stages<false, false, CB>(A, Bf, a.ax, CB, 0);
+        U = axis_stages<N, VAR, false, false, CB>(A, Bf, a.ax, CB, 0);
         if (mode == COL_FWD) {
             for (int idx = tid; idx < cnt; idx += nthr) a.out[gidx(idx)] = cscale(U[idx], a.scale_fwd);
             return;
@@ -360,8 +525,44 @@ __device__ __forceinline__ void col_pass_block_t(const ColArgs& a, int mode, int
 
     // ---- inverse column transform (line 4: F^H of P^-1 z, or the return line)
     float2* other = (X == A) ? Bf : A;
-    float2* res = fft_stages<true, false, CB>(X, other, a.ax, CB, 0);
+    float2* res = axis_stages<N, VAR, true, false, CB>(X, other, a.ax, CB, 0);
     for (int idx = tid; idx < cnt; idx += nthr) a.out[gidx(idx)] = cscale(res[idx], a.scale_inv);
+}
+
+// Column block with a compiled plan where the column axis has one of the
+// workloads' plans, else with the axis' own plan.
+template <int CB, int N, int VAR>
+__device__ __forceinline__ bool col_pass_ct(const ColArgs& a, int mode, int u_zero, int cblk,
+                                            int nparts, int slice, float2* sm) {
+    if (a.ny != N || !axis_has_plan<N, VAR>(a.ax)) return false;
+    col_pass_block_t<CB, N, VAR>(a, mode, u_zero, cblk, nparts, slice, sm);
+    return true;
+}
+
+template <int CB>
+__device__ __forceinline__ void col_pass_dispatch_cb(const ColArgs& a, int mode, int u_zero,
+                                                     int cblk, int nparts, int slice, float2* sm) {
+    if (col_pass_ct<CB, 256, 0>(a, mode, u_zero, cblk, nparts, slice, sm)) return;
+    if (col_pass_ct<CB, 256, 1>(a, mode, u_zero, cblk, nparts, slice, sm)) return;
+    if (col_pass_ct<CB, 320, 0>(a, mode, u_zero, cblk, nparts, slice, sm)) return;
+    if (col_pass_ct<CB, 320, 2>(a, mode, u_zero, cblk, nparts, slice, sm)) return;
+    if (col_pass_ct<CB, 384, 0>(a, mode, u_zero, cblk, nparts, slice, sm)) return;
+    if (col_pass_ct<CB, 384, 2>(a, mode, u_zero, cblk, nparts, slice, sm)) return;
+    if (col_pass_ct<CB, 128, 0>(a, mode, u_zero, cblk, nparts, slice, sm)) return;
+    if (col_pass_ct<CB, 128, 1>(a, mode, u_zero, cblk, nparts, slice, sm)) return;
+    col_pass_block_t<CB>(a, mode, u_zero, cblk, nparts, slice, sm);
+}
+
+// The column pass with compiled plans for the workloads' column lengths.
+static __device__ void col_pass_dispatch(const ColArgs& a, int mode, int u_zero, int cblk,
+                                         int nparts, int slice, float2* sm) {
+    switch (a.cb) {
+        case 2: col_pass_dispatch_cb<2>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+        case 4: col_pass_dispatch_cb<4>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+        case 8: col_pass_dispatch_cb<8>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+        case 16: col_pass_dispatch_cb<16>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+        default: col_pass_block_t<1>(a, mode, u_zero, cblk, nparts, slice, sm); break;
+    }
 }
 
 static __device__ void col_pass_block(const ColArgs& a, int mode, int u_zero, int cblk, int nparts,

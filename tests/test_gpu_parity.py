@@ -102,6 +102,30 @@ def test_fft2_matches_oracle(ny, nx):
     plan.close()
 
 
+@pytest.mark.parametrize("ny,nx", [(256, 256), (384, 320), (320, 384), (128, 128)])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("cb", [2, 8, 16])
+def test_fft2_every_radix_plan_and_column_block(ny, nx, variant, cb):
+    """The lengths with compiled radix plans (128, 256, 320, 384): each radix plan on both
+    axes (compiled or run-time) and several column blocks, against the oracle's DFT."""
+    rng = np.random.default_rng(ny + nx + 10 * variant + cb)
+    plan = vb.Plan(ny, nx, "haar", 1, max_batch=2)
+    t = plan.tuning()
+    plan.set_tuning(dict(t, col_block=cb, radix_y=variant, radix_x=variant))
+    x = crand(rng, (2, ny, nx)).astype(np.complex64)
+    xd = dev(x)
+    out = torch.empty_like(xd)
+    back = torch.empty_like(xd)
+    vb.vdamp_fft2(plan.handle, 2, xd, out, inverse=False)
+    vb.vdamp_fft2(plan.handle, 2, out, back, inverse=True)
+    torch.cuda.synchronize()
+    x64 = x.astype(np.complex128)
+    ref = np.stack([O.fft2u(xi) for xi in x64])
+    assert rel(out.cpu().numpy(), ref) < 2e-6
+    assert rel(back.cpu().numpy(), x64) < 2e-6
+    plan.close()
+
+
 @pytest.mark.parametrize("wav,ny,nx,s", [("haar", 64, 64, 3), ("db4", 256, 256, 4),
                                          ("db4", 48, 80, 2), ("db4", 384, 320, 4),
                                          ("db4", 320, 320, 5), ("haar", 16, 16, 4),
