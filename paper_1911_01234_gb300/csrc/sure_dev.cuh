@@ -396,12 +396,22 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
     part_record_sums(a, part, b, slice, p0, p1, ps2, ph);
 }
 
-// The magnitudes a thread holds in registers: the smallest power of two that
-// covers the subband (a 100-coefficient subband runs one unrolled step, not 16).
+// The magnitudes a thread holds in registers.  One CTA per subband (FUSED):
+// the smallest power of two that covers the subband (a 100-coefficient
+// subband runs one unrolled step, not 16).  Parts of a lone slice: 16 or 32
+// (measured: the six variants cost the split sort 3 % per 256x256 solve,
+// and gain the one-CTA kernel 1 % at 256 x 320x320).
 template <bool FUSED>
 static __device__ void sure_sort_part_f(const SureArgs& a, const float2* rk, int part, int b,
                                         int slice, float* keys) {
     const int nb = a.off[b + 1] - a.off[b];
+    if (!FUSED) {
+        if (nb <= 16 * SURE_THREADS)
+            sure_sort_part_t<16, FUSED>(a, rk, part, b, slice, keys);
+        else
+            sure_sort_part_t<SORT_MAX_PER_THREAD, FUSED>(a, rk, part, b, slice, keys);
+        return;
+    }
     if (nb <= SURE_THREADS)
         sure_sort_part_t<1, FUSED>(a, rk, part, b, slice, keys);
     else if (nb <= 2 * SURE_THREADS)
