@@ -353,6 +353,34 @@ def run_mixed(args, vb, torch, flush_buf, stream):
             "tuning": tunings or None}
 
 
+def run_profile_case(args):
+    """Untimed solves of one workload for a profiler (no JSON contract line)."""
+    import torch
+    from paper_1911_01234_gb300 import binding as vb
+    from paper_1911_01234_gb300 import build
+    build.build()
+    vb.load()
+    wl = WL if args.profile_case == "plain" else synth.BATCH_320_DB4_5
+    nb = 1 if args.profile_case == "plain" else args.batched_slices
+    probs = [synth.make_problem(wl, i) for i in range(nb)]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
+    y, m, p = dev([q.y for q in probs]), dev([q.mask for q in probs]), dev([q.density for q in probs])
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
+    if args.tuning:
+        t = [int(v) for v in args.tuning.split(",")]
+        plan.set_tuning(t + [0] * (8 - len(t)))
+    for _ in range(args.warmup + args.steps):
+        plan.solve(y, m, p, [q.sigma for q in probs], wl.iters)
+    torch.cuda.synchronize()
+    st = vb.vdamp_device_status(plan.handle)[0]
+    plan.close()
+    print(json.dumps({"profile_case": args.profile_case, "slices": nb, "solves":
+                      args.warmup + args.steps, "tuning": args.tuning or "default",
+                      "status": st}), flush=True)
+    if st != vb.VDAMP_OK:
+        raise SystemExit(1)
+
+
 def run_fft_reference(vb, torch, stream):
     """The unitary 2D DFT of the library (row and column kernels, `vdamp_fft2`) timed beside
     cuFFT (torch.fft.fft2, norm="ortho") on the same data: a reference, not on the hot path
@@ -708,9 +736,15 @@ def main():
                     help="keep the plans' default launch shapes")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "steps"],
                     help="solve as one persistent cluster launch, or one kernel per step")
+    ap.add_argument("--profile-case", default="", choices=["", "plain", "batched"],
+                    help="only run solves of one workload, untimed (for ncu captures): "
+                         "--warmup + --steps solves of the 256x256 slice or of "
+                         "--batched-slices 320x320 slices, with --tuning if given")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case:
+        run_profile_case(args)
     else:
         run_gpu(args)
 
