@@ -236,7 +236,11 @@ vdamp_status vdamp_cnn_pack_weights(const float* w, int bands, int cin, int cout
 
 /* Weight and bias gradients of a convolution: dw[band][co][tap][ci] +=
  * sum_p x[p + offset(tap)][ci] dy[p][co], db[band][co] += sum_p dy[p][co]
- * (FP32, accumulated with atomics: summation order is not fixed). */
+ * (FP32; band < 32).  Each CTA's sums over its tiles are stored as records and
+ * then added per band in record order, so the result does not depend on the
+ * order in which CTAs run.  The records live in a device buffer the library
+ * grows on demand and keeps (about total_tiles (9 cin cout + cout) floats);
+ * calls that overlap on the GPU share it and must not run concurrently. */
 vdamp_status vdamp_cnn_wgrad(const void* x, int cin, int cin_pad, const void* dy, int cout,
                              int cout_pad, const int* images, int n_img, int total_tiles,
                              float* dw, float* db, void* stream);

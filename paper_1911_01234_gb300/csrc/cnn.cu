@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "../../include/vdamp.h"
 #include "cnn_dev.cuh"
@@ -326,14 +327,19 @@ __global__ void pack_weights_kernel(const float* w, int bands, int cin, int cout
 // ------------------------------------------------------ weight gradient ---
 // dw[band][co][tap][ci] += sum over the image pixels p of
 //   x[p + offset(tap)][ci] dy[p][co]       (zero outside the image)
-// db[band][co] += sum_p dy[p][co].  A CTA takes tiles of 128 pixels
-// grid-stride; thread j owns the (co, ci) pairs j, j + 256, ... for all nine
-// taps and sums them in FP32 registers over its tiles, then adds the sums to
-// dw with one atomic per output (also whenever the band changes).
+// db[band][co] += sum_p dy[p][co].  CTA i takes the WGRAD_CHUNK consecutive
+// tiles of 128 pixels from i WGRAD_CHUNK on; thread j owns the (co, ci) pairs
+// j, j + 256, ... for all nine taps and sums them in FP32 registers over the
+// tiles of one band, then stores the sums as record i WGRAD_CHUNK + s of
+// `part` (s counts the CTA's bands; pband names each record's band, -1 when
+// unused).  wgrad_reduce_kernel adds the records of each band in record
+// order: the gradient does not depend on the order in which CTAs finish.
+#define WGRAD_CHUNK 2
+#define WGRAD_MAX_BANDS 32
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16* x, const __nv_bfloat16* dy,
                                                     int cin, int cout, const CnnImage* img, int n_img,
-                                                    int total_tiles, float* dw, float* db) {
+                                                    int total_tiles, float* part, int* pband) {
     constexpr int PPT = (COUT * CIN + 255) / 256;   // (co, ci) pairs per thread
     __shared__ float sx[128][CIN + 1];
     __shared__ float sd[128][COUT + 1];
@@ -342,21 +348,27 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16* x, cons
     const int pairs = cout * cin;
     float acc[9][PPT];
     float accb = 0.f;
-    int band = -1;
+    int band = -1, seg = 0;
+    const size_t wtot = (size_t)cout * 9 * cin + cout;   // a record: weights, then biases
     auto flush = [&]() {
         if (band < 0) return;
+        const size_t rec = (size_t)blockIdx.x * WGRAD_CHUNK + seg;
+        float* dst = part + rec * wtot;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int q = tid + j * 256;
             if (q >= pairs) continue;
             const int co = q / cin, ci = q - co * cin;
 #pragma unroll
-            for (int tp = 0; tp < 9; ++tp)
-                atomicAdd(&dw[(((size_t)band * cout + co) * 9 + tp) * cin + ci], acc[tp][j]);
+            for (int tp = 0; tp < 9; ++tp) dst[((size_t)co * 9 + tp) * cin + ci] = acc[tp][j];
         }
-        if (tid < cout) atomicAdd(&db[(size_t)band * cout + tid], accb);
+        if (tid < cout) dst[(size_t)cout * 9 * cin + tid] = accb;
+        if (tid == 0) pband[rec] = band;
+        ++seg;
     };
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    const int t_begin = blockIdx.x * WGRAD_CHUNK;
+    const int t_end = min(total_tiles, t_begin + WGRAD_CHUNK);
+    for (int t = t_begin; t < t_end; ++t) {
         const CnnImage im = img[find_image(img, n_img, t)];
         if (im.band != band) {   // uniform over the CTA
             flush();
@@ -403,6 +415,36 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16* x, cons
         }
     }
     flush();
+    if (tid == 0)
+        for (int s2 = seg; s2 < WGRAD_CHUNK; ++s2) pband[(size_t)blockIdx.x * WGRAD_CHUNK + s2] = -1;
+}
+
+// dw[b][w] += sum over the records r with pband[r] == b, in increasing r, of
+// part[r][w] (w < cout 9 cin; the biases follow in part and go to db).
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, const int* pband,
+                                                           int nrec, int cout, int cin, float* dw,
+                                                           float* db) {
+    __shared__ float sacc[WGRAD_MAX_BANDS][256];
+    cudaGridDependencySynchronize();
+    const int tid = threadIdx.x;
+    const size_t nw = (size_t)cout * 9 * cin, wtot = nw + cout;
+    const size_t w = (size_t)blockIdx.x * 256 + tid;
+    for (int b = 0; b < WGRAD_MAX_BANDS; ++b) sacc[b][tid] = 0.f;
+    unsigned touched = 0u;
+    if (w < wtot) {
+        for (int r = 0; r < nrec; ++r) {
+            const int b = pband[r];
+            if (b < 0 || b >= WGRAD_MAX_BANDS) continue;
+            sacc[b][tid] += part[(size_t)r * wtot + w];
+            touched |= 1u << b;
+        }
+        while (touched) {
+            const int b = __ffs(touched) - 1;
+            touched &= touched - 1;
+            if (w < nw) dw[(size_t)b * nw + w] += sacc[b][tid];
+            else db[(size_t)b * cout + (w - nw)] += sacc[b][tid];
+        }
+    }
 }
 
 // ------------------------------------------------------- input planes ---
@@ -655,6 +697,33 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t st) {
 
 using namespace vdamp;
 
+// Device records of vdamp_cnn_wgrad, grown on demand and kept for the process
+// (one set for all calls: calls that overlap on the GPU would share it).
+static bool wgrad_workspace(size_t floats, size_t ints, float** part, int** pband) {
+    static std::mutex mu;
+    static float* p = nullptr;
+    static int* q = nullptr;
+    static size_t np = 0, nq = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (floats > np) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        np = 0;
+        if (cudaMalloc(&p, floats * sizeof(float)) != cudaSuccess) return false;
+        np = floats;
+    }
+    if (ints > nq) {
+        if (q) cudaFree(q);
+        q = nullptr;
+        nq = 0;
+        if (cudaMalloc(&q, ints * sizeof(int)) != cudaSuccess) return false;
+        nq = ints;
+    }
+    *part = p;
+    *pband = q;
+    return true;
+}
+
 static vdamp_status cnn_fail(const char* msg) {
     vdamp::set_last_error(msg);
     return VDAMP_EINVAL;
@@ -721,23 +790,29 @@ extern "C" vdamp_status vdamp_cnn_wgrad(const void* x, int cin, int cin_pad, con
         return cnn_fail("vdamp_cnn_wgrad: invalid argument");
     cudaStream_t st = (cudaStream_t)stream;
     const CnnImage* im = (const CnnImage*)images;
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::max(1, std::min(total_tiles, 4 * sms));
+    if (total_tiles < 1) return VDAMP_OK;
+    const int grid = (total_tiles + WGRAD_CHUNK - 1) / WGRAD_CHUNK;
+    const int nrec = grid * WGRAD_CHUNK;
+    const size_t wtot = (size_t)cout * 9 * cin + cout;
+    float* part = nullptr;
+    int* pband = nullptr;
+    if (!wgrad_workspace((size_t)nrec * wtot, (size_t)nrec, &part, &pband))
+        return cnn_fail("vdamp_cnn_wgrad: cannot allocate the gradient records");
     const __nv_bfloat16* xb = (const __nv_bfloat16*)x;
     const __nv_bfloat16* db16 = (const __nv_bfloat16*)dy;
     if (cin_pad == 16 && cout_pad == 32)
         launch_pdl(wgrad_kernel<16, 32>, dim3(grid), dim3(256), 0, st, xb, db16, cin, cout, im,
-                   n_img, total_tiles, dw, db);
+                   n_img, total_tiles, part, pband);
     else if (cin_pad == 32 && cout_pad == 32)
         launch_pdl(wgrad_kernel<32, 32>, dim3(grid), dim3(256), 0, st, xb, db16, cin, cout, im,
-                   n_img, total_tiles, dw, db);
+                   n_img, total_tiles, part, pband);
     else if (cin_pad == 32 && cout_pad == 16)
         launch_pdl(wgrad_kernel<32, 16>, dim3(grid), dim3(256), 0, st, xb, db16, cin, cout, im,
-                   n_img, total_tiles, dw, db);
+                   n_img, total_tiles, part, pband);
     else
         return cnn_fail("vdamp_cnn_wgrad: unsupported channel padding");
+    launch_pdl(wgrad_reduce_kernel, dim3((unsigned)((wtot + 255) / 256)), dim3(256), 0, st,
+               (const float*)part, (const int*)pband, nrec, cout, cin, dw, db);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VDAMP_OK : cnn_fail(cudaGetErrorString(e));
 }

@@ -234,3 +234,21 @@ def test_training_reduces_the_loss():
     # padded weights stay zero
     assert float(net.w[0][..., 3:].abs().max()) == 0.0
     assert float(net.w[4][:, 2:].abs().max()) == 0.0
+
+
+def test_training_is_reproducible():
+    """Two trainings from the same start on the same data give the same weights bit for bit:
+    the weight gradients are reduced in a fixed order (per-CTA records added by band in
+    record order), not by atomics whose order depends on scheduling."""
+    states = []
+    for _ in range(2):
+        net, im, r, w0, tau = _net_setup(seed=5)
+        B = 2
+        rd, w0d = torch.from_numpy(r).cuda(), torch.from_numpy(w0).cuda()
+        td = torch.from_numpy(tau).cuda()
+        for _ in range(20):
+            net.train_step(im, rd, w0d, td, B, 1e-3)
+        torch.cuda.synchronize()
+        states.append(net.state())
+    for k in states[0]:
+        assert np.array_equal(states[0][k], states[1][k]), k
