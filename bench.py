@@ -368,7 +368,7 @@ def run_profile_case(args):
     plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
     if args.tuning:
         t = [int(v) for v in args.tuning.split(",")]
-        plan.set_tuning(t + [0] * (8 - len(t)))
+        plan.set_tuning(t + vb.vdamp_plan_get_tuning(plan.handle)[len(t):])   # rest: defaults
     for _ in range(args.warmup + args.steps):
         plan.solve(y, m, p, [q.sigma for q in probs], wl.iters)
     torch.cuda.synchronize()
@@ -576,9 +576,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     if args.tuning:
         t = [int(v) for v in args.tuning.split(",")]
-        if len(t) == 7:
-            t.append(0)   # no SURE-parts entry given: parts by batch size
-        plan.set_tuning(t)
+        plan.set_tuning(t + vb.vdamp_plan_get_tuning(plan.handle)[len(t):])   # rest: defaults
         tuning = plan.tuning()
     else:
         # 40 iterations per candidate: shapes differ by a few per cent at one slice
@@ -731,7 +729,8 @@ def main():
                     help="skip the learned-denoiser measurement (trains for a few seconds)")
     ap.add_argument("--tuning", default="",
                     help="explicit launch shapes for the 256x256 plan (comma-separated, "
-                         "vdamp_plan_set_tuning order) instead of autotuning it")
+                         "vdamp_plan_set_tuning order; entries left out keep the plan's "
+                         "defaults) instead of autotuning it")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plans' default launch shapes")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "steps"],
