@@ -291,6 +291,34 @@ def test_onsager_linear_denoiser_and_identity():
     assert np.array_equal(O.onsager(r, r, np.zeros(len(sbs)), sbs), r)
 
 
+def test_onsager_of_the_soft_threshold_in_closed_form():
+    """Line 8 for the soft threshold: (soft(r, theta) - alpha r) / (1 - alpha) equals
+    r (1 - theta / ((1 - alpha) |r|)) above theta and -alpha / (1 - alpha) r at or below it,
+    the form the CUDA path evaluates from (theta, theta / (1 - alpha), alpha / (1 - alpha));
+    alpha of a coarse subband can be within 1e-4 of 1, where the two forms differ most."""
+    rng = np.random.default_rng(21)
+    sbs = O.subbands(16, 16, 2)
+    r = _crand(rng, 256) * 3.0
+    r[5] = 0.0
+    theta = np.linspace(0.05, 2.0, len(sbs))
+    w_hat = np.empty_like(r)
+    alpha = np.empty(len(sbs))
+    for sb in sbs:
+        rb = r[sb.offset:sb.offset + sb.size]
+        w_hat[sb.offset:sb.offset + sb.size] = O.soft(rb, theta[sb.index])
+        alpha[sb.index] = O.soft_divergence_mean(np.abs(rb), theta[sb.index])
+    alpha[0] = 1.0 - 1e-4   # a subband whose denoiser is nearly the identity
+    w_hat[sbs[0].offset:sbs[0].offset + sbs[0].size] = (
+        r[sbs[0].offset:sbs[0].offset + sbs[0].size])
+    theta[0] = 0.0
+    ref = O.onsager(w_hat, r, alpha, sbs)
+    a = np.abs(r)
+    th, al = O.expand(theta, sbs), O.expand(alpha, sbs)
+    c1, c2 = th / (1.0 - al), al / (1.0 - al)
+    closed = np.where(a > th, 1.0 - c1 / np.where(a > 0, a, 1.0), -c2) * r
+    assert np.allclose(closed, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
 def test_return_line_is_data_consistent():
     pr = synth.make_problem(synth.PLAIN_64_HAAR3)
     res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, 3)
