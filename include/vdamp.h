@@ -68,9 +68,9 @@ const char* vdamp_last_error(void);
  * Create a plan for ny x nx slices with wavelet `wavelet` at `levels` scales
  * (Algorithm 1 "Require": Psi; line 1: S = |Phi Psi^H|^2 is tabulated here
  * from its 1 + 3s unique columns, Sec. 2).  Sizes: ny and nx divisible by
- * 2^levels, of the form 2^a 3^b 5^c, 8 <= n <= 1024, with ny nx / 4 <= 32768
- * (the SURE search holds a whole finest subband in shared memory: 512 x 256
- * and 384 x 320 fit, 512 x 512 does not); 1 <= levels <= 6; 1 <= max_batch.  Allocates all device workspace for up to max_batch slices
+ * 2^levels, of the form 2^a 3^b 5^c, 8 <= n <= 1024; 1 <= levels <= 6;
+ * 1 <= max_batch.  Finest subbands above 32768 coefficients (ny nx > 131072,
+ * e.g. 512 x 512) always take the split SURE search (tuning entry 7 >= 4).  Allocates all device workspace for up to max_batch slices
  * on the current device.  On success *out holds the plan; on failure *out is
  * NULL and the status says why.
  */

@@ -319,7 +319,7 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     const size_t N = (size_t)ny * nx;
     const int max_band = (int)(N / 4);
     if (vdamp::sure_smem(max_band) > 227 * 1024)
-        return fail(VDAMP_EINVAL, "vdamp_plan_create: finest subband exceeds 32768 coefficients");
+        return fail(VDAMP_EINVAL, "vdamp_plan_create: the SURE search does not fit shared memory");
 
     vdamp_plan* p = new vdamp_plan();
     p->ny = ny;
@@ -783,6 +783,9 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
         split += vdamp::sure_parts(p->off[b + 1] - p->off[b], SURE_MAX_PARTS);
     a.max_parts = p->sure_parts ? p->sure_parts
                                 : ((c.batch * split > p->num_sms) ? 1 : SURE_MAX_PARTS);
+    // a finest subband above what one CTA holds is always split (SURE_MIN_PARTS_BIG or more)
+    if ((int)(p->N / 4) > SURE_SMALL_BAND && a.max_parts < SURE_MIN_PARTS_BIG)
+        a.max_parts = SURE_MAX_PARTS;
     c.pre();
     // one kernel (sort and search in one CTA) when every subband is one part, else two
     c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), c.st), VDAMP_KERNEL_SURE,
@@ -1250,6 +1253,7 @@ bool tuning_valid(const vdamp_plan* p, const int* t) {
     if (dto != 16 && dto != 32) return false;
     if (t[6] != 0 && t[6] != 1) return false;
     if (t[7] != 0 && t[7] != 1 && t[7] != 2 && t[7] != 4 && t[7] != SURE_MAX_PARTS) return false;
+    if ((int)(p->N / 4) > SURE_SMALL_BAND && t[7] != 0 && t[7] < SURE_MIN_PARTS_BIG) return false;
     if (vdamp::idwt_tile_smem(ito, p->filt.L) > p->smem_dwt ||
         vdamp::dwt_tile_smem(dto, p->filt.L) > p->smem_dwt)
         return false;

@@ -30,17 +30,19 @@ __global__ void __launch_bounds__(SURE_THREADS) sure_one_cta_kernel(const __grid
     sure_search_part_t<true>(a, a.k, 0, b, blockIdx.z, sm_keys);
 }
 
-size_t sure_smem(int max_band) { return sure_smem_bytes(max_band); }
+// Shared memory the SURE kernels are configured for: subbands held whole (up
+// to SURE_SMALL_BAND coefficients) or one part of a larger subband.
+size_t sure_smem(int max_band) { return sure_split_smem_bytes(max_band); }
 
 cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, cudaStream_t st) {
     if (a.max_parts == 1)
         return launch_pdl(sure_one_cta_kernel, dim3(1, a.B, batch), dim3(SURE_THREADS),
                           sure_smem_bytes(max_band), st, a);
     cudaError_t e = launch_pdl(sure_sort_kernel, dim3(a.max_parts, a.B, batch),
-                               dim3(SURE_THREADS), sure_smem_bytes(max_band), st, a);
+                               dim3(SURE_THREADS), sure_split_smem_bytes(max_band), st, a);
     if (e != cudaSuccess) return e;
     return launch_pdl(sure_search_kernel, dim3(a.max_parts, a.B, batch), dim3(SURE_THREADS),
-                      sure_search_smem_bytes(max_band), st, a);
+                      sure_split_search_smem_bytes(max_band), st, a);
 }
 
 cudaError_t configure_sure(size_t smem_bytes) {

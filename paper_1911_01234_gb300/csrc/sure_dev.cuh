@@ -51,6 +51,9 @@ namespace vdamp {
 #define SURE_THREADS 1024
 #define SURE_MAX_PARTS 8
 #define SURE_KEYS_PER_PART 2048
+#define SURE_SMALL_BAND (SORT_MAX_PER_THREAD * SURE_THREADS)   // subbands held whole in shared memory
+#define SURE_PART_CAP 32768               // keys one part of a larger subband may hold
+#define SURE_MIN_PARTS_BIG 4              // parts of a larger subband at least
 
 // Buckets per octave: about nb / 16, between 16 and 1024 (a power of two).
 __host__ __device__ inline int sort_log2_per_octave(int nb) {
@@ -76,6 +79,16 @@ inline size_t sure_smem_bytes(int max_band) {
     int np = 2;
     while (np < max_band) np <<= 1;
     return ((size_t)np + 4) * sizeof(float) + SORT_HIST_WORDS * sizeof(int);
+}
+
+// Shared memory of the split sort and search for subbands of up to max_band
+// coefficients: whole subbands up to SURE_SMALL_BAND, else one part's keys.
+inline size_t sure_split_smem_bytes(int max_band) {
+    if (max_band <= SURE_SMALL_BAND) return sure_smem_bytes(max_band);
+    return ((size_t)SURE_PART_CAP + 8) * sizeof(float) + SORT_HIST_WORDS * sizeof(int);
+}
+inline size_t sure_split_search_smem_bytes(int max_band) {
+    return ((size_t)(max_band <= SURE_SMALL_BAND ? max_band : SURE_PART_CAP) + 8) * sizeof(float);
 }
 
 __device__ __forceinline__ void record_numeric(int* status, int k) {
@@ -396,6 +409,176 @@ __device__ __forceinline__ void sure_sort_part_t(const SureArgs& a, const float2
     part_record_sums(a, part, b, slice, p0, p1, ps2, ph);
 }
 
+// Part `part` of a subband above SURE_SMALL_BAND coefficients (split search
+// only).  The magnitudes are read from global memory three times (maximum,
+// histogram, scatter) instead of being held in registers, and only the
+// part's own buckets go to shared memory, at keys[position - base].  Exact
+// zeros (a mostly or wholly zero subband) take the first positions without a
+// bucket; part 0 writes them and publishes its range from the last of them
+// on.  Buckets are sorted by the register networks or, above 32 keys, by
+// insertion in shared memory.  A part whose buckets hold more than
+// SURE_PART_CAP keys (magnitudes packed into a few buckets) records a numeric
+// failure and publishes nothing.
+static __device__ void sure_sort_part_big(const SureArgs& a, const float2* rk, int part, int b,
+                                          int slice, float* keys) {
+    __shared__ unsigned s_max_bits;
+    __shared__ int wsum[32];
+    __shared__ int s_qa, s_qb, s_zero, s_base, s_end;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    const int off = a.off[b], nb = a.off[b + 1] - off;
+    const int Q = sure_parts(nb, a.max_parts);
+    if (part >= Q) return;  // uniform over the CTA
+    const int lo_pos = (int)(((long long)part * nb + Q - 1) / Q);
+    const int hi_pos = (int)(((long long)(part + 1) * nb + Q - 1) / Q);
+    int* hist = reinterpret_cast<int*>(keys + SURE_PART_CAP + 8);
+    float* out = a.sorted + (size_t)slice * a.N + off;
+    const float2* r = rk + (size_t)slice * a.N + off;
+    const size_t rec = ((size_t)slice * a.B + b) * SURE_MAX_PARTS + part;
+
+    if (tid == 0) {
+        s_max_bits = 0u;
+        s_qa = 0;
+        s_qb = 0;
+        s_zero = 0;
+    }
+    unsigned mx = 0u;
+    for (int i = tid; i < nb; i += nthr) mx = max(mx, __float_as_uint(cabs_f(r[i])));
+    const int lpo = sort_log2_per_octave(nb);
+    const int nbk = 16 << lpo;
+    const int shift = 23 - lpo;
+    for (int i = tid; i < nbk + (nbk >> 5); i += nthr) hist[i] = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if (lane == 0) atomicMax(&s_max_bits, mx);
+    __syncthreads();
+    const unsigned span = (unsigned)nbk << shift;
+    const unsigned lo_bits = s_max_bits + 1u > span ? s_max_bits + 1u - span : 0u;
+    auto bucket = [&](unsigned u) -> int {
+        return u < lo_bits ? 0 : (int)((u - lo_bits) >> shift);
+    };
+    int nz = 0;
+    for (int i = tid; i < nb; i += nthr) {
+        const unsigned u = __float_as_uint(cabs_f(r[i]));
+        if (u == 0u) ++nz;
+        else atomicAdd(&hist[HIX(bucket(u))], 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    if (lane == 0 && nz) atomicAdd(&s_zero, nz);
+    __syncthreads();
+    const int z = s_zero;
+    {   // exclusive scan of the counts from position z on; each thread owns `per` buckets
+        const int per = nbk >= nthr ? nbk / nthr : 1;
+        const int b0 = min(tid * per, nbk);
+        const int nq = min(per, nbk - b0);
+        int loc = 0;
+        for (int q = 0; q < nq; ++q) loc += hist[HIX(b0 + q)];
+        int inc = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            int v = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        int run = z + inc - loc + (warp > 0 ? wsum[warp - 1] : 0);
+        int na = 0, nbq = 0;
+        for (int q = 0; q < nq; ++q) {
+            const int c = hist[HIX(b0 + q)];
+            hist[HIX(b0 + q)] = run;
+            na += run < lo_pos;
+            nbq += run < hi_pos;
+            run += c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            na += __shfl_xor_sync(0xffffffffu, na, o);
+            nbq += __shfl_xor_sync(0xffffffffu, nbq, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&s_qa, na);
+            atomicAdd(&s_qb, nbq);
+        }
+    }
+    __syncthreads();
+    const int qa = s_qa, qb = s_qb;
+    if (tid == 0) {   // the part's buckets occupy positions [base, end)
+        s_base = qb > qa ? hist[HIX(qa)] : z;
+        s_end = qb > qa ? (qb < nbk ? hist[HIX(qb)] : nb) : z;
+    }
+    __syncthreads();
+    const int base = s_base, end = s_end;
+    if (end - base > SURE_PART_CAP) {
+        if (tid == 0) {
+            record_numeric(a.status, a.k);
+            a.partrec[rec] = make_double4_32a(-1.0, -1.0, 0.0, 0.0);
+        }
+        return;
+    }
+    if (part == 0)
+        for (int i = tid; i < z; i += nthr) out[i] = 0.f;
+    for (int i = tid; i < nb; i += nthr) {
+        const float x = cabs_f(r[i]);
+        const unsigned u = __float_as_uint(x);
+        if (u == 0u) continue;
+        const int q = bucket(u);
+        if (q >= qa && q < qb) keys[atomicAdd(&hist[HIX(q)], 1) - base] = x;
+    }
+    __syncthreads();
+    // hist[q] now holds the end of bucket q for the part's buckets
+    float ps2 = 0.f, ph = 0.f;
+    for (int q = qa + tid; q < qb; q += nthr) {
+        const int s0 = q > qa ? hist[HIX(q - 1)] : base, s1 = hist[HIX(q)];
+        const int n = s1 - s0;
+        if (n <= 0) continue;
+        float* kin = keys + (s0 - base);
+        float* kout = out + s0;
+        if (n <= 2) {
+            sort_bucket_regs<2, false>(kin, kout, 0, n, ps2, ph);
+        } else if (n <= 4) {
+            sort_bucket_regs<4, false>(kin, kout, 0, n, ps2, ph);
+        } else if (n <= 8) {
+            sort_bucket_regs<8, false>(kin, kout, 0, n, ps2, ph);
+        } else if (n <= 16) {
+            sort_bucket_regs<16, false>(kin, kout, 0, n, ps2, ph);
+        } else if (n <= 32) {
+            sort_bucket_regs<32, false>(kin, kout, 0, n, ps2, ph);
+        } else {
+            for (int i = 1; i < n; ++i) {
+                const float x = kin[i];
+                int j = i - 1;
+                while (j >= 0 && kin[j] > x) {
+                    kin[j + 1] = kin[j];
+                    --j;
+                }
+                kin[j + 1] = x;
+            }
+            for (int i = 0; i < n; ++i) {
+                const float x = kin[i];
+                kout[i] = x;
+                ps2 += x * x;
+                ph += x > 0.f ? __frcp_rn(x) : 0.f;
+            }
+        }
+    }
+    // part 0 starts at the last zero (the search needs one key to offer theta >= max a)
+    const int p0 = part == 0 ? (z > 0 ? z - 1 : 0) : base;
+    const int p1 = qb > qa ? end : (part == 0 ? z : p0);
+    part_record_sums(a, part, b, slice, p0, p1, ps2, ph);
+}
+
 // The magnitudes a thread holds in registers.  One CTA per subband (FUSED):
 // the smallest power of two that covers the subband (a 100-coefficient
 // subband runs one unrolled step, not 16).  Parts of a lone slice: 16 or 32
@@ -406,7 +589,9 @@ static __device__ void sure_sort_part_f(const SureArgs& a, const float2* rk, int
                                         int slice, float* keys) {
     const int nb = a.off[b + 1] - a.off[b];
     if (!FUSED) {
-        if (nb <= 16 * SURE_THREADS)
+        if (nb > SURE_SMALL_BAND)
+            sure_sort_part_big(a, rk, part, b, slice, keys);
+        else if (nb <= 16 * SURE_THREADS)
             sure_sort_part_t<16, FUSED>(a, rk, part, b, slice, keys);
         else
             sure_sort_part_t<SORT_MAX_PER_THREAD, FUSED>(a, rk, part, b, slice, keys);

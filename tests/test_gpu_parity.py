@@ -441,3 +441,59 @@ def test_fused_and_stepwise_paths_agree(wl):
         assert rel(fused["x_hat_iters"].cpu().numpy()[k, 0], step["x_hat_iters"].cpu().numpy()[k, 0]) < 1e-5, k
         assert rel(fused["tau"].cpu().numpy()[0, k], step["tau"].cpu().numpy()[0, k]) < 1e-5, k
     plan.close()
+
+
+def test_paper_size_512_haar4():
+    """The paper's image size and wavelet (512x512, Haar, 4 levels; Sec. 3): finest subbands
+    of 65536 coefficients, more than one CTA holds, so their SURE search is split into parts
+    whose magnitudes stream from global memory.  Teacher-forced steps against the oracle, a
+    batch of three equal to single-slice solves bit for bit, and an empty mask (all-zero
+    subbands: the exact zeros take no bucket) gives zero."""
+    wl = synth.Workload("t", 78, 512, 512, 20, True, "haar", 4, 5.0, 5.0, 24, 30.0, 30.0, 3, 1)
+    prs = [synth.make_problem(wl, i) for i in range(3)]
+    pr = prs[0]
+    ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, 3, ops=ops)
+    plan = vb.Plan(512, 512, "haar", 4, max_batch=3)
+    N, B = 512 * 512, plan.B
+    y, m, p = _problem_on_device(pr)
+    y64 = np.where(pr.mask == 1, pr.y.astype(np.complex128), 0.0)
+    r = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    rn = torch.empty_like(r)
+    tau = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+    for k in (0, 2):
+        rt32 = res.records[k].r_tilde.astype(np.complex64)
+        rec = O.iterate(rt32.astype(np.complex128), y64, ops, float(pr.sigma) ** 2)
+        vb.vdamp_iterate(plan.handle, 1, dev(rt32[None]), y, m, p, [pr.sigma], r, tau, thr, alpha,
+                         rn)
+        torch.cuda.synchronize()
+        assert rel(r.cpu().numpy()[0], rec.r) < 1e-5, k
+        tg = tau.cpu().numpy()[0]
+        assert tau_ok(tg, rec.tau), (k, rel(tg, rec.tau))
+        ok, band = theta_ok(rec.r, ops.sbs, rec.tau, thr.cpu().numpy()[0], rec.theta)
+        assert ok, (k, band)
+        if np.allclose(thr.cpu().numpy()[0], rec.theta, rtol=1e-3, atol=0):
+            assert np.max(np.abs(alpha.cpu().numpy()[0] - rec.alpha)) < 1e-4, k
+            assert rel(rn.cpu().numpy()[0], O.next_r_tilde(rec, ops)) < 1e-4, k
+    assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+
+    yb = dev(np.stack([q.y for q in prs]))
+    mb = dev(np.stack([q.mask for q in prs]))
+    pb = dev(np.stack([q.density for q in prs]))
+    sig = [q.sigma for q in prs]
+    bat = plan.solve(yb, mb, pb, sig, 3)
+    for i in range(3):
+        one = plan.solve(yb[i:i + 1].contiguous(), mb[i:i + 1].contiguous(),
+                         pb[i:i + 1].contiguous(), [sig[i]], 3)
+        torch.cuda.synchronize()
+        assert torch.equal(one["x_hat"][0], bat["x_hat"][i]), i
+        assert torch.equal(one["thr"][0], bat["thr"][i]), i
+    assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+
+    zero = torch.zeros((1, 512, 512), dtype=torch.uint8, device="cuda")
+    out = plan.solve(y, zero, p, [pr.sigma], 2)
+    torch.cuda.synchronize()
+    assert torch.all(out["x_hat"] == 0) and torch.all(out["tau"] == 0)
+    assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+    plan.close()

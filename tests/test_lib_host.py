@@ -57,7 +57,6 @@ def test_spectra_match_bruteforce_s(lib, name, ny, nx, s):
     (7 * 16, 64, "db4", 4),  # 7 is not an FFT radix
     (64, 4, "haar", 1),      # too small
     (2048, 64, "haar", 1),   # too large
-    (512, 512, "db4", 4),    # finest subband above the SURE shared-memory bound
     (64, 64, "db4", 3, 0),   # max_batch < 1
 ])
 def test_plan_create_rejects_bad_arguments(lib, args):
