@@ -67,10 +67,6 @@ __host__ __device__ inline int sure_parts(int nb, int max_parts) {
     return q < 1 ? 1 : (q > max_parts ? max_parts : q);
 }
 
-// Shared memory of the search: the keys of a part and the one below it.
-inline size_t sure_search_smem_bytes(int max_band) {
-    return ((size_t)max_band + 4) * sizeof(float);
-}
 
 // Shared memory of the sort (and an upper bound for the search): keys padded
 // to a power of two, four spare slots (the one-CTA sort + search keeps its
@@ -87,6 +83,7 @@ inline size_t sure_split_smem_bytes(int max_band) {
     if (max_band <= SURE_SMALL_BAND) return sure_smem_bytes(max_band);
     return ((size_t)SURE_PART_CAP + 8) * sizeof(float) + SORT_HIST_WORDS * sizeof(int);
 }
+// Shared memory of the search: the keys of a part and the one below it.
 inline size_t sure_split_search_smem_bytes(int max_band) {
     return ((size_t)(max_band <= SURE_SMALL_BAND ? max_band : SURE_PART_CAP) + 8) * sizeof(float);
 }
