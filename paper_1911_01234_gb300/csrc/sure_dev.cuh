@@ -578,9 +578,10 @@ static __device__ void sure_sort_part_big(const SureArgs& a, const float2* rk, i
 
 // The magnitudes a thread holds in registers.  One CTA per subband (FUSED):
 // the smallest power of two that covers the subband (a 100-coefficient
-// subband runs one unrolled step, not 16).  Parts of a lone slice: 16 or 32
-// (measured: the six variants cost the split sort 3 % per 256x256 solve,
-// and gain the one-CTA kernel 1 % at 256 x 320x320).
+// subband runs one unrolled step, not 16).  Split parts: 16 or 32, and
+// subbands above SURE_SMALL_BAND stream from global memory (measured: the
+// six register variants cost the split sort 3 % per 256x256 solve, and gain
+// the one-CTA kernel 1 % at 256 x 320x320).
 template <bool FUSED>
 static __device__ void sure_sort_part_f(const SureArgs& a, const float2* rk, int part, int b,
                                         int slice, float* keys) {
