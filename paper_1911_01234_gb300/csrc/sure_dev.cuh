@@ -29,8 +29,12 @@
 // bucket 0) are exactly ordered.  Each
 // bucket belongs to the part in which its first position falls, and is
 // sorted in registers by a bitonic network of 2, 4, 8, 16 or 32 keys (the
-// smallest that holds it) or, above 32 keys, in shared memory.  A bucket above SORT_MAX_BUCKET keys (ties, or a degenerate subband)
-// sends the whole subband to a bitonic sort done by part 0.
+// smallest that holds it) or, above 32 keys, in shared memory.  A bucket
+// above SORT_MAX_BUCKET keys (ties, or a degenerate subband) sends the whole
+// subband to a bitonic sort done by part 0.  Subbands above SURE_SMALL_BAND
+// coefficients (512x512 images) do not fit one CTA's shared memory: their
+// parts stream the magnitudes from global memory and keep only their own
+// buckets (sure_sort_part_big).
 //
 // Precision: magnitudes, keys and per-thread partial sums are FP32; the
 // cross-warp scans of C and H, tau, theta and alpha of the chosen interval
