@@ -190,7 +190,7 @@ struct SureArgs {
     double* alpha_out;
     float4* coef;         // [batch][B]
     int* status;          // [0] code, [1] first bad iteration
-    int max_parts;        // sort parts per subband at most (1: one CTA sorts and searches)
+    int max_parts;        // sort parts per subband at most (1 when slices fill the GPU)
     double4_32a* partrec; // [batch][B][SURE_MAX_PARTS] (first, end, sum a^2, sum 1/a) of a part
     double4_32a* bestrec; // [batch][B][SURE_MAX_PARTS] (SURE, theta, H, m) of a part's best
     unsigned* counter;    // [batch][B] search parts done (returns to 0 after each search)
