@@ -53,10 +53,10 @@ def config_block(slices_per_gpu, world):
 class OracleRunner:
     """The FP64 oracle iterating the same workload; operators (S) built once."""
 
-    def __init__(self):
+    def __init__(self, slice_idx=0):
         from oracle import vdamp_oracle as O
         self.O = O
-        self.pr = synth.make_problem(WL)
+        self.pr = synth.make_problem(WL, slice_idx)
         self.ops = O.make_operators(self.pr.mask, self.pr.density, self.pr.wavelet,
                                     self.pr.levels)
         self.y = np.where(self.pr.mask == 1, self.pr.y.astype(np.complex128), 0.0)
@@ -83,29 +83,65 @@ class OracleRunner:
                 return done, el
 
 
+_START = None
+
+
+def _oracle_init(barrier):
+    global _START
+    _START = barrier
+
+
+def _oracle_worker(job):
+    """One host process: the oracle on its own slice, `warm` untimed seconds, then the
+    timed budgets one after another (started together with the other workers)."""
+    slice_idx, warm, budgets = job
+    runner = OracleRunner(slice_idx)
+    if warm > 0:
+        runner.run(warm)
+    if _START is not None:
+        _START.wait(timeout=300)
+    return [runner.run(b) for b in budgets]
+
+
+def oracle_throughput(warm, budgets, workers):
+    """FP64 oracle slice-iterations/s over all `workers` host processes (one slice each;
+    spawned, so safe after CUDA is initialised).  Returns (per-budget list of
+    (iterations summed over workers, slowest worker's seconds), workers used)."""
+    if workers > 1:
+        try:
+            import multiprocessing as mp
+            ctx = mp.get_context("spawn")
+            barrier = ctx.Barrier(workers)
+            with ctx.Pool(workers, initializer=_oracle_init, initargs=(barrier,)) as pool:
+                job = pool.map_async(_oracle_worker, [(i, warm, budgets) for i in range(workers)])
+                res = job.get(timeout=warm + sum(budgets) + 600)
+            steps = [(sum(r[j][0] for r in res), max(r[j][1] for r in res))
+                     for j in range(len(budgets))]
+            return steps, workers
+        except Exception:
+            pass   # no process pool here: one process
+    return _oracle_worker((0, warm, budgets)), 1
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    runner = OracleRunner()
     budget = max(0.2, min(args.ref_step_seconds, 150.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        runner.run(budget)
-    total_it, total_s = 0, 0.0
-    for _ in range(args.steps):
-        it, el = runner.run(budget)
-        total_it += it
-        total_s += el
+    steps, cores = oracle_throughput(budget * args.warmup, [budget] * args.steps,
+                                     args.ref_workers or os.cpu_count() or 1)
+    total_it = sum(it for it, _ in steps)
+    total_s = sum(el for _, el in steps)
     value = total_it / total_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_block(1, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} steps of ~{budget:.2f} s of FP64 numpy "
-                                       f"oracle iterations on the 256x256 slice "
-                                       f"({total_it} iterations)"},
+                                       f"oracle iterations, one 256x256 slice per host "
+                                       f"process ({cores} processes, {total_it} iterations)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -688,10 +724,10 @@ def run_gpu(args):
                         "d2h_bytes_per_step": d2h},
                 "roofline": roofline,
                 "wall_s_timed": wall}
-        # the batched, mixed and learned measurements are single-GPU blocks: at
-        # N > 1 the line holds the replicated solve only
+        # the batched, mixed and learned measurements and the host baseline are
+        # single-GPU blocks: at N > 1 the line holds the replicated solve only
         if world > 1:
-            args.no_batched = args.no_learned = True
+            args.no_batched = args.no_learned = args.no_cpu_baseline = True
         if not args.no_batched:
             line["batched"] = run_batched(args, vb, torch, flush_buf, stream)
             line["mixed"] = run_mixed(args, vb, torch, flush_buf, stream)
@@ -701,10 +737,14 @@ def run_gpu(args):
             if not args.no_batched:
                 line["learned_batched"] = run_learned_batched(args, vb, torch, flush_buf, stream)
         if not args.no_cpu_baseline:
-            it, el = OracleRunner().run(args.cpu_seconds)
-            line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"{it} FP64 numpy oracle iterations of the same "
-                                              f"256x256 slice in {el:.1f} s (one core)"}
+            steps, cores = oracle_throughput(1.0, [args.cpu_seconds],
+                                             args.ref_workers or os.cpu_count() or 1)
+            it, el = steps[0]
+            line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": cores,
+                                    "kind": "oracle",
+                                    "sample": f"{it} FP64 numpy oracle iterations in {el:.1f} s, "
+                                              f"one 256x256 slice per host process "
+                                              f"({cores} processes)"}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
@@ -720,6 +760,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--ref-workers", type=int, default=0,
+                    help="host processes of the oracle baseline (0: one per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 256 x 320x320 batched measurement")
