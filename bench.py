@@ -3,8 +3,10 @@
 One step = one vdamp_solve of the whole hot path (30 iterations of lines 3-8
 plus the return line) on one synthetic slice whose inputs are resident in
 HBM.  Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on
-the host cores instead.  Under torchrun each rank solves its own slice
-(independent replicas, weak scaling, no collective on the data path).
+the host cores instead.  Under torchrun each rank solves its own 256x256 slice
+for the headline (weak scaling), and the batched and mixed blocks partition
+their slices over the ranks (balanced by pixels x iterations) and gather the
+results on rank 0; no collective touches the data path.
 """
 import os
 
@@ -237,6 +239,97 @@ MEASURED_TRAFFIC = {
 }
 
 
+def taps(wavelet):
+    return 2 if wavelet == "haar" else 8
+
+
+def iteration_bytes(N, n):
+    """Algorithmic bytes of one slice-iteration under the iteration's two global sync
+    points: r_k in and r_{k+1} out (complex64), y and 1/p on Omega, the mask as bits."""
+    return 16 * N + 12 * n + N / 8
+
+
+def iteration_flops(ny, nx, levels, L):
+    """Algorithmic FLOPs of one slice-iteration: the FFT pair (5 N log2 N each), the DWT
+    pair (complex data, real L-tap filters, two 1D passes per scale: 8 L N_j per transform
+    summed over the scales), and ~40 N elementwise (tau terms, line 8, threshold)."""
+    N = ny * nx
+    dwt = sum(8 * L * N / 4 ** j for j in range(levels))
+    return 2 * 5 * N * math.log2(N) + 2 * dwt + 40 * N
+
+
+def kernel_flops(kind, ny, nx, levels, L):
+    """Algorithmic FLOPs per launch of one slice (the same kinds as algorithmic_bytes)."""
+    N = ny * nx
+    lv = [N / 4 ** (j - 1) for j in range(1, levels + 1)]
+    if kind == "fft_rows":
+        return 5 * N * math.log2(nx)
+    if kind == "col_pass":
+        return 2 * 5 * N * math.log2(ny) + 30 * N
+    if kind in ("idwt", "dwt"):
+        return statistics.mean(8 * L * v for v in lv)
+    if kind == "sure":          # |r|, the prefix sums and one candidate quadratic per coefficient
+        return 20 * N
+    return 0.0
+
+
+def bound_of(byts, flops, bw_gbs, p_tflops):
+    """'hbm' or 'alu': the larger of the two lower bounds on the time."""
+    if not p_tflops:
+        return "hbm"
+    return "alu" if flops / (p_tflops * 1e12) > byts / (bw_gbs * 1e9) else "hbm"
+
+
+def iteration_roofline(s_per_slice_iter, ny, nx, n, levels, L, bw_gbs, p_fp32_tflops):
+    """Whole-iteration roofline: T_roof = max(B_alg / BW, F_alg / P_fp32) against the
+    measured time per slice-iteration, and the two partial fractions."""
+    N = ny * nx
+    b, f = iteration_bytes(N, n), iteration_flops(ny, nx, levels, L)
+    t_hbm = b / (bw_gbs * 1e9)
+    t_alu = f / (p_fp32_tflops * 1e12) if p_fp32_tflops else 0.0
+    t_roof = max(t_hbm, t_alu)
+    return {"bytes_per_slice_iter": b, "flops_per_slice_iter": f,
+            "intensity_flop_per_byte": f / b, "us_per_slice_iter": s_per_slice_iter * 1e6,
+            "t_roof_us": t_roof * 1e6, "frac": t_roof / s_per_slice_iter,
+            "hbm_frac": t_hbm / s_per_slice_iter,
+            "alu_frac": (t_alu / s_per_slice_iter) if p_fp32_tflops else None,
+            "bound": "alu" if t_alu > t_hbm else "hbm",
+            "peaks": {"hbm_gbs": bw_gbs, "fp32_tflops": p_fp32_tflops}}
+
+
+def partition_slices(costs, world):
+    """Slices to ranks, balanced by cost (pixels x iterations): longest first, each to the
+    least-loaded rank (ties to the lower rank).  Returns one ascending index list per rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += costs[i]
+    return [sorted(x) for x in out]
+
+
+def gather_by_slice(parts, world, rank, local, total):
+    """Host gather of per-slice results to rank 0: `local` maps this rank's slice indices
+    (parts[rank]) to result objects; rank 0 gets them back in slice order [0, total)."""
+    if world <= 1:
+        got = [local]
+    else:
+        import torch.distributed as dist
+        got = [None] * world if rank == 0 else None
+        dist.gather_object(local, got, dst=0)
+    if rank != 0:
+        return None
+    out = [None] * total
+    for r in range(world):
+        for i, v in got[r].items():
+            assert out[i] is None and i in parts[r], i
+            out[i] = v
+    assert all(v is not None for v in out)
+    return out
+
+
 def slowest_rank_ms(local_ms, world, device=None):
     """Max over ranks of the timed region (ms); the job's clock is its slowest rank."""
     if world <= 1:
@@ -277,108 +370,167 @@ def source_hash(kernel="idwt"):
     return h.hexdigest()[:16]
 
 
-def run_batched(args, vb, torch, flush_buf, stream):
-    """Batched workload: 256 slices of 320x320, db4 s=5, R=6, 30 dB, 20 iterations."""
+def timed_steps(torch, fn, steps, flush_buf, stream, world, warm=2):
+    """Events around each of `steps` calls after `warm` untimed ones, L2 flushed before
+    each (outside the events), barrier and synchronize on both sides; returns
+    (this rank's total ms, the slowest rank's total ms)."""
+    import torch.distributed as dist
+    for i in range(warm):
+        flush_buf.fill_(float(i))
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush_buf.fill_(float(i))
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    return ms, slowest_rank_ms(ms, world, device="cuda")
+
+
+def dominant_kernel(vb, plan, step, reps=1):
+    """Per-kind event times of `reps` directly launched solves: (kind, {kind: (ms, n)})."""
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 1)
+    vb.vdamp_kernel_times(plan.handle)
+    for _ in range(reps):
+        step()
+    kt = vb.vdamp_kernel_times(plan.handle)
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 0)
+    dom = max((k for k in kt if kt[k][1] > 0 and k != "other"), key=lambda k: kt[k][0])
+    return dom, kt
+
+
+def kernel_roofline(dom, kt, wl, slices, n_per_slice, peaks_, reps=1):
+    """The dominant kernel's roofline: algorithmic bytes (and FLOPs) per launch over its
+    mean event-timed launch, against the measured HBM peak (or FP32 peak if ALU-bound)."""
+    hbm, src, p32 = peaks_["hbm_gbs"], peaks_["hbm_source"], peaks_.get("fp32_tflops")
+    N = wl.ny * wl.nx
+    L = taps(wl.wavelet)
+    avg_s = kt[dom][0] / kt[dom][1] / 1e3
+    if dom == "fused":
+        byt = slices * wl.iters * iteration_bytes(N, n_per_slice)
+        fl = slices * wl.iters * iteration_flops(wl.ny, wl.nx, wl.levels, L)
+    else:
+        byt = slices * algorithmic_bytes(dom, N, n_per_slice, wl.levels)
+        fl = slices * kernel_flops(dom, wl.ny, wl.nx, wl.levels, L)
+    bound = bound_of(byt, fl, hbm, p32)
+    tot = sum(x[0] for x in kt.values())
+    out = {"bound": bound, "kernel": dom, "avg_launch_us": avg_s * 1e6,
+           "algorithmic_bytes_per_launch": byt, "algorithmic_flops_per_launch": fl,
+           "time_share": {k: round(v[0] / tot, 4) for k, v in kt.items()},
+           "launches_per_step": {k: v[1] // reps for k, v in kt.items()},
+           "avg_us_by_kernel": {k: round(1e3 * v[0] / v[1], 2) for k, v in kt.items() if v[1]}}
+    if bound == "hbm":
+        out.update(achieved=byt / avg_s / 1e9, peak=hbm, peak_source=src, unit="GB/s",
+                   frac=byt / avg_s / 1e9 / hbm)
+    else:
+        out.update(achieved=fl / avg_s / 1e12, peak=p32, peak_source="measured (vdamp_fma_peak)",
+                   unit="TFLOP/s", frac=fl / avg_s / 1e12 / p32)
+    out["hbm_frac"] = byt / avg_s / 1e9 / hbm
+    out["alu_frac"] = (fl / avg_s / 1e12 / p32) if p32 else None
+    return out
+
+
+def run_batched(args, vb, torch, flush_buf, stream, rank, world, peaks_):
+    """Batched workload: 256 slices of 320x320, db4 s=5, R=6, 30 dB, 20 iterations.  At
+    N > 1 the slices are partitioned over the ranks (balanced by pixels x iterations),
+    every rank solves its share, and x_hat, tau, theta, alpha are gathered on rank 0."""
     wl = synth.BATCH_320_DB4_5
     nb = args.batched_slices
-    probs = [synth.make_problem(wl, i) for i in range(nb)]
+    N = wl.ny * wl.nx
+    parts = partition_slices([N * wl.iters] * nb, world)
+    mine = parts[rank]
+    probs = [synth.make_problem(wl, i) for i in mine]
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
     y, m, p = dev([q.y for q in probs]), dev([q.mask for q in probs]), dev([q.density for q in probs])
     sig = [q.sigma for q in probs]
     n_samp = int(sum(int(q.mask.sum()) for q in probs))
-    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
+    nm = len(mine)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nm)
     if args.path != "auto":
         vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 1 if args.path == "fused" else 0)
-    tuning = None if args.no_autotune else plan.autotune(nb, trials=3, stream=stream.cuda_stream)
+    tuning = None if args.no_autotune else plan.autotune(nm, trials=3, stream=stream.cuda_stream)
     K = wl.iters
-    x_hat = torch.empty((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
-    tau = torch.empty((nb, K, plan.B), dtype=torch.float64, device="cuda")
+    x_hat = torch.empty((nm, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+    tau = torch.empty((nm, K, plan.B), dtype=torch.float64, device="cuda")
     thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
 
     def step():
-        vb.vdamp_solve(plan.handle, nb, y, m, p, sig, K, None, x_hat, tau, thr, alpha,
+        vb.vdamp_solve(plan.handle, nm, y, m, p, sig, K, None, x_hat, tau, thr, alpha,
                        stream=stream.cuda_stream)
-    for i in range(2):
-        flush_buf.fill_(float(i))
-        step()
-    torch.cuda.synchronize()
     steps = args.batched_steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    for i in range(steps):
-        flush_buf.fill_(float(i))
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    _, max_ms = timed_steps(torch, step, steps, flush_buf, stream, world)
     if vb.vdamp_device_status(plan.handle)[0] != vb.VDAMP_OK:
         raise RuntimeError("batched solve reported a non-finite tau or alpha")
-    # dominant kernel over one timed solve
-    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 1)
-    vb.vdamp_kernel_times(plan.handle)
-    step()
-    kt = vb.vdamp_kernel_times(plan.handle)
-    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 0)
-    dom = max((k for k in kt if kt[k][1] > 0 and k != "other"), key=lambda k: kt[k][0])
-    avg_s = kt[dom][0] / kt[dom][1] / 1e3
-    N = wl.ny * wl.nx
-    byt = nb * algorithmic_bytes(dom, N, n_samp / nb, wl.levels) if dom != "fused" else \
-        nb * K * (16 * N + 12 * n_samp / nb + N / 8)
-    hbm, src = peaks()
+    # host gather of the results on rank 0 (outside the timed region)
+    t0 = time.perf_counter()
+    local = {i: (x_hat[j].cpu().numpy(), tau[j].cpu().numpy(), thr[j].cpu().numpy(),
+                 alpha[j].cpu().numpy()) for j, i in enumerate(mine)}
+    allres = gather_by_slice(parts, world, rank, local, nb)
+    gather_s = time.perf_counter() - t0
+    dom, kt = dominant_kernel(vb, plan, step)
+    out = None
+    if rank == 0:
+        s_per = max_ms / 1e3 / (nb * K * steps)
+        out = {"workload": wl.name, "slices": nb, "iters": K, "steps": steps,
+               "value": nb * K * steps / (max_ms / 1e3), "unit": UNIT,
+               "ms_per_step": max_ms / steps, "tuning": tuning,
+               "partition": {"ranks": world, "slices_per_rank": [len(q) for q in parts],
+                             "balance": "pixels x iterations, longest first",
+                             "gathered_slices": sum(r is not None for r in allres),
+                             "gather_s": round(gather_s, 3)},
+               "roofline": kernel_roofline(dom, kt, wl, nm, n_samp / nm, peaks_),
+               "iteration_roofline": iteration_roofline(
+                   s_per, wl.ny, wl.nx, n_samp / nm, wl.levels, taps(wl.wavelet),
+                   peaks_["hbm_gbs"], peaks_.get("fp32_tflops"))}
     plan.close()
-    return {"workload": wl.name, "slices": nb, "iters": K, "steps": steps,
-            "value": nb * K * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
-            "tuning": tuning,
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": byt / avg_s / 1e9,
-                         "peak": hbm, "peak_source": src, "unit": "GB/s",
-                         "frac": byt / avg_s / 1e9 / hbm, "avg_launch_us": avg_s * 1e6,
-                         "algorithmic_bytes_per_launch": byt,
-                         "time_share": {k: round(v[0] / sum(x[0] for x in kt.values()), 4)
-                                        for k, v in kt.items()}}}
+    return out
 
 
-def run_mixed(args, vb, torch, flush_buf, stream):
+def run_mixed(args, vb, torch, flush_buf, stream, rank, world):
     """Mixed-size batch: 32 slices each of 128x128, 256x256 and 384x320 (db4 s=4,
     per-slice R ~ U[3, 8] and SNR ~ U[25, 40] dB, 30 iterations) as one grouped
-    graph launch, next to the same groups solved one after another."""
+    graph launch, next to the same groups solved one after another.  At N > 1 the
+    96 slices are partitioned over the ranks, balanced by pixels x iterations."""
     wls = synth.mixed_batch_workloads()
+    K = wls[0].iters
+    allsl = [(w, i) for w, wl in enumerate(wls) for i in range(wl.batch)]
+    parts = partition_slices([wls[w].ny * wls[w].nx * K for w, _ in allsl], world)
     groups, plans, tunings = [], [], {}
-    for wl in wls:
-        probs = [synth.make_problem(wl, i) for i in range(wl.batch)]
+    for w, wl in enumerate(wls):
+        idx = [allsl[j][1] for j in parts[rank] if allsl[j][0] == w]
+        if not idx:
+            continue
+        probs = [synth.make_problem(wl, i) for i in idx]
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
-        plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=wl.batch)
+        plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=len(idx))
         if not args.no_autotune:
-            tunings[f"{wl.ny}x{wl.nx}"] = plan.autotune(wl.batch, trials=3, stream=stream.cuda_stream)
+            tunings[f"{wl.ny}x{wl.nx}"] = plan.autotune(len(idx), trials=3,
+                                                         stream=stream.cuda_stream)
         plans.append(plan)
         groups.append((plan, dev([q.y for q in probs]), dev([q.mask for q in probs]),
                        dev([q.density for q in probs]), [q.sigma for q in probs]))
-    K = wls[0].iters
-    slices = sum(wl.batch for wl in wls)
-
-    def timed(fn, steps):
-        for i in range(2):
-            flush_buf.fill_(float(i))
-            fn()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        for i in range(steps):
-            flush_buf.fill_(float(i))
-            ev[i][0].record(stream)
-            fn()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev)
-
+    slices = len(allsl)
     steps = args.batched_steps
-    ms_grouped = timed(lambda: vb.solve_groups(groups, K, stream=stream.cuda_stream), steps)
-    ms_serial = timed(lambda: [g[0].solve(*g[1:], K, stream=stream.cuda_stream) for g in groups],
-                      steps)
+    _, ms_grouped = timed_steps(torch, lambda: vb.solve_groups(groups, K,
+                                                               stream=stream.cuda_stream),
+                                steps, flush_buf, stream, world)
+    _, ms_serial = timed_steps(torch, lambda: [g[0].solve(*g[1:], K, stream=stream.cuda_stream)
+                                               for g in groups], steps, flush_buf, stream, world)
     for plan in plans:
         if vb.vdamp_device_status(plan.handle)[0] != vb.VDAMP_OK:
             raise RuntimeError("mixed solve reported a non-finite tau or alpha")
         plan.close()
+    if rank != 0:
+        return None
     return {"workload": "batched 96 mixed slices (32 x 128x128, 32 x 256x256, 32 x 384x320) "
                         "db4 s=4 R~U[3,8] SNR~U[25,40] K=30",
             "slices": slices, "iters": K, "steps": steps,
@@ -386,6 +538,7 @@ def run_mixed(args, vb, torch, flush_buf, stream):
             "ms_per_step": ms_grouped / steps,
             "one_group_after_another": {"value": slices * K * steps / (ms_serial / 1e3),
                                         "ms_per_step": ms_serial / steps},
+            "partition": {"ranks": world, "slices_per_rank": [len(q) for q in parts]},
             "tuning": tunings or None}
 
 
@@ -453,11 +606,42 @@ def run_fft_reference(vb, torch, stream):
     return out
 
 
+def solve_closure(vb, torch, plan, y, m, p, sig, iters, stream):
+    """A plain solve of `iters` iterations into preallocated outputs (so that every call
+    replays the same cached graph)."""
+    b = y.shape[0]
+    x = torch.empty((b, plan.ny, plan.nx), dtype=torch.complex64, device="cuda")
+    t = torch.empty((b, iters, plan.B), dtype=torch.float64, device="cuda")
+    th, al = torch.empty_like(t), torch.empty_like(t)
+    return lambda: vb.vdamp_solve(plan.handle, b, y, m, p, sig, iters, None, x, t, th, al,
+                                  stream=stream.cuda_stream)
+
+
+def first_reaching(curve, target):
+    """1-based count of iterations after which `curve` (NMSE per iteration) is <= target."""
+    return next((k + 1 for k, v in enumerate(curve) if v <= target), None)
+
+
+def timed_mean_ms(torch, fn, flush_buf, stream, reps=5, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for i in range(reps):
+        flush_buf.fill_(float(i))
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+
 def run_learned_batched(args, vb, torch, flush_buf, stream):
-    """Learned VDAMP at scale: 256 slices of 320x320 db4 s=5 R=6 (a 16-subband
-    network trained on pairs of that kind), time to reach the plain method's
-    30-iteration mean NMSE, next to plain batched VDAMP (20 and 30 iterations)."""
-    from oracle import vdamp_oracle as O
+    """Learned VDAMP at scale: 256 slices of 320x320 db4 s=5 R=6 (a 16-subband network
+    trained on pairs of that kind).  Both methods' mean-NMSE curves are measured per
+    iteration; the target is the plain method's 30-iteration mean NMSE, and each method's
+    time to it is the time of a solve of the iterations it needs to reach it."""
     from paper_1911_01234_gb300 import learned
     wl = synth.BATCH_320_DB4_5
     nb = args.batched_slices
@@ -467,113 +651,132 @@ def run_learned_batched(args, vb, torch, flush_buf, stream):
     probs = [synth.make_problem(wl, i) for i in range(nb)]
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.stack(a))).cuda()
     y, m, p = dev([q.y for q in probs]), dev([q.mask for q in probs]), dev([q.density for q in probs])
+    x0 = dev([q.x0.astype(np.complex64) for q in probs])
+    x0n = (x0.abs().double() ** 2).sum(dim=(1, 2))
     sig = [q.sigma for q in probs]
     plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=nb)
     if not args.no_autotune:
         plan.autotune(nb, trials=3, stream=stream.cuda_stream)
 
-    def mean_nmse(x):
-        xs = x.cpu().numpy()
-        return float(np.mean([O.nmse_db(xs[i], probs[i].x0) for i in range(nb)]))
+    def mean_nmse(x):   # evaluation only: mean over slices of 10 log10 |x - x0|^2 / |x0|^2
+        e = ((x - x0).abs().double() ** 2).sum(dim=(1, 2))
+        return float(torch.mean(10.0 * torch.log10(e / x0n)).item())
 
-    def timed(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(reps)]
-        for i in range(reps):
-            flush_buf.fill_(float(i))
-            ev[i][0].record(stream)
-            fn()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev) / reps
-
-    plain30 = plan.solve(y, m, p, sig, 30)
+    plain = plan.solve(y, m, p, sig, 30, want_iters=True)
     torch.cuda.synchronize()
-    target = mean_nmse(plain30["x_hat"])
-    ms_plain30 = timed(lambda: plan.solve(y, m, p, sig, 30, stream=stream.cuda_stream))
-    ms_plain20 = timed(lambda: plan.solve(y, m, p, sig, wl.iters, stream=stream.cuda_stream))
-    nm_plain20 = mean_nmse(plan.solve(y, m, p, sig, wl.iters)["x_hat"])
+    plain_curve = [mean_nmse(plain["x_hat_iters"][k]) for k in range(30)]
+    del plain
+    target = plain_curve[-1]
+    need_plain = first_reaching(plain_curve, target)
+    ms_plain = {k: timed_mean_ms(torch, solve_closure(vb, torch, plan, y, m, p, sig, k, stream),
+                                 flush_buf, stream, reps=3)
+                for k in sorted({1, need_plain, wl.iters, 30})}
     full = learned.LearnedSolver(plan, net, nb, wl.iters, want_iters=True)
     out = full.run(y, m, p, sig)
     torch.cuda.synchronize()
+    full.check()
     curve = [mean_nmse(out["x_hat_iters"][k]) for k in range(wl.iters)]
     use = out["use"].float().mean(dim=(0, 1)).cpu().numpy()
     del full, out
-    need = next((k + 1 for k, v in enumerate(curve) if v <= target), None)
-    ms_need = None
-    if need is not None:
-        solver = learned.LearnedSolver(plan, net, nb, need).capture(y, m, p, sig)
-        ms_need = timed(solver.replay)
+    need = first_reaching(curve, target)
+    ms_learned = {}
+    for k in sorted({1, wl.iters} | ({need} if need else set())):
+        solver = learned.LearnedSolver(plan, net, nb, k).capture(y, m, p, sig)
+        ms_learned[k] = timed_mean_ms(torch, solver.replay, flush_buf, stream, reps=3)
+        solver.check()
+        del solver
     plan.close()
+    per_it_plain = (ms_plain[30] - ms_plain[1]) / 29
+    per_it_learned = (ms_learned[wl.iters] - ms_learned[1]) / max(1, wl.iters - 1)
     return {"workload": wl.name + ", learned per-subband CNN (16 networks) chosen by SURE",
             "metric": "time to reach the plain method's 30-iteration mean NMSE", "unit": "ms",
-            "plain_mean_nmse_db_30": target, "plain_mean_nmse_db_20": nm_plain20,
-            "ms_plain_30": ms_plain30, "ms_plain_20": ms_plain20,
-            "learned_mean_nmse_db_by_iter": [round(v, 3) for v in curve],
-            "learned_iters_to_plain_nmse": need, "ms_learned_to_plain_nmse": ms_need,
-            "speedup_to_plain_nmse": (ms_plain30 / ms_need) if ms_need else None,
+            "target_mean_nmse_db": target,
+            "plain_mean_nmse_db_by_iter": [round(v, 4) for v in plain_curve],
+            "learned_mean_nmse_db_by_iter": [round(v, 4) for v in curve],
+            "plain_iters_to_target": need_plain, "ms_plain_to_target": ms_plain[need_plain],
+            "learned_iters_to_target": need,
+            "ms_learned_to_target": ms_learned.get(need) if need else None,
+            "speedup_to_target": (ms_plain[need_plain] / ms_learned[need]) if need else None,
+            "final_nmse_gain_db": plain_curve[wl.iters - 1] - curve[-1],
+            "ms_plain_by_iters": ms_plain, "ms_learned_by_iters": ms_learned,
+            "ms_per_iteration": {"plain": per_it_plain, "learned": per_it_learned,
+                                 "learned_over_plain": per_it_learned / per_it_plain},
             "network_use_per_subband": [round(float(u), 2) for u in use],
             "training": tim}
 
 
-def run_learned(args, vb, torch, flush_buf, stream):
-    """Learned VDAMP at 256x256 db4 s=4 (per-subband CNN chosen by SURE): time to
-    reach the plain method's 30-iteration NMSE, next to the plain solve."""
+def run_learned(args, vb, torch, flush_buf, stream, slices=4):
+    """Learned VDAMP at 256x256 db4 s=4 (per-subband CNN chosen by SURE) on `slices`
+    held-out slices: per slice, both NMSE curves, the first iteration at which each method
+    reaches the plain method's own 30-iteration NMSE, and each method's time to get there
+    (a solve of that many iterations); the medians over the slices are the headline."""
     from oracle import vdamp_oracle as O
     from paper_1911_01234_gb300 import learned
     tim = {}
     net, _ = learned.train_default(steps=1500, timings=tim)
     wl = WL
-    pr = synth.make_problem(wl, 0)
-    d = lambda a: torch.from_numpy(np.ascontiguousarray(a[None])).cuda()
-    y, m, p = d(pr.y), d(pr.mask), d(pr.density)
     plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
     if not args.no_autotune:
         plan.autotune(1, trials=3, stream=stream.cuda_stream)
     K = wl.iters
-    plain = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
-    torch.cuda.synchronize()
-    nm_plain = [O.nmse_db(plain["x_hat_iters"][k, 0].cpu().numpy(), pr.x0) for k in range(K)]
-    solver = learned.LearnedSolver(plan, net, 1, K, want_iters=True)
-    out = solver.run(y, m, p, [pr.sigma])
-    torch.cuda.synchronize()
-    nm_l = [O.nmse_db(out["x_hat_iters"][k, 0].cpu().numpy(), pr.x0) for k in range(K)]
-    target = nm_plain[-1]
-    need = next((k + 1 for k, v in enumerate(nm_l) if v <= target), None)
-
-    def timed(fn, reps=10):
-        for i in range(3):
-            fn()
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a[None])).cuda()
+    per_slice, uses = [], []
+    for s_idx in range(slices):
+        pr = synth.make_problem(wl, s_idx)
+        y, m, p = d(pr.y), d(pr.mask), d(pr.density)
+        plain = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(reps)]
-        for i in range(reps):
-            flush_buf.fill_(float(i))
-            ev[i][0].record(stream)
-            fn()
-            ev[i][1].record(stream)
+        nm_p = [O.nmse_db(plain["x_hat_iters"][k, 0].cpu().numpy(), pr.x0) for k in range(K)]
+        solver = learned.LearnedSolver(plan, net, 1, K, want_iters=True)
+        out = solver.run(y, m, p, [pr.sigma])
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev) / reps
-
-    ms_plain = timed(lambda: plan.solve(y, m, p, [pr.sigma], K, stream=stream.cuda_stream))
-    full = learned.LearnedSolver(plan, net, 1, K).capture(y, m, p, [pr.sigma])
-    ms_learned = timed(full.replay)
-    ms_need = None
-    if need is not None:
-        short = learned.LearnedSolver(plan, net, 1, need).capture(y, m, p, [pr.sigma])
-        ms_need = timed(short.replay)
-    use = out["use"].cpu().numpy()[:, 0, :].mean(0)
+        solver.check()
+        nm_l = [O.nmse_db(out["x_hat_iters"][k, 0].cpu().numpy(), pr.x0) for k in range(K)]
+        uses.append(out["use"].cpu().numpy()[:, 0, :].mean(0))
+        target = nm_p[-1]
+        per_slice.append({"slice": s_idx, "plain_nmse_db_30": target,
+                          "learned_nmse_db_30": nm_l[-1],
+                          "plain_iters_to_target": first_reaching(nm_p, target),
+                          "learned_iters_to_target": first_reaching(nm_l, target),
+                          "plain_nmse_db_by_iter": [round(v, 4) for v in nm_p],
+                          "learned_nmse_db_by_iter": [round(v, 4) for v in nm_l]})
+    # solve times by iteration count (they do not depend on the slice's values)
+    pr = synth.make_problem(wl, 0)
+    y, m, p = d(pr.y), d(pr.mask), d(pr.density)
+    ks_p = sorted({1, K} | {r["plain_iters_to_target"] for r in per_slice})
+    ks_l = sorted({1, K} | {r["learned_iters_to_target"] for r in per_slice
+                            if r["learned_iters_to_target"]})
+    ms_p = {k: timed_mean_ms(torch, solve_closure(vb, torch, plan, y, m, p, [pr.sigma], k,
+                                                  stream),
+                             flush_buf, stream, reps=10, warm=3) for k in ks_p}
+    ms_l = {}
+    for k in ks_l:
+        sv = learned.LearnedSolver(plan, net, 1, k).capture(y, m, p, [pr.sigma])
+        ms_l[k] = timed_mean_ms(torch, sv.replay, flush_buf, stream, reps=10, warm=3)
+        sv.check()
     plan.close()
+    sp = []
+    for r in per_slice:
+        r["ms_plain_to_target"] = ms_p[r["plain_iters_to_target"]]
+        kl = r["learned_iters_to_target"]
+        r["ms_learned_to_target"] = ms_l[kl] if kl else None
+        r["speedup_to_target"] = (r["ms_plain_to_target"] / ms_l[kl]) if kl else None
+        if kl:
+            sp.append(r["speedup_to_target"])
+    per_it_p = (ms_p[K] - ms_p[1]) / (K - 1)
+    per_it_l = (ms_l[K] - ms_l[1]) / (K - 1)
     return {"workload": "learned VDAMP, 256x256 db4 s=4 R=5 30 dB, per-subband 5-layer CNN "
                         "(32 ch, BF16 tcgen05) chosen by SURE, Hutchinson divergence",
             "metric": "time to reach the plain method's 30-iteration NMSE", "unit": "ms",
-            "plain_nmse_db_30": target, "learned_nmse_db_30": nm_l[-1],
-            "learned_iters_to_plain_nmse": need, "ms_plain_30": ms_plain,
-            "ms_learned_to_plain_nmse": ms_need, "ms_learned_30": ms_learned,
-            "speedup_to_plain_nmse": (ms_plain / ms_need) if ms_need else None,
-            "network_use_per_subband": [round(float(u), 2) for u in use],
+            "slices": slices,
+            "median_speedup_to_target": statistics.median(sp) if sp else None,
+            "median_final_nmse_gain_db": statistics.median(
+                r["plain_nmse_db_30"] - r["learned_nmse_db_30"] for r in per_slice),
+            "ms_plain_by_iters": ms_p, "ms_learned_by_iters": ms_l,
+            "ms_per_iteration": {"plain": per_it_p, "learned": per_it_l,
+                                 "learned_over_plain": per_it_l / per_it_p},
+            "per_slice": per_slice,
+            "network_use_per_subband": [round(float(u), 2) for u in np.mean(uses, axis=0)],
             "training": tim}
 
 
@@ -657,33 +860,30 @@ def run_gpu(args):
     max_ms = slowest_rank_ms(tot_ms, world, device="cuda")
     value = job_throughput(world, args.steps, K, 1, max_ms)
 
-    # ---- dominant kernel, timed live with CUDA events on the launching stream
-    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 1)
-    vb.vdamp_kernel_times(plan.handle)
-    reps = 5
-    for i in range(reps):
-        flush_buf.fill_(float(i))
-        step()
-    kt = vb.vdamp_kernel_times(plan.handle)
-    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_KERNEL_TIMING, 0)
-    dom = max((k for k in kt if kt[k][1] > 0 and k != "other"), key=lambda k: kt[k][0])
-    dom_ms, dom_cnt = kt[dom]
-    avg_s = dom_ms / dom_cnt / 1e3
-    byt = algorithmic_bytes(dom, N, n_samp, WL.levels)
+    # ---- peaks of this GPU: HBM from MEASURED_PEAKS.json, FP32 / FP64 FMA measured here
     hbm, src = peaks()
-    achieved = byt / avg_s / 1e9
-    meas = MEASURED_TRAFFIC.get(dom)
-    traffic = meas["bytes_per_launch"] if meas and meas.get("source") == source_hash(dom) \
-        else None
-    shares = {k: round(v[0] / sum(x[0] for x in kt.values()), 4) for k, v in kt.items()}
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                "algorithmic_bytes_per_launch": byt, "avg_launch_us": avg_s * 1e6,
-                "launches_per_step": {k: v[1] // reps for k, v in kt.items()},
-                "avg_us_by_kernel": {k: round(1e3 * v[0] / v[1], 2) for k, v in kt.items() if v[1]},
-                "time_share": shares}
+    p32, ms32 = vb.vdamp_fma_peak(32, 20000, stream=stream.cuda_stream)
+    p64, ms64 = vb.vdamp_fma_peak(64, 400, stream=stream.cuda_stream)
+    peaks_ = {"hbm_gbs": hbm, "hbm_source": src, "fp32_tflops": p32, "fp64_tflops": p64,
+              "fma_kernel_ms": {"fp32": ms32, "fp64": ms64}}
 
-    # ---- end to end through the host-buffer entry point (pinned host memory)
+    # ---- dominant kernel, timed live with CUDA events on the launching stream
+    reps = 5
+
+    def timed_reps():
+        for i in range(reps):
+            flush_buf.fill_(float(i))
+            step()
+    dom, kt = dominant_kernel(vb, plan, timed_reps, reps=1)
+    roofline = kernel_roofline(dom, kt, WL, 1, n_samp, peaks_, reps=reps)
+    meas = MEASURED_TRAFFIC.get(dom)
+    roofline["traffic"] = meas["bytes_per_launch"] if meas and meas.get("source") == \
+        source_hash(dom) else None
+    roofline["iteration"] = iteration_roofline(max_ms / 1e3 / (args.steps * K), WL.ny, WL.nx,
+                                               n_samp, WL.levels, taps(WL.wavelet), hbm, p32)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory); the L2
+    # flush before each step is outside the wall-clock region
     hy = torch.from_numpy(pr.y[None].copy()).pin_memory()
     hm = torch.from_numpy(pr.mask[None].copy()).pin_memory()
     hp = torch.from_numpy(pr.density[None].copy()).pin_memory()
@@ -695,18 +895,19 @@ def run_gpu(args):
 
     def e2e_step():
         vb.check(lib.vdamp_solve_host(plan.handle, 1, hy.data_ptr(), hm.data_ptr(),
-                                      hp.data_ptr(), sig, K, None, hx.data_ptr(), ht.data_ptr(),
+                                      hp.data_ptr(), sig, K, None, 0, hx.data_ptr(), ht.data_ptr(),
                                       hth.data_ptr(), hal.data_ptr(), stream.cuda_stream),
                  "vdamp_solve_host")
     for i in range(3):
         e2e_step()
     e2e_steps = max(10, min(args.steps, 200))
-    t0 = time.perf_counter()
+    e2e_s = 0.0
     for i in range(e2e_steps):
         flush_buf.fill_(float(i))
         torch.cuda.synchronize()
-        e2e_step()
-    e2e_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        e2e_step()   # copies in, solve, copies out, and waits for them
+        e2e_s += time.perf_counter() - t0
     e2e_val = world * e2e_steps * K / e2e_s
     h2d = 8 * N + N + 4 * N
     d2h = 8 * N + 3 * 8 * K * plan.B
@@ -722,16 +923,19 @@ def run_gpu(args):
                 "gpu_launches": launches_per_step * args.steps,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "roofline": roofline,
+                "roofline": roofline, "peaks": peaks_,
                 "wall_s_timed": wall}
-        # the batched, mixed and learned measurements and the host baseline are
-        # single-GPU blocks: at N > 1 the line holds the replicated solve only
-        if world > 1:
-            args.no_batched = args.no_learned = args.no_cpu_baseline = True
-        if not args.no_batched:
-            line["batched"] = run_batched(args, vb, torch, flush_buf, stream)
-            line["mixed"] = run_mixed(args, vb, torch, flush_buf, stream)
+    # the batched and mixed blocks run on every rank (slices partitioned over the ranks);
+    # the learned blocks and the host baseline are single-GPU measurements
+    if world > 1:
+        args.no_learned = args.no_cpu_baseline = True
+    if not args.no_batched:
+        bat = run_batched(args, vb, torch, flush_buf, stream, rank, world, peaks_)
+        mix = run_mixed(args, vb, torch, flush_buf, stream, rank, world)
+        if rank == 0:
+            line["batched"], line["mixed"] = bat, mix
             line["fft_reference"] = run_fft_reference(vb, torch, stream)
+    if rank == 0:
         if not args.no_learned:
             line["learned"] = run_learned(args, vb, torch, flush_buf, stream)
             if not args.no_batched:

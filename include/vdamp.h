@@ -69,13 +69,17 @@ const char* vdamp_last_error(void);
  * (Algorithm 1 "Require": Psi; line 1: S = |Phi Psi^H|^2 is tabulated here
  * from its 1 + 3s unique columns, Sec. 2).  Sizes: ny and nx divisible by
  * 2^levels, of the form 2^a 3^b 5^c, 8 <= n <= 1024; 1 <= levels <= 6;
- * 1 <= max_batch.  Finest subbands above 32768 coefficients (ny nx > 131072,
- * e.g. 512 x 512) always take the split SURE search (tuning entry 7 >= 4).  Allocates all device workspace for up to max_batch slices
- * on the current device.  On success *out holds the plan; on failure *out is
+ * 1 <= max_batch; 1 <= max_iters <= 100000 (the most iterations any solve on
+ * the plan may run; it sizes the plan's staging of the per-iteration outputs
+ * of vdamp_solve_host and vdamp_solve_batched).  Finest subbands above 32768
+ * coefficients (ny nx > 131072, e.g. 512 x 512) always take the split SURE
+ * search (tuning entry 7 >= 4).  Allocates the device workspace for up to
+ * max_batch slices on the current device (the input staging of the host and
+ * descriptor entry points on their first call).  On success *out holds the plan; on failure *out is
  * NULL and the status says why.
  */
 vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int wavelet, int levels,
-                               int max_batch);
+                               int max_iters, int max_batch);
 
 /* Release the plan and its device memory (waits for its work to finish). */
 vdamp_status vdamp_plan_destroy(vdamp_plan* plan);
@@ -229,6 +233,21 @@ vdamp_status vdamp_cnn_conv3x3(const void* in, int cin_pad, const void* wimg, in
                                int mirror, int cout_store, const int* images, int n_img,
                                int conv_tiles_total, int max_w, int* status, void* stream);
 
+/* Failure detection of the convolution's bounded waits.  Each tile's
+ * tensor-core result is awaited on an mbarrier for at most `polls` polls
+ * (default vdamp_cnn_default_wait_limit(), about 1.7e7); when that runs out
+ * the kernel sets its status to 1, gives the operations still in flight one
+ * more wait of the default length, frees its tensor memory and returns, so
+ * the context stays usable.  vdamp_cnn_set_wait_limit sets the first limit
+ * for convolutions launched afterwards by this process (0 gives up at once,
+ * which is how the tests exercise this path) and returns the old one in
+ * *previous (may be NULL).  vdamp_cnn_status waits for `stream`, reads and
+ * clears a status word written by vdamp_cnn_conv3x3 and returns VDAMP_OK or
+ * VDAMP_ETIMEOUT. */
+vdamp_status vdamp_cnn_set_wait_limit(unsigned polls, unsigned* previous);
+unsigned vdamp_cnn_default_wait_limit(void);
+vdamp_status vdamp_cnn_status(int* status, void* stream);
+
 /* FP32 weights [bands][cout][9][cin] -> BF16 operand images; transpose = 1
  * packs the transposed convolution (cin outputs from cout inputs) used for
  * the gradient with respect to the layer input (with mirror = 1). */
@@ -308,9 +327,13 @@ vdamp_status vdamp_last_sure(vdamp_plan* plan, int batch, double* out, void* str
  *   density   device  [batch][ny][nx] float32    sampling probability p; 0 < p <= 1
  *                                                wherever mask = 1 (P of Algorithm 1)
  *   sigma     host    [batch] float32            noise level sigma_eps (Eq. 1), >= 0
- *   iters     number of iterations K_it >= 1
+ *   iters     number of iterations, 1 <= iters <= max_iters of the plan
  *   r_tilde0  device  [batch][ny*nx] complex64 packed, or NULL: starting r~_0
  *                     (NULL = 0 as in line 1; non-NULL resumes a stopped run)
+ *   k0        index of the first iteration: 0 for a cold start, the number of
+ *             iterations already run when resuming (Algorithm 1 does not
+ *             depend on k, so k0 changes no result; vdamp_device_status
+ *             reports iteration numbers k0 + k)
  *   x_hat     device  [batch][ny][nx] complex64 out: the return line applied to
  *                     the last denoiser output
  *   tau, thr, alpha  device  [batch][iters][B] double out (see conventions)
@@ -324,7 +347,7 @@ vdamp_status vdamp_last_sure(vdamp_plan* plan, int batch, double* out, void* str
  */
 vdamp_status vdamp_solve(vdamp_plan* plan, int batch, const float* y, const uint8_t* mask,
                          const float* density, const float* sigma, int iters,
-                         const float* r_tilde0, float* x_hat, double* tau, double* thr,
+                         const float* r_tilde0, int k0, float* x_hat, double* tau, double* thr,
                          double* alpha, float* r_tilde_out, float* x_hat_iters, void* stream);
 
 /*
@@ -335,8 +358,41 @@ vdamp_status vdamp_solve(vdamp_plan* plan, int batch, const float* y, const uint
  */
 vdamp_status vdamp_solve_host(vdamp_plan* plan, int batch, const float* y, const uint8_t* mask,
                               const float* density, const float* sigma, int iters,
-                              const float* r_tilde0, float* x_hat, double* tau, double* thr,
-                              double* alpha, void* stream);
+                              const float* r_tilde0, int k0, float* x_hat, double* tau,
+                              double* thr, double* alpha, void* stream);
+
+/*
+ * One slice of vdamp_solve_batched: the arguments of vdamp_solve for a single
+ * slice of the plan's size, each in its own device buffers.
+ */
+typedef struct {
+    const float* y;          /* device [ny][nx] complex64 measurements (ignored off the mask) */
+    const uint8_t* mask;     /* device [ny][nx] uint8, 1 where sampled */
+    const float* density;    /* device [ny][nx] float32 p, 0 < p <= 1 on the mask */
+    float sigma;             /* noise level sigma_eps >= 0 (Eq. 1) */
+    int iters;               /* iterations, 1 <= iters <= max_iters */
+    const float* r_tilde0;   /* device [ny*nx] packed complex64 to resume from, or NULL */
+    int k0;                  /* index of the first iteration (0 with r_tilde0 = NULL) */
+    float* x_hat;            /* device [ny][nx] complex64 out (return line) */
+    double* tau;             /* device [iters][B] out */
+    double* thr;             /* device [iters][B] out */
+    double* alpha;           /* device [iters][B] out */
+} vdamp_slice_desc;
+
+/*
+ * Batched VDAMP from slice descriptors (Algorithm 1 per slice, as vdamp_solve):
+ * `count` slices of the plan's size whose buffers lie anywhere in device
+ * memory.  Slices that share (iters, k0, cold start or not) are solved
+ * together, up to max_batch at a time, as one vdamp_solve on the plan's
+ * staging: a kernel gathers their inputs into it and another scatters x_hat,
+ * tau, thr and alpha back, so each slice's results equal those of vdamp_solve
+ * on that slice.  Asynchronous on `stream`; VDAMP_EINVAL (nothing launched)
+ * for an invalid descriptor; non-finite tau or alpha is recorded for
+ * vdamp_device_status as in vdamp_solve.  Slices already contiguous in
+ * memory are solved faster by vdamp_solve (no gather or scatter).
+ */
+vdamp_status vdamp_solve_batched(vdamp_plan* plan, const vdamp_slice_desc* slices, int count,
+                                 void* stream);
 
 /*
  * One pass of Algorithm 1 lines 3-8 from an explicit r~_k (device buffers as
@@ -392,16 +448,33 @@ vdamp_status vdamp_wavelet_filter(int wavelet, double* h, int* len);
  */
 vdamp_status vdamp_subband_spectra(int wavelet, int levels, int n, double* out);
 
+/* ---- measurement of the machine ------------------------------------------ */
+
+/*
+ * Peak fused multiply-add throughput of the current GPU in FP32 (precision =
+ * 32) or FP64 (64), in TFLOP/s (2 FLOP per FMA), from `iters` rounds of a
+ * kernel of independent FMA chains (4 resident CTAs of 256 threads per SM,
+ * 8 chains of 16 FMAs per thread and round): the denominator of the ALU
+ * roofline of the transforms.  The paper has no counterpart; this measures
+ * the machine, not the method.  Blocks until done (one warm-up launch, then
+ * the fastest of three, timed with CUDA events on `stream`); *ms (may be
+ * NULL) gets that launch's milliseconds.
+ */
+vdamp_status vdamp_fma_peak(int precision, int iters, double* tflops, double* ms, void* stream);
+
 /* ---- no device allocation ------------------------------------------------ */
 
 /* Largest ny or nx that vdamp_tau_estimate_noalloc accepts. */
 #define VDAMP_NOALLOC_MAX_SIDE 1024
 
 /*
- * The colored noise estimate tau (Algorithm 1 line 5,
- * tau = S^H P^-1 [(P^-1 - 1)|z|^2 + sigma^2]) from a k-space residual z, for
- * callers that cannot allocate device memory.  The paper has no counterpart:
- * this is a service of the library, not a step of the method.
+ * The paper has no counterpart to this entry point: it is a service of the
+ * library, not a step of the method.  It computes the same per-subband noise
+ * estimate tau that a solve reports, tau_b = sum_i S[i,b] w_i ((w_i - 1)|z_i|^2
+ * + sigma^2) with w = 1/p on the mask, from a k-space residual z, for callers
+ * that cannot allocate device memory: code running inside a fixed device
+ * memory pool or budget, hosts without an allocator, or tools that must not
+ * disturb a caching allocator they share with other code.
  *
  * It needs no plan and calls no cudaMalloc, cudaFree or other allocating
  * routine.  Its device scratch (the S tables and per-block partial sums, about
@@ -413,12 +486,17 @@ vdamp_status vdamp_subband_spectra(int wavelet, int levels, int n, double* out);
  *   mask     device [ny][nx] uint8;  density device [ny][nx] float32 (p, > 0 on the mask)
  *   sigma    noise level sigma_eps >= 0
  *   tau      device out [1 + 3 levels] double, subbands in packed order
- * Asynchronous on `stream`.  The first call on each device looks up the
- * scratch address with that device current; make that first call before any
- * stream capture.  All calls share the one scratch array: calls that overlap
- * on the GPU (different streams, no ordering) race and give wrong results.
- * Every partial sum is written before it is read, so nothing needs clearing
- * between calls.
+ * Asynchronous on `stream`: the S tables are filled on the device by a kernel
+ * of this call (from the filter taps, passed by value), so no host buffer is
+ * read after the call returns.  The first call on each device looks up the
+ * scratch address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one scratch
+ * array and each overwrites it: calls that overlap on the GPU (different
+ * streams, no ordering between them) race and give wrong results; calls on
+ * one stream are ordered and correct.  Every partial sum is written before it
+ * is read, so nothing needs clearing between calls.  A CUDA error already
+ * pending when the call starts is returned as VDAMP_ECUDA with its text, and
+ * nothing is launched.
  */
 vdamp_status vdamp_tau_estimate_noalloc(int ny, int nx, int wavelet, int levels, const float* z,
                                         const uint8_t* mask, const float* density, float sigma,

@@ -147,6 +147,22 @@ def sure(f: np.ndarray, r: np.ndarray, tau: float, div: float) -> float:
     return float(np.sum(np.abs(f - r) ** 2) - r.size * tau + tau * div)
 
 
+def adam_step(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, lr: float,
+              beta1: float, beta2: float, eps: float, t: int):
+    """One step of Adam (Kingma and Ba 2015, Algorithm 1) at step number t >= 1.
+
+    Moment estimates m <- beta1 m + (1 - beta1) g and v <- beta2 v + (1 - beta2) g^2,
+    their bias-corrected forms m_hat = m / (1 - beta1^t), v_hat = v / (1 - beta2^t),
+    and the update p <- p - lr m_hat / (sqrt(v_hat) + eps) (eps added after the root).
+    Returns the new (p, m, v); the inputs are not modified.
+    """
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
 def init_params(rng: np.random.Generator, cin=3, hidden=32, cout=2, layers=5):
     """He-normal weights, zero biases."""
     out = []

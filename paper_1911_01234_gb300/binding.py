@@ -36,14 +36,15 @@ _I = ctypes.c_int
 _D = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "vdamp_last_error": (ctypes.c_char_p, []),
-    "vdamp_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I]),
+    "vdamp_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _I]),
     "vdamp_plan_destroy": (_I, [_P]),
     "vdamp_num_subbands": (_I, [_P]),
     "vdamp_workspace_bytes": (ctypes.c_size_t, [_P]),
     "vdamp_plan_set_option": (_I, [_P, _I, _I]),
     "vdamp_last_launch_count": (_I, [_P]),
-    "vdamp_solve": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "vdamp_solve_host": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
+    "vdamp_solve": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
+    "vdamp_solve_host": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _P]),
+    "vdamp_solve_batched": (_I, [_P, _P, _I, _P]),
     "vdamp_iterate": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "vdamp_final_estimate": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "vdamp_psi": (_I, [_P, _I, _P, _P, _P]),
@@ -70,6 +71,10 @@ _SIGS = {
                             ctypes.c_float, ctypes.c_float, _I, _P]),
     "vdamp_cnn_onsager": (_I, [_P] * 6 + [_I] + [_P] * 2 + [_I, _I] + [_P] * 5),
     "vdamp_last_sure": (_I, [_P, _I, _P, _P]),
+    "vdamp_cnn_set_wait_limit": (_I, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint)]),
+    "vdamp_cnn_default_wait_limit": (ctypes.c_uint, []),
+    "vdamp_cnn_status": (_I, [_P, _P]),
+    "vdamp_fma_peak": (_I, [_I, _I, _D, _D, _P]),
 }
 
 VDAMP_TUNING_LEN = 8
@@ -82,6 +87,16 @@ class vdamp_group(ctypes.Structure):
     _fields_ = [("plan", _P), ("batch", _I), ("y", _P), ("mask", _P), ("density", _P),
                 ("sigma", ctypes.POINTER(ctypes.c_float)), ("iters", _I), ("x_hat", _P),
                 ("tau", _P), ("thr", _P), ("alpha", _P)]
+
+
+class vdamp_slice_desc(ctypes.Structure):
+    """struct vdamp_slice_desc of include/vdamp.h."""
+    _fields_ = [("y", _P), ("mask", _P), ("density", _P), ("sigma", ctypes.c_float),
+                ("iters", _I), ("r_tilde0", _P), ("k0", _I), ("x_hat", _P), ("tau", _P),
+                ("thr", _P), ("alpha", _P)]
+
+
+DEFAULT_MAX_ITERS = 64
 
 _lib: Optional[ctypes.CDLL] = None
 
@@ -141,10 +156,11 @@ def _sigma_array(sigma, batch):
 
 # ------------------------------------------------------------ C-ABI calls ---
 
-def vdamp_plan_create(ny: int, nx: int, wavelet, levels: int, max_batch: int = 1) -> int:
+def vdamp_plan_create(ny: int, nx: int, wavelet, levels: int, max_batch: int = 1,
+                      max_iters: int = DEFAULT_MAX_ITERS) -> int:
     w = WAVELETS.get(wavelet, wavelet) if isinstance(wavelet, str) else int(wavelet)
     h = _P()
-    check(load().vdamp_plan_create(ctypes.byref(h), ny, nx, w, levels, max_batch),
+    check(load().vdamp_plan_create(ctypes.byref(h), ny, nx, w, levels, max_iters, max_batch),
           "vdamp_plan_create")
     return h.value
 
@@ -170,25 +186,39 @@ def vdamp_last_launch_count(plan: int) -> int:
 
 
 def vdamp_solve(plan, batch, y, mask, density, sigma, iters, r_tilde0, x_hat, tau, thr, alpha,
-                r_tilde_out=None, x_hat_iters=None, stream=None) -> None:
+                r_tilde_out=None, x_hat_iters=None, stream=None, k0=0) -> None:
     """Device-buffer solve; tensors are CUDA torch tensors (complex64/uint8/float32/float64)."""
     sig = _sigma_array(sigma, batch)
     check(load().vdamp_solve(plan, batch, _ptr(y), _ptr(mask), _ptr(density), sig, iters,
-                             _ptr(r_tilde0), _ptr(x_hat), _ptr(tau), _ptr(thr), _ptr(alpha),
+                             _ptr(r_tilde0), int(k0), _ptr(x_hat), _ptr(tau), _ptr(thr),
+                             _ptr(alpha),
                              _ptr(r_tilde_out), _ptr(x_hat_iters), _stream(stream)),
           "vdamp_solve")
 
 
 def vdamp_solve_host(plan, batch, y, mask, density, sigma, iters, r_tilde0, x_hat, tau, thr,
-                     alpha, stream=None) -> None:
+                     alpha, stream=None, k0=0) -> None:
     """Host-buffer solve; arrays are C-contiguous numpy arrays of the header's types."""
     sig = _sigma_array(sigma, batch)
 
     def a(x):
         return None if x is None else x.ctypes.data
     check(load().vdamp_solve_host(plan, batch, a(y), a(mask), a(density), sig, iters,
-                                  a(r_tilde0), a(x_hat), a(tau), a(thr), a(alpha),
+                                  a(r_tilde0), int(k0), a(x_hat), a(tau), a(thr), a(alpha),
                                   _stream(stream)), "vdamp_solve_host")
+
+
+def vdamp_solve_batched(plan, slices, stream=None) -> None:
+    """slices: list of dicts with the vdamp_slice_desc fields (tensors for device arrays;
+    r_tilde0 and k0 may be left out for a cold start)."""
+    arr = (vdamp_slice_desc * len(slices))()
+    for i, d in enumerate(slices):
+        arr[i] = vdamp_slice_desc(_ptr(d["y"]), _ptr(d["mask"]), _ptr(d["density"]),
+                                  float(d["sigma"]), int(d["iters"]), _ptr(d.get("r_tilde0")),
+                                  int(d.get("k0", 0)), _ptr(d["x_hat"]), _ptr(d["tau"]),
+                                  _ptr(d["thr"]), _ptr(d["alpha"]))
+    check(load().vdamp_solve_batched(plan, ctypes.cast(arr, _P), len(slices), _stream(stream)),
+          "vdamp_solve_batched")
 
 
 def vdamp_iterate(plan, batch, r_tilde, y, mask, density, sigma, r, tau, thr, alpha,
@@ -235,11 +265,37 @@ def vdamp_kernel_times(plan):
 
 def vdamp_tau_estimate_noalloc(ny, nx, wavelet, levels, z, mask, density, sigma, tau,
                                stream=None) -> None:
-    """tau of Algorithm 1 line 5 from a residual z, with no device allocation (no plan)."""
+    """The per-subband noise estimate tau from a residual z, with no device allocation and
+    no plan (for callers that cannot allocate device memory; the paper has no counterpart)."""
     w = WAVELETS.get(wavelet, wavelet) if isinstance(wavelet, str) else int(wavelet)
     check(load().vdamp_tau_estimate_noalloc(ny, nx, w, levels, _ptr(z), _ptr(mask), _ptr(density),
                                             float(sigma), _ptr(tau), _stream(stream)),
           "vdamp_tau_estimate_noalloc")
+
+
+def vdamp_fma_peak(precision, iters, stream=None):
+    """(TFLOP/s, ms) of the FP32 (32) or FP64 (64) FMA-throughput kernel."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(load().vdamp_fma_peak(precision, iters, ctypes.byref(tf), ctypes.byref(ms),
+                                _stream(stream)), "vdamp_fma_peak")
+    return tf.value, ms.value
+
+
+def vdamp_cnn_set_wait_limit(polls):
+    """Set the first-wait poll limit of later convolutions; returns the previous limit."""
+    prev = ctypes.c_uint(0)
+    check(load().vdamp_cnn_set_wait_limit(int(polls), ctypes.byref(prev)),
+          "vdamp_cnn_set_wait_limit")
+    return prev.value
+
+
+def vdamp_cnn_default_wait_limit():
+    return load().vdamp_cnn_default_wait_limit()
+
+
+def vdamp_cnn_status(status, stream=None):
+    """VDAMP_OK or VDAMP_ETIMEOUT from a convolution status word (read and cleared)."""
+    return load().vdamp_cnn_status(_ptr(status), _stream(stream))
 
 
 def vdamp_wavelet_filter(wavelet):
@@ -298,10 +354,10 @@ def vdamp_solve_groups(groups, stream=None) -> None:
 class Plan:
     """Owns a vdamp_plan; solve() allocates outputs with torch on the plan's device."""
 
-    def __init__(self, ny, nx, wavelet, levels, max_batch=1):
+    def __init__(self, ny, nx, wavelet, levels, max_batch=1, max_iters=DEFAULT_MAX_ITERS):
         self.ny, self.nx, self.levels, self.max_batch = ny, nx, levels, max_batch
-        self.wavelet = wavelet
-        self.handle = vdamp_plan_create(ny, nx, wavelet, levels, max_batch)
+        self.wavelet, self.max_iters = wavelet, max_iters
+        self.handle = vdamp_plan_create(ny, nx, wavelet, levels, max_batch, max_iters)
         self.B = vdamp_num_subbands(self.handle)
 
     def close(self):
@@ -316,7 +372,7 @@ class Plan:
             pass
 
     def solve(self, y, mask, density, sigma, iters, r_tilde0=None, want_iters=False,
-              want_state=False, stream=None):
+              want_state=False, stream=None, k0=0):
         import torch
         batch = y.shape[0] if y.dim() == 3 else 1
         dev = y.device
@@ -329,7 +385,7 @@ class Plan:
         xi = torch.empty((iters, batch, self.ny, self.nx), dtype=torch.complex64, device=dev) \
             if want_iters else None
         vdamp_solve(self.handle, batch, y, mask, density, sigma, iters, r_tilde0, x_hat, tau, thr,
-                    alpha, rt, xi, stream)
+                    alpha, rt, xi, stream, k0)
         return {"x_hat": x_hat, "tau": tau, "thr": thr, "alpha": alpha, "r_tilde": rt,
                 "x_hat_iters": xi}
 

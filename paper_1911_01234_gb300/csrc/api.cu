@@ -191,7 +191,8 @@ __global__ void set_sigma_kernel(float* dst, SigmaBlock b) {
 }  // namespace
 
 struct vdamp_plan {
-    int ny, nx, levels, wavelet, B, max_batch;
+    int ny, nx, levels, wavelet, B, max_batch, max_iters;
+    int last_k0 = 0;                   // k0 of the last solve (added to reported iterations)
     size_t N;
     Filt filt;
     FftAxis axy, axx;
@@ -304,7 +305,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* acc) {
 }
 
 extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int wavelet,
-                                          int levels, int max_batch) {
+                                          int levels, int max_iters, int max_batch) {
     if (!out) return fail(VDAMP_EINVAL, "vdamp_plan_create: out is NULL");
     *out = nullptr;
     const int L = wavelet_taps(wavelet);
@@ -316,6 +317,8 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     if ((ny % (1 << levels)) || (nx % (1 << levels)))
         return fail(VDAMP_EINVAL, "vdamp_plan_create: ny and nx must be divisible by 2^levels");
     if (max_batch < 1) return fail(VDAMP_EINVAL, "vdamp_plan_create: max_batch must be >= 1");
+    if (max_iters < 1 || max_iters > 100000)
+        return fail(VDAMP_EINVAL, "vdamp_plan_create: max_iters must be in [1, 100000]");
     const size_t N = (size_t)ny * nx;
     const int max_band = (int)(N / 4);
     if (vdamp::sure_smem(max_band) > 227 * 1024)
@@ -328,6 +331,7 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     p->wavelet = wavelet;
     p->B = 1 + 3 * levels;
     p->max_batch = max_batch;
+    p->max_iters = max_iters;
     p->N = N;
 
     double h[VDAMP_MAX_TAPS];
@@ -426,6 +430,9 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(dalloc(&p->coef, MB * p->B, &acc));
     A(dalloc(&p->sigma_d, MB, &acc));
     A(dalloc(&p->status, (size_t)2, &acc));
+    // output staging of the host-buffer and descriptor entry points (tau, thr, alpha)
+    p->st_out_cap = 3 * MB * (size_t)max_iters * p->B;
+    A(dalloc(&p->st_out, p->st_out_cap, &acc));
     if (e != cudaSuccess) {
         plan_free(p);
         return fail(e == cudaErrorMemoryAllocation ? VDAMP_ENOMEM : VDAMP_ECUDA,
@@ -814,6 +821,7 @@ struct SolveArgs {
     double *tau, *thr, *alpha;
     float2* r_tilde_out;
     float2* x_hat_iters;
+    bool reset_status = true;   // clear the plan's error record first (false: keep earlier ones)
 };
 
 void enq_fused(Ctx& c, const SolveArgs& s);
@@ -825,8 +833,10 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
         enq_fused(c, s);
         return;
     }
-    if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status, 0, sizeof(int), c.st);
-    if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
+    if (s.reset_status && c.err == cudaSuccess)
+        c.err = cudaMemsetAsync(p->status, 0, sizeof(int), c.st);
+    if (s.reset_status && c.err == cudaSuccess)
+        c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
     float2* prev = p->rA;  // r_{k-1}
     float2* cur = p->rB;   // r_k
     for (int k = 0; k < s.iters; ++k) {
@@ -856,8 +866,10 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
 // Algorithm 1, lines 1-10, as one persistent cluster launch.
 void enq_fused(Ctx& c, const SolveArgs& s) {
     vdamp_plan* p = c.p;
-    if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status, 0, sizeof(int), c.st);
-    if (c.err == cudaSuccess) c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
+    if (s.reset_status && c.err == cudaSuccess)
+        c.err = cudaMemsetAsync(p->status, 0, sizeof(int), c.st);
+    if (s.reset_status && c.err == cudaSuccess)
+        c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
     const int lv = p->levels;
     const size_t N = p->N;
     vdamp::FusedArgs f;
@@ -974,16 +986,19 @@ vdamp_status check_sigma(const float* sigma, int batch, const char* who) {
 
 }  // namespace
 
-extern "C" vdamp_status vdamp_solve(vdamp_plan* p, int batch, const float* y, const uint8_t* mask,
-                                    const float* density, const float* sigma, int iters,
-                                    const float* r_tilde0, float* x_hat, double* tau, double* thr,
-                                    double* alpha, float* r_tilde_out, float* x_hat_iters,
-                                    void* stream) {
+static vdamp_status solve_impl(vdamp_plan* p, int batch, const float* y, const uint8_t* mask,
+                               const float* density, const float* sigma, int iters,
+                               const float* r_tilde0, int k0, float* x_hat, double* tau,
+                               double* thr, double* alpha, float* r_tilde_out,
+                               float* x_hat_iters, void* stream, bool reset_status) {
     vdamp_status st = check_common(p, batch, "vdamp_solve");
     if (st != VDAMP_OK) return st;
     if (!y || !mask || !density || !x_hat || !tau || !thr || !alpha)
         return fail(VDAMP_EINVAL, "vdamp_solve: a required pointer is NULL");
-    if (iters < 1) return fail(VDAMP_EINVAL, "vdamp_solve: iters must be >= 1");
+    if (iters < 1 || iters > p->max_iters)
+        return fail(VDAMP_EINVAL, "vdamp_solve: iters must be in [1, max_iters]");
+    if (k0 < 0 || (!r_tilde0 && k0 != 0))
+        return fail(VDAMP_EINVAL, "vdamp_solve: k0 must be >= 0, and 0 for a cold start");
     if ((st = check_sigma(sigma, batch, "vdamp_solve")) != VDAMP_OK) return st;
     cudaStream_t us = (cudaStream_t)stream;
     int launches = 0;
@@ -1001,13 +1016,14 @@ extern "C" vdamp_status vdamp_solve(vdamp_plan* p, int batch, const float* y, co
     s.alpha = alpha;
     s.r_tilde_out = (float2*)r_tilde_out;
     s.x_hat_iters = (float2*)x_hat_iters;
+    s.reset_status = reset_status;
 
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CUDA_TRY(cudaStreamIsCapturing(us, &cs));
     if (p->use_graph && !p->timing && cs == cudaStreamCaptureStatusNone) {
         GraphKey key;
         memset(&key, 0, sizeof(key));
-        key.kind = 1;
+        key.kind = reset_status ? 1 : 3;
         key.batch = batch;
         key.iters = iters;
         const void* ptrs[] = {y, mask, density, r_tilde0, x_hat, tau, thr, alpha, r_tilde_out,
@@ -1042,54 +1058,64 @@ extern "C" vdamp_status vdamp_solve(vdamp_plan* p, int batch, const float* y, co
         }
         CUDA_TRY(cudaGraphLaunch(hit->exec, us));
         p->last_launches = launches + hit->launches;
+        p->last_k0 = k0;
         return VDAMP_OK;
     }
     Ctx c{p, batch, us};
     c.timed = p->timing != 0;
     enq_solve(c, s);
     p->last_launches = launches + c.launches;
+    p->last_k0 = k0;
     if (c.err != cudaSuccess)
         return fail(VDAMP_ECUDA, std::string("vdamp_solve: ") + cudaGetErrorString(c.err));
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_solve(vdamp_plan* p, int batch, const float* y, const uint8_t* mask,
+                                    const float* density, const float* sigma, int iters,
+                                    const float* r_tilde0, int k0, float* x_hat, double* tau,
+                                    double* thr, double* alpha, float* r_tilde_out,
+                                    float* x_hat_iters, void* stream) {
+    return solve_impl(p, batch, y, mask, density, sigma, iters, r_tilde0, k0, x_hat, tau, thr,
+                      alpha, r_tilde_out, x_hat_iters, stream, true);
+}
+
+// Device staging of one batch of inputs and image outputs for the host-buffer
+// and descriptor entry points (allocated on first use, kept by the plan).
+static vdamp_status ensure_staging(vdamp_plan* p, const char* who) {
+    if (p->st_y) return VDAMP_OK;
+    const size_t MB = (size_t)p->max_batch, N = p->N;
+    cudaError_t e = cudaSuccess;
+    size_t acc = 0;
+    auto A = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    A(dalloc(&p->st_y, MB * N, &acc));
+    A(dalloc(&p->st_mask, MB * N, &acc));
+    A(dalloc(&p->st_p, MB * N, &acc));
+    A(dalloc(&p->st_x, MB * N, &acc));
+    A(dalloc(&p->st_r0, MB * N, &acc));
+    if (e != cudaSuccess)
+        return fail(VDAMP_ENOMEM, std::string(who) + ": staging: " + cudaGetErrorString(e));
+    p->ws_bytes += acc;
     return VDAMP_OK;
 }
 
 extern "C" vdamp_status vdamp_solve_host(vdamp_plan* p, int batch, const float* y,
                                          const uint8_t* mask, const float* density,
                                          const float* sigma, int iters, const float* r_tilde0,
-                                         float* x_hat, double* tau, double* thr, double* alpha,
-                                         void* stream) {
+                                         int k0, float* x_hat, double* tau, double* thr,
+                                         double* alpha, void* stream) {
     vdamp_status st = check_common(p, batch, "vdamp_solve_host");
     if (st != VDAMP_OK) return st;
     if (!y || !mask || !density || !x_hat || !tau || !thr || !alpha)
         return fail(VDAMP_EINVAL, "vdamp_solve_host: a required pointer is NULL");
-    if (iters < 1) return fail(VDAMP_EINVAL, "vdamp_solve_host: iters must be >= 1");
+    if (iters < 1 || iters > p->max_iters)
+        return fail(VDAMP_EINVAL, "vdamp_solve_host: iters must be in [1, max_iters]");
     if ((st = check_sigma(sigma, batch, "vdamp_solve_host")) != VDAMP_OK) return st;
-    const size_t MB = (size_t)p->max_batch, N = p->N;
-    if (!p->st_y) {
-        cudaError_t e = cudaSuccess;
-        size_t acc = 0;
-        auto A = [&](cudaError_t r) {
-            if (e == cudaSuccess) e = r;
-        };
-        A(dalloc(&p->st_y, MB * N, &acc));
-        A(dalloc(&p->st_mask, MB * N, &acc));
-        A(dalloc(&p->st_p, MB * N, &acc));
-        A(dalloc(&p->st_x, MB * N, &acc));
-        A(dalloc(&p->st_r0, MB * N, &acc));
-        if (e != cudaSuccess)
-            return fail(VDAMP_ENOMEM, std::string("vdamp_solve_host: ") + cudaGetErrorString(e));
-        p->ws_bytes += acc;
-    }
-    const size_t nout = (size_t)batch * iters * p->B;
-    if (p->st_out_cap < 3 * nout) {
-        if (p->st_out) cudaFree(p->st_out);
-        p->st_out = nullptr;
-        p->st_out_cap = 0;
-        size_t acc = 0;
-        if (dalloc(&p->st_out, 3 * nout, &acc) != cudaSuccess)
-            return fail(VDAMP_ENOMEM, "vdamp_solve_host: output staging");
-        p->st_out_cap = 3 * nout;
-    }
+    if ((st = ensure_staging(p, "vdamp_solve_host")) != VDAMP_OK) return st;
+    const size_t N = p->N;
+    const size_t nout = (size_t)batch * iters * p->B;   // <= a third of st_out_cap
     cudaStream_t us = (cudaStream_t)stream;
     const size_t n = (size_t)batch * N;
     CUDA_TRY(cudaMemcpyAsync(p->st_y, y, n * sizeof(float2), cudaMemcpyHostToDevice, us));
@@ -1099,7 +1125,7 @@ extern "C" vdamp_status vdamp_solve_host(vdamp_plan* p, int batch, const float* 
         CUDA_TRY(cudaMemcpyAsync(p->st_r0, r_tilde0, n * sizeof(float2), cudaMemcpyHostToDevice,
                                  us));
     st = vdamp_solve(p, batch, (const float*)p->st_y, p->st_mask, p->st_p, sigma, iters,
-                     r_tilde0 ? (const float*)p->st_r0 : nullptr, (float*)p->st_x, p->st_out,
+                     r_tilde0 ? (const float*)p->st_r0 : nullptr, k0, (float*)p->st_x, p->st_out,
                      p->st_out + nout, p->st_out + 2 * nout, nullptr, nullptr, stream);
     if (st != VDAMP_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(x_hat, p->st_x, n * sizeof(float2), cudaMemcpyDeviceToHost, us));
@@ -1110,6 +1136,145 @@ extern "C" vdamp_status vdamp_solve_host(vdamp_plan* p, int batch, const float* 
                              cudaMemcpyDeviceToHost, us));
     int it = 0;
     return vdamp_device_status(p, &it, stream);
+}
+
+// ------------------------------------------- solve from slice descriptors ---
+namespace {
+
+constexpr int kDescChunk = 32;   // slices per gather / scatter launch
+
+struct GatherChunk {
+    int n;
+    const float2* y[kDescChunk];
+    const uint8_t* mask[kDescChunk];
+    const float* density[kDescChunk];
+    const float2* r0[kDescChunk];   // NULL: zeros
+};
+
+// staging[base + s] <- slice s of the chunk (blockIdx.y = s), grid-stride over N
+__global__ void gather_slices_kernel(GatherChunk g, size_t N, int base, float2* sy, uint8_t* sm,
+                                     float* sp, float2* sr0) {
+    const int s = blockIdx.y;
+    if (s >= g.n) return;
+    const size_t o = (size_t)(base + s) * N;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        sy[o + i] = g.y[s][i];
+        sm[o + i] = g.mask[s][i];
+        sp[o + i] = g.density[s][i];
+        if (sr0) sr0[o + i] = g.r0[s] ? g.r0[s][i] : make_float2(0.f, 0.f);
+    }
+}
+
+struct ScatterChunk {
+    int n;
+    float2* x[kDescChunk];
+    double* tau[kDescChunk];
+    double* thr[kDescChunk];
+    double* alpha[kDescChunk];
+};
+
+// slice s of the chunk <- staging[base + s]: x_hat (N values) and the three
+// [iters][B] records, which the staging holds as [batch][iters][B] each.
+__global__ void scatter_slices_kernel(ScatterChunk g, size_t N, int base, size_t nrec,
+                                      const float2* sx, const double* sout, size_t nout) {
+    const int s = blockIdx.y;
+    if (s >= g.n) return;
+    const size_t o = (size_t)(base + s) * N, r = (size_t)(base + s) * nrec;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        g.x[s][i] = sx[o + i];
+        if (i < nrec) {
+            g.tau[s][i] = sout[r + i];
+            g.thr[s][i] = sout[nout + r + i];
+            g.alpha[s][i] = sout[2 * nout + r + i];
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" vdamp_status vdamp_solve_batched(vdamp_plan* p, const vdamp_slice_desc* slices,
+                                            int count, void* stream) {
+    if (!p) return fail(VDAMP_EINVAL, "vdamp_solve_batched: NULL plan");
+    if (!slices || count < 1) return fail(VDAMP_EINVAL, "vdamp_solve_batched: no slices");
+    for (int i = 0; i < count; ++i) {
+        const vdamp_slice_desc& d = slices[i];
+        if (!d.y || !d.mask || !d.density || !d.x_hat || !d.tau || !d.thr || !d.alpha)
+            return fail(VDAMP_EINVAL, "vdamp_solve_batched: a required pointer is NULL");
+        if (d.iters < 1 || d.iters > p->max_iters)
+            return fail(VDAMP_EINVAL, "vdamp_solve_batched: iters must be in [1, max_iters]");
+        if (d.k0 < 0 || (!d.r_tilde0 && d.k0 != 0))
+            return fail(VDAMP_EINVAL, "vdamp_solve_batched: k0 must be >= 0, 0 for a cold start");
+        if (!(d.sigma >= 0.f) || !std::isfinite(d.sigma))
+            return fail(VDAMP_EINVAL, "vdamp_solve_batched: sigma must be finite and >= 0");
+    }
+    vdamp_status st = ensure_staging(p, "vdamp_solve_batched");
+    if (st != VDAMP_OK) return st;
+    cudaStream_t us = (cudaStream_t)stream;
+    const size_t N = p->N;
+    const int gx = (int)std::min<size_t>((N + 255) / 256, 64);
+    // slices that share (iters, k0, cold start) are solved together, up to max_batch at a time
+    std::vector<char> done(count, 0);
+    int launches = 0;
+    const int first = 0;
+    for (int i0 = 0; i0 < count; ++i0) {
+        if (done[i0]) continue;
+        const vdamp_slice_desc& k = slices[i0];
+        std::vector<int> grp;
+        for (int i = i0; i < count && (int)grp.size() < p->max_batch; ++i)
+            if (!done[i] && slices[i].iters == k.iters && slices[i].k0 == k.k0 &&
+                (slices[i].r_tilde0 == nullptr) == (k.r_tilde0 == nullptr)) {
+                grp.push_back(i);
+                done[i] = 1;
+            }
+        const int nb = (int)grp.size();
+        const bool cold = k.r_tilde0 == nullptr;
+        std::vector<float> sig(nb);
+        for (int c0 = 0; c0 < nb; c0 += kDescChunk) {
+            GatherChunk g;
+            memset(&g, 0, sizeof(g));
+            g.n = std::min(kDescChunk, nb - c0);
+            for (int j = 0; j < g.n; ++j) {
+                const vdamp_slice_desc& d = slices[grp[c0 + j]];
+                g.y[j] = (const float2*)d.y;
+                g.mask[j] = d.mask;
+                g.density[j] = d.density;
+                g.r0[j] = (const float2*)d.r_tilde0;
+            }
+            gather_slices_kernel<<<dim3(gx, g.n), 256, 0, us>>>(g, N, c0, p->st_y, p->st_mask,
+                                                                p->st_p, cold ? nullptr : p->st_r0);
+            CUDA_TRY(cudaGetLastError());
+            ++launches;
+        }
+        for (int j = 0; j < nb; ++j) sig[j] = slices[grp[j]].sigma;
+        const size_t nout = (size_t)nb * k.iters * p->B;
+        // the first group clears the error record, later ones keep what earlier ones found
+        st = solve_impl(p, nb, (const float*)p->st_y, p->st_mask, p->st_p, sig.data(), k.iters,
+                        cold ? nullptr : (const float*)p->st_r0, k.k0, (float*)p->st_x,
+                        p->st_out, p->st_out + nout, p->st_out + 2 * nout, nullptr, nullptr,
+                        stream, i0 == first);
+        if (st != VDAMP_OK) return st;
+        launches += p->last_launches;
+        for (int c0 = 0; c0 < nb; c0 += kDescChunk) {
+            ScatterChunk g;
+            memset(&g, 0, sizeof(g));
+            g.n = std::min(kDescChunk, nb - c0);
+            for (int j = 0; j < g.n; ++j) {
+                const vdamp_slice_desc& d = slices[grp[c0 + j]];
+                g.x[j] = (float2*)d.x_hat;
+                g.tau[j] = d.tau;
+                g.thr[j] = d.thr;
+                g.alpha[j] = d.alpha;
+            }
+            scatter_slices_kernel<<<dim3(gx, g.n), 256, 0, us>>>(
+                g, N, c0, (size_t)k.iters * p->B, p->st_x, p->st_out, nout);
+            CUDA_TRY(cudaGetLastError());
+            ++launches;
+        }
+    }
+    p->last_launches = launches;
+    return VDAMP_OK;
 }
 
 extern "C" vdamp_status vdamp_iterate(vdamp_plan* p, int batch, const float* r_tilde,
@@ -1137,6 +1302,7 @@ extern "C" vdamp_status vdamp_iterate(vdamp_plan* p, int batch, const float* r_t
     enq_sure(c, (const float2*)r, 1, 0, tau, thr, alpha);
     enq_line8(c, (const float2*)r, (float2*)r_tilde_next);
     p->last_launches = launches + c.launches;
+    p->last_k0 = 0;
     if (c.err != cudaSuccess)
         return fail(VDAMP_ECUDA, std::string("vdamp_iterate: ") + cudaGetErrorString(c.err));
     return VDAMP_OK;
@@ -1215,8 +1381,9 @@ extern "C" vdamp_status vdamp_device_status(vdamp_plan* p, int* iter, void* stre
     CUDA_TRY(cudaMemcpy(h, p->status, sizeof(h), cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
     if (h[0] == VDAMP_ENUMERIC) {
-        if (iter) *iter = h[1];
-        return fail(VDAMP_ENUMERIC, "non-finite tau or alpha at iteration " + std::to_string(h[1]));
+        const int k = h[1] + p->last_k0;
+        if (iter) *iter = k;
+        return fail(VDAMP_ENUMERIC, "non-finite tau or alpha at iteration " + std::to_string(k));
     }
     if (iter) *iter = -1;
     return VDAMP_OK;
@@ -1497,7 +1664,8 @@ extern "C" vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count,
         if (st != VDAMP_OK) return st;
         if (!g.y || !g.mask || !g.density || !g.x_hat || !g.tau || !g.thr || !g.alpha)
             return fail(VDAMP_EINVAL, "vdamp_solve_groups: a required pointer is NULL");
-        if (g.iters < 1) return fail(VDAMP_EINVAL, "vdamp_solve_groups: iters must be >= 1");
+        if (g.iters < 1 || g.iters > g.plan->max_iters)
+            return fail(VDAMP_EINVAL, "vdamp_solve_groups: iters must be in [1, max_iters]");
         if ((st = check_sigma(g.sigma, g.batch, "vdamp_solve_groups")) != VDAMP_OK) return st;
         for (int j = 0; j < i; ++j)
             if (groups[j].plan == g.plan)
@@ -1521,6 +1689,7 @@ extern "C" vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count,
             c.timed = groups[i].plan->timing != 0;
             enq_solve(c, group_args(groups[i]));
             groups[i].plan->last_launches = launches[i] + c.launches;
+            groups[i].plan->last_k0 = 0;
             if (c.err != cudaSuccess)
                 return fail(VDAMP_ECUDA, std::string("vdamp_solve_groups: ") +
                                              cudaGetErrorString(c.err));
@@ -1581,7 +1750,10 @@ extern "C" vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count,
         hit = &g_group_graphs.back();
     }
     CUDA_TRY(cudaGraphLaunch(hit->exec, us));
-    for (int i = 0; i < count; ++i) groups[i].plan->last_launches = launches[i] + hit->launches[i];
+    for (int i = 0; i < count; ++i) {
+        groups[i].plan->last_launches = launches[i] + hit->launches[i];
+        groups[i].plan->last_k0 = 0;
+    }
     return VDAMP_OK;
 }
 

@@ -4,6 +4,7 @@
 // accumulator in tensor memory), its weight gradient, and the elementwise
 // steps around the network (input planes, residual output, Hutchinson probe,
 // loss gradient, Adam).
+#include <atomic>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3x3_kernel(const __grid_cons
         const bool new_band = more && nxt.band != band;
         if (new_band) {
             // the weights change: the tensor cores must be done with tile t first
-            ok = __syncthreads_and(tc::mbar_wait(&mbar[ac], phase[ac], kWaitLimit)) != 0;
+            ok = __syncthreads_and(tc::mbar_wait(&mbar[ac], phase[ac], a.wait_limit)) != 0;
             if (!ok) break;
             band = nxt.band;
             load_band(band, bslot ^ 1);
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3x3_kernel(const __grid_cons
 #pragma unroll
         for (int d = 0; d + 2 < D; ++d) ahead[d] = ahead[d + 1];
         ahead[D - 2] = fresh;
-        if (!new_band && !tc::mbar_wait(&mbar[ac], phase[ac], kWaitLimit)) {
+        if (!new_band && !tc::mbar_wait(&mbar[ac], phase[ac], a.wait_limit)) {
             timed_out = true;   // each warp waits on its own; the outcome meets at the next barrier
             continue;
         }
@@ -289,7 +290,8 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3x3_kernel(const __grid_cons
     if (ok && __syncthreads_or(timed_out)) ok = false;   // the last tile's wait
     if (!ok) {
         // a wait ran out: record it, give the MMAs in flight one more bounded
-        // wait, then free the tensor memory as on the normal path
+        // wait (always the full kWaitLimit, whatever the first wait's limit),
+        // then free the tensor memory as on the normal path
         if (tid == 0) atomicExch(a.status, 1);
         for (int i = 0; i < 2; ++i)
             if (pending[i]) tc::mbar_wait(&mbar[i], phase[i], kWaitLimit);
@@ -597,7 +599,11 @@ __global__ void cnn_loss_kernel(const float2* r, const float2* w0, const double*
 // Adam step on FP32 parameters (bias-corrected, step number t >= 1).
 __global__ void adam_kernel(float* p, const float* g, float* m, float* v, size_t n, float lr,
                             float b1, float b2, float eps, int t) {
-    const float c1 = 1.f / (1.f - powf(b1, (float)t)), c2 = 1.f / (1.f - powf(b2, (float)t));
+    // bias corrections 1 / (1 - beta^t), with 1 - beta^t = -expm1(t log1p(beta - 1)):
+    // beta - 1 is exact in FP32, and no difference of nearly equal numbers is formed
+    // (1 - powf(0.999, 2) would lose four digits)
+    const float c1 = -1.f / expm1f((float)t * log1pf(b1 - 1.f));
+    const float c2 = -1.f / expm1f((float)t * log1pf(b2 - 1.f));
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -729,6 +735,35 @@ static vdamp_status cnn_fail(const char* msg) {
     return VDAMP_EINVAL;
 }
 
+// Polls of the first wait for a tile's tensor-core result (set per process).
+static std::atomic<unsigned> g_wait_limit{kWaitLimit};
+
+extern "C" vdamp_status vdamp_cnn_set_wait_limit(unsigned polls, unsigned* previous) {
+    const unsigned old = g_wait_limit.exchange(polls);
+    if (previous) *previous = old;
+    return VDAMP_OK;
+}
+
+extern "C" unsigned vdamp_cnn_default_wait_limit(void) { return kWaitLimit; }
+
+extern "C" vdamp_status vdamp_cnn_status(int* status, void* stream) {
+    if (!status) return cnn_fail("vdamp_cnn_status: NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        vdamp::set_last_error(cudaGetErrorString(e));
+        return VDAMP_ECUDA;
+    }
+    if (h != 0) {
+        vdamp::set_last_error("vdamp_cnn_status: a bounded wait for the tensor cores ran out");
+        return VDAMP_ETIMEOUT;
+    }
+    return VDAMP_OK;
+}
+
 extern "C" vdamp_status vdamp_cnn_conv3x3(const void* in, int cin_pad, const void* wimg,
                                           int cout_pad, const float* bias, const void* mask,
                                           void* out, int mode, int mirror, int cout_store,
@@ -757,6 +792,7 @@ extern "C" vdamp_status vdamp_cnn_conv3x3(const void* in, int cin_pad, const voi
     a.mirror = mirror ? 1 : 0;
     a.mode = mode;
     a.status = status;
+    a.wait_limit = g_wait_limit.load();
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (cin_pad == 16 && cout_pad == 32) e = launch_conv<16, 32>(a, st);

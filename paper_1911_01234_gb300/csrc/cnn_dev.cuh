@@ -53,6 +53,7 @@ struct ConvArgs {
     int mirror;                  // 1: neighbour offsets negated (transposed convolution)
     int mode;
     int* status;                 // [0] set to 1 when a bounded wait ran out
+    unsigned wait_limit;         // polls of a tensor-core wait before it gives up
 };
 
 // Neighbour offset (dy, dx) of tap t = 3 (dy + 1) + (dx + 1).

@@ -1,6 +1,7 @@
-// vdamp_tau_estimate_noalloc: the colored noise estimate tau of Algorithm 1
-// line 5, computed from a k-space residual z without allocating any device
-// memory.
+// vdamp_tau_estimate_noalloc: the colored noise estimate tau of the VDAMP
+// iteration, computed from a k-space residual z without allocating any
+// device memory.  The paper has no such entry point; it is a service of the
+// library for callers that cannot allocate.
 //
 // Some callers cannot call cudaMalloc: code that runs inside a fixed device
 // memory pool or budget, allocator-less embedded or real-time hosts, and
@@ -10,9 +11,13 @@
 // __device__ array of fixed size.  Every GPU that loads the library holds
 // that array until the process exits.
 //
-// The kernel is a variant of the tau stage of the column pass: the same
-// per-frequency term p^-1 ((p^-1 - 1)|z|^2 + sigma^2) weighted by the
-// subband spectra, FP32 per thread, FP64 across warps and CTAs.
+// The tables are filled on the device by a kernel whose only inputs are the
+// wavelet's filter taps and the sizes, passed by value: the call reads no
+// host buffer after it returns, and calls on one stream see their own tables
+// in stream order.  The tau kernel is a variant of the tau stage of the
+// column pass: the same per-frequency term p^-1 ((p^-1 - 1)|z|^2 + sigma^2)
+// weighted by the subband spectra, FP32 per thread, FP64 across warps and
+// CTAs.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -55,6 +60,46 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Filter taps of the wavelet, by value (a kernel parameter).
+struct FilterTaps {
+    double h[VDAMP_MAX_TAPS];
+    int L;
+};
+
+// |sum_k f[k] e^{-i 2 pi k m / n}|^2 for integer frequency m (argument reduced
+// exactly: the phase of tap k is ((k m) mod n) / n of a turn).
+__device__ double resp2_dev(const double* f, int L, long long m, int n) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < L; ++k) {
+        double s, c;
+        sincospi(2.0 * (double)((k * m) % n) / (double)n, &s, &c);
+        re += f[k] * c;
+        im -= f[k] * s;
+    }
+    return re * re + im * im;
+}
+
+// The 1D factors of S along an axis of length n (the same quantity as the
+// plan's host tables): entry (2 (j - 1) + t) n + k is |F_n psi|^2 at frequency
+// k of the level-j scaling (t = 0) or wavelet (t = 1) atom.  The level-j atoms
+// have DTFT prod_{l<j} H(2^l w) and G(2^{j-1} w) prod_{l<j-1} H(2^l w),
+// sampled at w = 2 pi k / n (the unitary DFT of the periodised atom).
+// Grid-stride over k; one thread per frequency.
+__global__ void spectra_noalloc_kernel(FilterTaps ft, int levels, int n, float* out) {
+    double g[VDAMP_MAX_TAPS];
+    for (int k = 0; k < ft.L; ++k) g[k] = ((k & 1) ? -1.0 : 1.0) * ft.h[ft.L - 1 - k];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double low = 1.0;   // prod over the coarser factors so far
+        long long m = k;
+        for (int j = 1; j <= levels; ++j) {
+            out[(2 * (j - 1) + 1) * n + k] = (float)(low * resp2_dev(g, ft.L, m, n) / n);
+            low *= resp2_dev(ft.h, ft.L, m, n);
+            out[(2 * (j - 1)) * n + k] = (float)(low / n);
+            m = (2 * m) % n;
+        }
+    }
 }
 
 __global__ void tau_part_noalloc_kernel(TauArgs a) {
@@ -113,6 +158,12 @@ vdamp_status bad(vdamp_status st, const char* msg) {
     return st;
 }
 
+vdamp_status bad_cuda(const char* what, cudaError_t e) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    return bad(VDAMP_ECUDA, buf);
+}
+
 bool radix_ok(int n) {
     for (int f : {2, 3, 5})
         while (n % f == 0) n /= f;
@@ -135,6 +186,11 @@ extern "C" vdamp_status vdamp_tau_estimate_noalloc(int ny, int nx, int wavelet, 
     if (!z || !mask || !density || !tau) return bad(VDAMP_EINVAL, "a pointer is NULL");
     if (!(sigma >= 0.f) || !std::isfinite(sigma)) return bad(VDAMP_EINVAL, "sigma must be >= 0");
 
+    // An error left by earlier work (asynchronous, or sticky) is reported as
+    // such, before anything is launched, and not cleared.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return bad_cuda("an earlier CUDA error is pending", e);
+
     // Set-up, once per device with that device current: the device address of
     // the scratch array.
     int dev = 0;
@@ -145,8 +201,8 @@ extern "C" vdamp_status vdamp_tau_estimate_noalloc(int ny, int nx, int wavelet, 
         std::lock_guard<std::mutex> lk(g_mu);
         if (!g_scratch_addr[dev]) {
             void* ptr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess || !ptr) return bad(VDAMP_ECUDA, cudaGetErrorString(e));
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) return bad_cuda("cudaGetSymbolAddress", e);
             g_scratch_addr[dev] = ptr;
         }
         base = g_scratch_addr[dev];
@@ -155,24 +211,15 @@ extern "C" vdamp_status vdamp_tau_estimate_noalloc(int ny, int nx, int wavelet, 
     float* ex = ey + 2 * VDAMP_MAX_LEVELS * kMaxSide;
     double* part = (double*)((unsigned char*)base + kSpecBytes);
 
-    // S factors for this call, computed on the host into fixed buffers and
-    // copied over the previous call's tables (calls on one stream are ordered).
+    // S factors for this call, filled on the device over the previous call's
+    // tables (calls on one stream are ordered; the taps travel by value).
     const int nt = 2 * levels;
-    static thread_local double hd[2 * VDAMP_MAX_LEVELS * kMaxSide];
-    static thread_local float hy[2 * VDAMP_MAX_LEVELS * kMaxSide];
-    static thread_local float hx[2 * VDAMP_MAX_LEVELS * kMaxSide];
-    if (vdamp_subband_spectra(wavelet, levels, ny, hd) != VDAMP_OK)
-        return bad(VDAMP_EINVAL, "spectra");
-    for (int i = 0; i < nt * ny; ++i) hy[i] = (float)hd[i];
-    if (vdamp_subband_spectra(wavelet, levels, nx, hd) != VDAMP_OK)
-        return bad(VDAMP_EINVAL, "spectra");
-    for (int i = 0; i < nt * nx; ++i) hx[i] = (float)hd[i];
+    FilterTaps ft;
+    if (vdamp_wavelet_filter(wavelet, ft.h, &ft.L) != VDAMP_OK) return bad(VDAMP_EINVAL, "filter");
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(ey, hy, (size_t)nt * ny * sizeof(float), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(ex, hx, (size_t)nt * nx * sizeof(float), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess)
-        return bad(VDAMP_ECUDA, "table upload failed");
+    spectra_noalloc_kernel<<<(ny + 127) / 128, 128, 0, st>>>(ft, levels, ny, ey);
+    spectra_noalloc_kernel<<<(nx + 127) / 128, 128, 0, st>>>(ft, levels, nx, ex);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bad_cuda("table launch failed", e);
 
     TauArgs a;
     a.z = (const float2*)z;
@@ -204,8 +251,8 @@ extern "C" vdamp_status vdamp_tau_estimate_noalloc(int ny, int nx, int wavelet, 
     threads = threads < 64 ? 64 : (threads > 512 ? 512 : threads);
     threads = (threads + 31) / 32 * 32;
     tau_part_noalloc_kernel<<<nparts, threads, 0, st>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return bad(VDAMP_ECUDA, "partials launch failed");
+    if ((e = cudaGetLastError()) != cudaSuccess) return bad_cuda("partials launch failed", e);
     tau_reduce_noalloc_kernel<<<1, 32, 0, st>>>(part, nparts, a.B, tau);
-    if (cudaGetLastError() != cudaSuccess) return bad(VDAMP_ECUDA, "reduce launch failed");
+    if ((e = cudaGetLastError()) != cudaSuccess) return bad_cuda("reduce launch failed", e);
     return VDAMP_OK;
 }

@@ -369,10 +369,18 @@ class LearnedSolver:
             if want_iters else None
         self.graph = None
 
-    def run(self, y, mask, density, sigma, stream=None):
+    def run(self, y, mask, density, sigma, stream=None, r_tilde0=None, k0=0):
+        """Iterations k0 .. k0 + iters - 1 from r~ = r_tilde0 (None: 0, with k0 = 0); the
+        probe of iteration k has seed + k, so a resumed run draws the probes the
+        uninterrupted one would have."""
         L, st = lib(), _st(stream)
         plan, B = self.plan, self.plan.B
-        self.rt.zero_()
+        if r_tilde0 is None:
+            if k0 != 0:
+                raise ValueError("k0 must be 0 for a cold start")
+            self.rt.zero_()
+        else:
+            self.rt.copy_(r_tilde0)
         for k in range(self.iters):
             vb.vdamp_iterate(plan.handle, self.batch, self.rt, y, mask, density, sigma, self.r,
                              self.tau, self.thr, self.alpha, self.rt_soft, stream=st)
@@ -381,8 +389,8 @@ class LearnedSolver:
             self.taus[k].copy_(self.tau)
             self.thrs[k].copy_(self.thr)
             if self.net is not None:
-                self.net.denoise(self.im, self.r, self.tau, B, self.seed + k, self.f, self.sums,
-                                 st)
+                self.net.denoise(self.im, self.r, self.tau, B, self.seed + k0 + k, self.f,
+                                 self.sums, st)
             else:
                 self.sums.zero_()
             vb.check(L.vdamp_cnn_onsager(_p(self.r), _p(self.f) if self.net is not None else None,
@@ -416,9 +424,15 @@ class LearnedSolver:
         self.graph.replay()
         return self.outputs()
 
+    def check(self, stream=None):
+        """Raise VdampError(VDAMP_ETIMEOUT) if a convolution's bounded wait for the tensor
+        cores ran out since the last check (waits for `stream`; not inside a capture)."""
+        if self.net is not None:
+            vb.check(vb.vdamp_cnn_status(self.net.status, _st(stream)), "learned solve")
+
     def outputs(self):
         B = self.plan.B
-        return {"x_hat": self.x_hat, "tau": self.taus, "thr": self.thrs,
+        return {"x_hat": self.x_hat, "tau": self.taus, "thr": self.thrs, "r_tilde": self.rt,
                 "use": self.use.view(self.iters, self.batch, B),
                 "alpha": self.al.view(self.iters, self.batch, B), "x_hat_iters": self.xs}
 

@@ -59,3 +59,21 @@ def test_throughput_and_algorithmic_bytes():
     assert bench.algorithmic_bytes("sure", N, n, 4) == 8 * N
     assert bench.algorithmic_bytes("idwt", N, n, 4) == sum(16 * N / 4 ** j for j in range(4)) / 4
     assert len(bench.source_hash()) == 16
+
+
+def test_iteration_roofline_arithmetic():
+    sys.path.insert(0, ROOT)
+    import bench
+    # F_alg per slice-iteration: about 24 MFLOP at 256x256 db4 s=4, 38.6 at 320x320 s=5
+    assert abs(bench.iteration_flops(256, 256, 4, 8) / 1e6 - 24.2) < 0.2
+    assert abs(bench.iteration_flops(320, 320, 5, 8) / 1e6 - 38.6) < 0.2
+    N, n = 65536, 13107
+    r = bench.iteration_roofline(10e-6, 256, 256, n, 4, 8, 6800.0, 80.0)
+    b, f = 16 * N + 12 * n + N / 8, bench.iteration_flops(256, 256, 4, 8)
+    assert r["bytes_per_slice_iter"] == b
+    assert abs(r["hbm_frac"] - b / 6.8e12 / 10e-6) < 1e-12
+    assert abs(r["alu_frac"] - f / 80e12 / 10e-6) < 1e-12
+    assert r["bound"] == ("alu" if f / 80e12 > b / 6.8e12 else "hbm")
+    assert r["frac"] == max(r["hbm_frac"], r["alu_frac"])
+    assert bench.bound_of(100.0, 1.0, 6800.0, 80.0) == "hbm"
+    assert bench.bound_of(1.0, 1e6, 6800.0, 80.0) == "alu"

@@ -6,6 +6,11 @@ convolution), central finite differences of the oracle's own forward pass
 for its hand-written gradient and JVP, the exact Jacobian trace for the
 Hutchinson estimate, Stein's identity checked by Monte Carlo for SURE, the
 published first outputs of SplitMix64, and the bfloat16 rounding rule.
+Adam's step is pinned by the closed forms that its bias correction makes
+exact (the first step from zero moments and any constant gradient move each
+parameter by lr g / (|g| + eps)), by where eps enters, by its invariance to
+the scale of the gradients, and by its reduction to sign descent at
+beta1 = beta2 = 0.
 """
 import numpy as np
 import pytest
@@ -163,3 +168,56 @@ def test_bf16_forward_stays_close_to_fp64():
     n64, _ = C.forward(params, C.input_planes(r, 0.5))
     n16, _ = C.forward(params, C.input_planes(r, 0.5), bf16=True)
     assert np.linalg.norm(n16 - n64) / np.linalg.norm(n64) < 3e-2
+
+
+# ---- Adam (Kingma and Ba 2015, Algorithm 1) ----------------------------------------
+
+def test_adam_first_step_is_lr_times_normalised_gradient():
+    rng = np.random.default_rng(3)
+    p0, g = rng.standard_normal(50), rng.standard_normal(50)
+    z = np.zeros(50)
+    p1, m1, v1 = C.adam_step(p0, g, z, z, 1e-3, 0.9, 0.999, 1e-8, 1)
+    # bias correction makes m_hat = g and v_hat = g^2 exactly at t = 1
+    assert np.allclose(p1, p0 - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m1, 0.1 * g, rtol=1e-14) and np.allclose(v1, 0.001 * g * g, rtol=1e-12)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    # m_t = (1 - beta1^t) g and v_t = (1 - beta2^t) g^2: the corrected moments are g and g^2
+    rng = np.random.default_rng(4)
+    p, g = rng.standard_normal(20), rng.standard_normal(20)
+    m = v = np.zeros(20)
+    p0 = p.copy()
+    for t in range(1, 61):
+        p, m, v = C.adam_step(p, g, m, v, 1e-2, 0.9, 0.999, 0.0, t)
+    assert np.allclose(p, p0 - 60 * 1e-2 * np.sign(g), rtol=0, atol=1e-12)
+
+
+def test_adam_eps_is_added_after_the_square_root():
+    g = np.array([1e-8, -1e-8])
+    z = np.zeros(2)
+    p1, _, _ = C.adam_step(np.zeros(2), g, z, z, 1.0, 0.9, 0.999, 1e-8, 1)
+    assert np.allclose(p1, [-0.5, 0.5], rtol=1e-12)   # lr g / (|g| + eps) with |g| = eps
+
+
+def test_adam_is_invariant_to_the_gradient_scale():
+    rng = np.random.default_rng(5)
+    gs = rng.standard_normal((8, 30))
+    runs = []
+    for c in (1.0, 1e3):
+        p, m, v = np.ones(30), np.zeros(30), np.zeros(30)
+        for t, g in enumerate(gs, start=1):
+            p, m, v = C.adam_step(p, c * g, m, v, 1e-3, 0.9, 0.999, 0.0, t)
+        runs.append(p)
+    assert np.allclose(runs[0], runs[1], rtol=1e-13, atol=0)
+
+
+def test_adam_without_momentum_is_sign_descent():
+    rng = np.random.default_rng(6)
+    p = rng.standard_normal(25)
+    m = v = np.zeros(25)
+    for t in range(1, 6):
+        g = rng.standard_normal(25)
+        q, m, v = C.adam_step(p, g, m, v, 0.1, 0.0, 0.0, 0.0, t)
+        assert np.allclose(q, p - 0.1 * np.sign(g), rtol=0, atol=1e-15)
+        p = q

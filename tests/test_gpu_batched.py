@@ -9,6 +9,9 @@
   1e-4 relative L2, thresholds within 1e-3 or a certified SURE tie).
 * Every tuning computes the same method: each launch shape is checked against
   the oracle, and unsupported shapes are refused.
+* vdamp_solve_batched (slices in separate buffers, described one by one)
+  groups slices of equal iteration count and start, and gives per slice the
+  same results, bit for bit, as vdamp_solve on the same grouping.
 """
 import numpy as np
 import pytest
@@ -292,4 +295,52 @@ def test_full_size_batched_workload_on_sampled_slices():
                 assert _forced_step_ok(plan, prs[j], ops, rec.r_tilde, (j, k))
                 break
             assert rel(xi[k, j], rec.x_hat) < 1e-4, (j, k)
+    plan.close()
+
+
+def test_solve_batched_descriptors_equal_solve():
+    """Five slices in separate buffers: two groups of cold starts with different iteration
+    counts (3 and 5 iterations) and one resumed slice (r_tilde0 after 3 iterations, k0 = 3);
+    each result equals vdamp_solve on the same slices bit for bit, on two calls in a row."""
+    wl = synth.PLAIN_64_HAAR3
+    prs = [synth.make_problem(wl, i) for i in range(5)]
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=4)
+    B, N = plan.B, wl.ny * wl.nx
+    one = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ys = [one(q.y) for q in prs]
+    ms = [one(q.mask) for q in prs]
+    ps = [one(q.density) for q in prs]
+    iters = [3, 5, 3, 2, 3]
+    state = plan.solve(ys[3][None], ms[3][None], ps[3][None], [prs[3].sigma], 3,
+                       want_state=True)["r_tilde"][0].clone()
+    descs, outs = [], []
+    for i, q in enumerate(prs):
+        o = {"x_hat": torch.full((wl.ny, wl.nx), 7.0 + 0j, dtype=torch.complex64, device="cuda"),
+             "tau": torch.full((iters[i], B), -1.0, dtype=torch.float64, device="cuda")}
+        o["thr"], o["alpha"] = o["tau"].clone(), o["tau"].clone()
+        outs.append(o)
+        d = {"y": ys[i], "mask": ms[i], "density": ps[i], "sigma": q.sigma, "iters": iters[i], **o}
+        if i == 3:
+            d.update(r_tilde0=state, k0=3)
+        descs.append(d)
+    # references: the same groups through vdamp_solve
+    stk = lambda xs, idx: torch.stack([xs[i] for i in idx]).contiguous()
+    ref = {}
+    for idx, K in (([0, 2, 4], 3), ([1], 5)):
+        r = plan.solve(stk(ys, idx), stk(ms, idx), stk(ps, idx), [prs[i].sigma for i in idx], K)
+        for j, i in enumerate(idx):
+            ref[i] = {k: r[k][j] for k in ("x_hat", "tau", "thr", "alpha")}
+    r = plan.solve(ys[3][None], ms[3][None], ps[3][None], [prs[3].sigma], 2,
+                   r_tilde0=state[None].contiguous(), k0=3)
+    ref[3] = {k: r[k][0] for k in ("x_hat", "tau", "thr", "alpha")}
+    for call in range(2):
+        vb.vdamp_solve_batched(plan.handle, descs)
+        torch.cuda.synchronize()
+        assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+        for i in range(5):
+            for k in ("x_hat", "tau", "thr", "alpha"):
+                assert torch.equal(outs[i][k], ref[i][k]), (call, i, k)
+    bad = dict(descs[0], iters=0)
+    with pytest.raises(vb.VdampError):
+        vb.vdamp_solve_batched(plan.handle, [descs[1], bad])
     plan.close()

@@ -8,7 +8,10 @@ flips (2^-8 relative) that propagate:
 * one convolution, FP32 output: within 1e-5 of the largest magnitude;
   BF16 output: within 2^-8 relative per element (plus 1e-6 of the scale);
 * the whole network n, its JVP and the gradients: within 2e-2 relative L2;
-* weight gradient of one convolution (FP32 atomics): within 1e-5 relative.
+* weight gradient of one convolution (FP32 atomics): within 1e-5 relative;
+* one Adam step (FP32 state, each step fed the kernel's own previous state):
+  the moments within 1e-6 of the size of their terms, the parameter step
+  within 1e-5 relative plus the FP32 rounding of the parameter.
 Images of ragged sizes (partial 128-pixel tiles, borders) are included.
 """
 import numpy as np
@@ -252,3 +255,80 @@ def test_training_is_reproducible():
         states.append(net.state())
     for k in states[0]:
         assert np.array_equal(states[0][k], states[1][k]), k
+
+
+def test_adam_matches_oracle():
+    """vdamp_cnn_adam against the oracle's Adam step (Kingma and Ba, bias-corrected), six
+    steps with fresh gradients; each step of the oracle starts from the kernel's FP32
+    state, and the hyper-parameters are the FP32 values the kernel receives."""
+    rng = np.random.default_rng(11)
+    n = 10007
+    f32 = lambda x: float(np.float32(x))
+    lr, b1, b2, eps = f32(1e-3), f32(0.9), f32(0.999), f32(1e-8)
+    p = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda()
+    m = torch.zeros(n, dtype=torch.float32, device="cuda")
+    v = torch.zeros_like(m)
+    L = vb.load()
+    for t in range(1, 7):
+        g = torch.from_numpy((rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 1, n))
+                             .astype(np.float32)).cuda()
+        p0, m0, v0 = (x.double().cpu().numpy() for x in (p, m, v))
+        vb.check(L.vdamp_cnn_adam(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), n,
+                                  lr, b1, b2, eps, t, None), "vdamp_cnn_adam")
+        torch.cuda.synchronize()
+        pw, mw, vw = C.adam_step(p0, g.double().cpu().numpy(), m0, v0, lr, b1, b2, eps, t)
+        pg, mg, vg = (x.double().cpu().numpy() for x in (p, m, v))
+        gd = g.double().cpu().numpy()
+        # moments: within 1e-6 of the size of their two terms (m may cancel to ~0)
+        m_scale = np.abs(b1 * m0) + np.abs((1 - b1) * gd)
+        v_scale = np.abs(b2 * v0) + np.abs((1 - b2) * gd * gd)
+        assert float(np.max(np.abs(mg - mw) / m_scale)) < 1e-6, t
+        assert float(np.max(np.abs(vg - vw) / v_scale)) < 1e-6, t
+        # parameters: the step within 1e-5 relative, plus the FP32 rounding of p itself
+        bound = 1e-5 * np.abs(pw - p0) + 2.0 ** -24 * np.abs(pw)
+        assert bool(np.all(np.abs(pg - pw) <= bound)), (t, float(np.max(np.abs(pg - pw) - bound)))
+
+
+def test_conv_wait_that_runs_out_reports_a_timeout():
+    """Failure detection of the bounded tensor-core waits, with no fault: with a first-wait
+    limit of 0 polls every wait gives up at once, the kernel records the timeout, still waits
+    (with the default limit) for the operations in flight, frees its tensor memory and
+    returns; vdamp_cnn_status reports VDAMP_ETIMEOUT and the context stays usable: with the
+    default limit back, the same convolution is complete and matches the oracle."""
+    rng = np.random.default_rng(5)
+    h, w = 24, 20
+    x = C.to_bf16(rng.standard_normal((h * w, 32)))
+    wt = (rng.standard_normal((1, 32, 9, 32)) * 0.2).astype(np.float32)
+    bt = rng.standard_normal((1, 32)).astype(np.float32)
+    im = learned.Images([(h, w, 0, w, 0, 0)])
+    L = vb.load()
+    wdev, bdev = torch.from_numpy(wt).cuda(), torch.from_numpy(bt).cuda()
+    img = torch.empty(32 * 9 * 32, dtype=torch.bfloat16, device="cuda")
+    xt = torch.from_numpy(x.astype(np.float32)).cuda().to(torch.bfloat16)
+    out = torch.zeros((h * w, 32), dtype=torch.bfloat16, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    vb.check(L.vdamp_cnn_pack_weights(wdev.data_ptr(), 1, 32, 32, 32, 32, 0, img.data_ptr(),
+                                      None), "vdamp_cnn_pack_weights")
+
+    def conv():
+        vb.check(L.vdamp_cnn_conv3x3(xt.data_ptr(), 32, img.data_ptr(), 32, bdev.data_ptr(),
+                                     None, out.data_ptr(), 0, 0, 32, im.dev.data_ptr(), im.n,
+                                     im.ctiles, im.max_w, status.data_ptr(), None),
+                 "vdamp_cnn_conv3x3")
+
+    default = vb.vdamp_cnn_default_wait_limit()
+    assert default > 0
+    prev = vb.vdamp_cnn_set_wait_limit(0)
+    try:
+        assert prev == default
+        conv()
+        assert vb.vdamp_cnn_status(status) == vb.VDAMP_ETIMEOUT
+        assert "ran out" in vb.last_error()
+        assert int(status.item()) == 0          # read and cleared
+    finally:
+        vb.vdamp_cnn_set_wait_limit(default)
+    conv()
+    assert vb.vdamp_cnn_status(status) == vb.VDAMP_OK
+    ref = np.maximum(C.conv3x3(x.reshape(h, w, 32), C.to_bf16(wt[0]), bt[0]), 0).reshape(-1, 32)
+    got = out.float().cpu().numpy()
+    assert float(np.max(np.abs(got - ref) - 2 ** -8 * np.abs(ref))) <= 1e-5 * float(np.abs(ref).max())

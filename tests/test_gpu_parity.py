@@ -349,7 +349,7 @@ def test_host_buffer_entry_point_matches_device():
     thr, alpha = np.zeros_like(tau), np.zeros_like(tau)
     vb.vdamp_solve_host(plan.handle, 1, np.ascontiguousarray(pr.y[None]),
                         np.ascontiguousarray(pr.mask[None]), np.ascontiguousarray(pr.density[None]),
-                        [pr.sigma], K, None, x, tau, thr, alpha)
+                        [pr.sigma], K, None, x, tau, thr, alpha, k0=0)
     assert np.array_equal(x, d["x_hat"].cpu().numpy())
     assert np.array_equal(tau, d["tau"].cpu().numpy())
     plan.close()
@@ -396,6 +396,30 @@ def test_non_finite_input_is_reported():
     plan.close()
 
 
+def test_resume_reports_iterations_from_k0():
+    """A resumed solve (r_tilde0 and k0 = 4) that meets a non-finite tau reports iteration
+    k0 + k; a cold start with k0 != 0, or more iterations than the plan's max_iters, is
+    refused before anything is launched."""
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    y = pr.y.copy()
+    y[tuple(np.argwhere(pr.mask == 1)[5])] = np.nan
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_iters=8)
+    rt = torch.zeros((1, wl.ny * wl.nx), dtype=torch.complex64, device="cuda")
+    plan.solve(dev(y[None]), dev(pr.mask[None]), dev(pr.density[None]), [pr.sigma], 3,
+               r_tilde0=rt, k0=4)
+    st, it = vb.vdamp_device_status(plan.handle)
+    assert st == vb.VDAMP_ENUMERIC and it == 4
+    yd, m, p = _problem_on_device(pr)
+    with pytest.raises(vb.VdampError) as e:
+        plan.solve(yd, m, p, [pr.sigma], 3, k0=2)
+    assert e.value.status == vb.VDAMP_EINVAL
+    with pytest.raises(vb.VdampError) as e:
+        plan.solve(yd, m, p, [pr.sigma], 9)
+    assert e.value.status == vb.VDAMP_EINVAL and "max_iters" in vb.last_error()
+    plan.close()
+
+
 def test_invalid_solve_arguments_launch_nothing():
     wl = synth.PLAIN_64_HAAR3
     pr = synth.make_problem(wl)
@@ -426,20 +450,39 @@ def test_largest_supported_slice():
 
 
 @pytest.mark.parametrize("wl", [synth.PLAIN_64_HAAR3, synth.PLAIN_256_DB4_4])
-def test_fused_and_stepwise_paths_agree(wl):
-    """The persistent cluster solve and the one-kernel-per-step solve compute the same
-    iteration; they differ only in the blocking of the tau partial sums."""
+def test_persistent_cluster_solve_matches_oracle(wl):
+    """The persistent cluster solve (VDAMP_OPT_FUSED = 1: the whole solve as one launch in
+    which a thread-block cluster iterates the slice) against the FP64 oracle at every
+    iteration (x_hat_k and tau_k to the solve tolerances, thresholds to 1e-3 or a certified
+    tie), and against the one-kernel-per-step solve; the launch count shows which ran."""
     pr = synth.make_problem(wl)
+    K = wl.iters if wl is synth.PLAIN_64_HAAR3 else 5
+    ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+    res = O.vdamp(pr.y, pr.mask, pr.density, pr.sigma, pr.wavelet, pr.levels, K, want_x=True,
+                  ops=ops)
     plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
     y, m, p = _problem_on_device(pr)
-    K = wl.iters if wl is synth.PLAIN_64_HAAR3 else 5
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 1)
     fused = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
+    torch.cuda.synchronize()
+    n_fused = vb.vdamp_last_launch_count(plan.handle)
+    assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
     vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_FUSED, 0)
     step = plan.solve(y, m, p, [pr.sigma], K, want_iters=True)
     torch.cuda.synchronize()
-    for k in range(K):
-        assert rel(fused["x_hat_iters"].cpu().numpy()[k, 0], step["x_hat_iters"].cpu().numpy()[k, 0]) < 1e-5, k
-        assert rel(fused["tau"].cpu().numpy()[0, k], step["tau"].cpu().numpy()[0, k]) < 1e-5, k
+    n_step = vb.vdamp_last_launch_count(plan.handle)
+    assert n_fused == 2, n_fused            # the sigma upload and the one persistent launch
+    assert n_step > 10 * K, n_step          # one kernel per step of every iteration
+    xf = fused["x_hat_iters"].cpu().numpy()[:, 0]
+    xs = step["x_hat_iters"].cpu().numpy()[:, 0]
+    tf = fused["tau"].cpu().numpy()[0]
+    thf = fused["thr"].cpu().numpy()[0]
+    for k, rec in enumerate(res.records):
+        assert rel(xf[k], rec.x_hat) < 1e-4, (k, rel(xf[k], rec.x_hat))
+        assert tau_ok(tf[k], rec.tau), (k, rel(tf[k], rec.tau))
+        assert theta_ok(rec.r, ops.sbs, rec.tau, thf[k], rec.theta)[0], k
+        assert rel(xf[k], xs[k]) < 1e-5, k
+        assert rel(tf[k], step["tau"].cpu().numpy()[0, k]) < 1e-5, k
     plan.close()
 
 

@@ -58,6 +58,7 @@ def test_spectra_match_bruteforce_s(lib, name, ny, nx, s):
     (64, 4, "haar", 1),      # too small
     (2048, 64, "haar", 1),   # too large
     (64, 64, "db4", 3, 0),   # max_batch < 1
+    (64, 64, "db4", 3, 1, 0),   # max_iters < 1
 ])
 def test_plan_create_rejects_bad_arguments(lib, args):
     with pytest.raises(vb.VdampError) as e:
@@ -70,4 +71,8 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.vdamp_plan_destroy(None) == vb.VDAMP_EINVAL
     assert lib.vdamp_num_subbands(None) == -1
     assert lib.vdamp_psi(None, 1, None, None, None) == vb.VDAMP_EINVAL
-    assert lib.vdamp_solve(None, 1, *([None] * 4), 1, *([None] * 8)) == vb.VDAMP_EINVAL
+    assert lib.vdamp_solve(None, 1, *([None] * 4), 1, None, 0, *([None] * 7)) == vb.VDAMP_EINVAL
+    assert lib.vdamp_solve_host(None, 1, *([None] * 4), 1, None, 0, *([None] * 5)) == \
+        vb.VDAMP_EINVAL
+    assert lib.vdamp_solve_batched(None, None, 1, None) == vb.VDAMP_EINVAL
+    assert "vdamp_solve_batched" in vb.last_error()

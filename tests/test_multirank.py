@@ -1,8 +1,10 @@
 """Host logic of the multi-GPU benchmark on CPU: two gloo ranks.
 
-Slices are independent problems, so ranks share no data: the only cross-rank
-step is the max over ranks of the timed region, from which the whole-job
-throughput (all ranks' slice-iterations over the slowest rank's time) follows.
+Slices are independent problems, so ranks share no data: the cross-rank steps
+are the max over ranks of the timed region, from which the whole-job
+throughput (all ranks' slice-iterations over the slowest rank's time) follows,
+and the host gather of the per-slice results on rank 0 after the batched
+workload was partitioned over the ranks (balanced by pixels x iterations).
 """
 import os
 import socket
@@ -54,3 +56,55 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.slowest_rank_ms(7.0, 1) == 7.0
     assert bench.job_throughput(1, 10, 30, 1, 1000.0) == 300.0
+
+
+def test_partition_is_balanced_and_covers_every_slice_once():
+    import bench
+    import numpy as np
+    rng = np.random.default_rng(0)
+    # the mixed workload's costs (pixels x iterations) and random ones
+    mixed = [128 * 128 * 30] * 32 + [256 * 256 * 30] * 32 + [384 * 320 * 30] * 32
+    for costs in (mixed, [320 * 320 * 20] * 256, list(rng.integers(1, 1000, 77))):
+        for world in (1, 2, 3, 8):
+            parts = bench.partition_slices(costs, world)
+            flat = sorted(i for q in parts for i in q)
+            assert flat == list(range(len(costs)))
+            loads = [sum(costs[i] for i in q) for q in parts]
+            assert max(loads) - min(loads) <= max(costs)
+    assert bench.partition_slices([5] * 256, 8) == [list(range(r, 256, 8)) for r in range(8)]
+
+
+def _gather_worker(rank, world, port, out):
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    costs = [128 * 128] * 5 + [384 * 320] * 4
+    parts = bench.partition_slices(costs, world)
+    local = {i: ("slice", i, rank) for i in parts[rank]}
+    res = bench.gather_by_slice(parts, world, rank, local, len(costs))
+    if rank == 0:
+        out["res"] = res
+        out["parts"] = parts
+    else:
+        out[f"none{rank}"] = res is None
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_gather_returns_every_slice_in_order():
+    world = 2
+    port = _free_port()
+    out = mp.get_context("spawn").Manager().dict()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_gather_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res, parts = out["res"], out["parts"]
+    assert [r[1] for r in res] == list(range(9))
+    for i, r in enumerate(res):
+        assert r[2] == (0 if i in parts[0] else 1)
+    assert all(len(q) > 0 for q in parts)
+    assert out["none1"] is True

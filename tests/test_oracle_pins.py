@@ -280,6 +280,52 @@ def test_sure_threshold_never_zero_when_noisy():
     assert th > 0.0
 
 
+def _tie_tau():
+    """tau at which SURE of one coefficient of magnitude 1 has two equal global minima:
+    the interior minimiser theta = tau / 2 of theta^2 + tau - tau theta (value
+    tau - tau^2 / 4) and the constant 1 - tau for theta >= 1; equal where
+    tau^2 - 8 tau + 4 = 0, i.e. tau = 4 - 2 sqrt(3)."""
+    return 4.0 - 2.0 * math.sqrt(3.0)
+
+
+def test_sure_tie_goes_to_the_smaller_threshold():
+    """Two exactly tied minima (up to rounding): the smaller theta wins; moving tau by
+    1e-6 either way breaks the tie in the direction the closed form says."""
+    t0 = _tie_tau()
+    for n in (1, 5):                       # n equal coefficients scale SURE by n
+        a = np.ones(n)
+        for t in (t0, t0 * (1 + 1e-14), t0 * (1 - 1e-14)):   # inside the 1e-12 tie band
+            th, v = O.sure_threshold(a, t)
+            assert abs(th - t / 2) < 1e-12, (n, t, th)
+            assert abs(v - n * (t - t * t / 4)) < 1e-12
+        th, _ = O.sure_threshold(a, t0 * (1 + 1e-6))   # interior value now above the flat one
+        assert th == 1.0
+        t = t0 * (1 - 1e-6)
+        th, _ = O.sure_threshold(a, t)                 # interior value below the flat one
+        assert abs(th - t / 2) < 1e-12
+
+
+def test_denoise_without_effective_noise_keeps_r():
+    """tau_b <= 0 (full sampling, sigma = 0): theta = alpha = 0, w_hat = r, line 8 gives
+    r~ = r, and the iteration returns x0 (to rounding) from its first step."""
+    rng = np.random.default_rng(31)
+    ny = nx = 32
+    x0 = _crand(rng, ny, nx)
+    mask = np.ones((ny, nx), dtype=np.uint8)
+    p = np.ones((ny, nx))
+    ops = O.make_operators(mask, p, "db4", 2)
+    y = O.fft2u(x0)
+    rec = O.iterate(np.zeros(ny * nx, dtype=np.complex128), y, ops, 0.0, want_x=True)
+    assert np.all(rec.tau == 0.0)
+    assert np.all(rec.theta == 0.0) and np.all(rec.alpha == 0.0)
+    assert np.array_equal(rec.w_hat, rec.r)
+    rt = O.next_r_tilde(rec, ops)
+    assert np.all(np.isfinite(rt)) and np.allclose(rt, rec.r, rtol=0, atol=1e-12)
+    assert np.allclose(rec.x_hat, x0, rtol=0, atol=1e-12)
+    w, th, al = O.denoise(rec.r, np.zeros(len(ops.sbs)), ops.sbs)
+    assert np.array_equal(w, rec.r) and not th.any() and not al.any()
+
+
 # ------------------------------------------------------- line 8, line 10 ---
 
 def test_onsager_linear_denoiser_and_identity():
@@ -413,7 +459,48 @@ def _bad_iterate_no_density_compensation(r_tilde, y, ops, sigma2, want_x=False):
     return O.Record(r_tilde=r_tilde, z=z, r=r, tau=tau, theta=theta, alpha=alpha, w_hat=w_hat)
 
 
+def _bad_sure_tie_larger(a, tau):
+    """The exact minimiser with ties sent to the LARGEST theta (a plausible slip)."""
+    a = np.sort(np.asarray(a, dtype=np.float64))
+    n = a.size
+    c = np.concatenate([[0.0], np.cumsum(a * a)])
+    inv = np.where(a > 0, 1.0 / np.where(a > 0, a, 1.0), 0.0)
+    hsum = np.concatenate([np.cumsum(inv[::-1])[::-1], [0.0]])
+    m = np.arange(n + 1)
+    k = n - m
+    lo = np.concatenate([[0.0], a])
+    hi = np.concatenate([a, [np.inf]])
+    th = np.maximum(tau * hsum / (2.0 * np.maximum(k, 1)), lo)
+    val = c - m * tau + k * th * th + k * tau - tau * th * hsum
+    ok = th < hi
+    ok[n] = True
+    th[n] = a[-1]
+    val[n] = c[n] - n * tau
+    vals = np.where(ok, val, np.inf)
+    cand = np.nonzero(vals <= vals.min() + 1e-12 * abs(vals.min()))[0]
+    best = cand[np.argmax(th[cand])]
+    return float(th[best]), float(vals[best])
+
+
+def _bad_denoise_no_zero_tau_branch(r, tau, sbs):
+    """Lines 6-7 without the tau <= 0 branch: the search runs on a noiseless subband."""
+    w_hat = np.empty_like(r)
+    theta = np.zeros(len(sbs))
+    alpha = np.zeros(len(sbs))
+    for sb in sbs:
+        rb = r[sb.offset:sb.offset + sb.size]
+        a = np.abs(rb)
+        th, _ = O.sure_threshold(a, float(tau[sb.index]))
+        theta[sb.index] = th
+        alpha[sb.index] = O.soft_divergence_mean(a, th)
+        w_hat[sb.offset:sb.offset + sb.size] = O.soft(rb, th)
+    return w_hat, theta, alpha
+
+
 @pytest.mark.parametrize("target,bad,pins", [
+    ("sure_threshold", _bad_sure_tie_larger, ["test_sure_tie_goes_to_the_smaller_threshold"]),
+    ("denoise", _bad_denoise_no_zero_tau_branch,
+     ["test_denoise_without_effective_noise_keeps_r"]),
     ("tau_estimate", _bad_tau_no_outer_pinv, ["test_r0_and_tau_unbiased_monte_carlo"]),
     ("tau_estimate", _bad_tau_no_noise, ["test_tau_full_sampling_closed_form"]),
     ("soft_divergence_mean", _bad_alpha_full_divergence,

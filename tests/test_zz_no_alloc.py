@@ -9,6 +9,10 @@ reached by the solver, and compares its tau with the tau that vdamp_iterate
 the tolerance the parity tests use: 1e-4 relative L2 on the tau vector and
 1e-3 relative per subband.
 
+A third test alternates two configurations (sizes, wavelets and levels) on one
+stream with no synchronisation in between: each call fills the shared scratch
+with its own tables on the device, so every result must still match.
+
 This file is named to be collected last, so that a run stopping at the first
 failure has already run every other test.
 """
@@ -74,3 +78,47 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         vb.vdamp_tau_estimate_noalloc(2048, 64, "db4", 2, t, t, t, 0.1, t)
     assert e.value.status == vb.VDAMP_EINVAL
     assert "scratch limit" in vb.last_error()
+
+
+def _reference_case(wl):
+    """(device residual z, mask, density, sigma, tau from the plan path) for one workload."""
+    pr = synth.make_problem(wl)
+    ny, nx, N = wl.ny, wl.nx, wl.ny * wl.nx
+    y = torch.from_numpy(pr.y[None].copy()).cuda()
+    m = torch.from_numpy(pr.mask[None].copy()).cuda()
+    p = torch.from_numpy(pr.density[None].copy()).cuda()
+    plan = vb.Plan(ny, nx, wl.wavelet, wl.levels)
+    img = torch.empty((1, ny, nx), dtype=torch.complex64, device="cuda")
+    kspace = torch.empty_like(img)
+    r = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    rn = torch.empty_like(r)
+    tau_ref = torch.empty((1, plan.B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau_ref), torch.empty_like(tau_ref)
+    r_tilde = plan.solve(y, m, p, [pr.sigma], 3, want_state=True)["r_tilde"]
+    vb.vdamp_iterate(plan.handle, 1, r_tilde, y, m, p, [pr.sigma], r, tau_ref, thr, alpha, rn)
+    vb.vdamp_psi_h(plan.handle, 1, r_tilde, img)
+    vb.vdamp_fft2(plan.handle, 1, img, kspace)
+    z = torch.where(m.bool(), y - kspace, torch.zeros_like(y)).contiguous()
+    torch.cuda.synchronize()
+    want = tau_ref.cpu().numpy()[0]
+    plan.close()
+    return z[0], m[0].contiguous(), p[0].contiguous(), float(pr.sigma), want
+
+
+def test_noalloc_alternating_configurations_on_one_stream():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    vb.load()
+    cases = [(wl, _reference_case(wl)) for wl in (synth.PLAIN_256_DB4_4, synth.PLAIN_64_HAAR3)]
+    outs = []
+    for rep in range(2):   # A, B, A, B back to back, no host synchronisation between them
+        for wl, (z, m, p, sigma, want) in cases:
+            t = torch.full((len(want),), -1.0, dtype=torch.float64, device="cuda")
+            vb.vdamp_tau_estimate_noalloc(wl.ny, wl.nx, wl.wavelet, wl.levels, z, m, p, sigma, t)
+            outs.append((t, want, wl.name, rep))
+    torch.cuda.synchronize()
+    for t, want, name, rep in outs:
+        got = t.cpu().numpy()
+        assert _rel(got, want) < 1e-4, (name, rep, _rel(got, want))
+        assert np.max(np.abs(got - want) / want) < 1e-3, (name, rep)
