@@ -352,7 +352,7 @@ def job_throughput(world, steps, iters_per_step, slices_per_rank, max_ms):
 KERNEL_SOURCES = {
     "idwt": ("dwt.cu", "dwt_dev.cuh", "vdamp_internal.cuh"),
     "dwt": ("dwt.cu", "dwt_dev.cuh", "vdamp_internal.cuh"),
-    "sure": ("sure.cu", "sure_dev.cuh", "vdamp_internal.cuh"),
+    "sure": ("sure.cu", "sure_dev.cuh", "sure_prune_dev.cuh", "vdamp_internal.cuh"),
     "fft_rows": ("fft.cu", "fft_dev.cuh", "vdamp_internal.cuh"),
     "col_pass": ("fft_col.cu", "fft_dev.cuh", "vdamp_internal.cuh"),
 }

@@ -135,7 +135,9 @@ int vdamp_last_launch_count(const vdamp_plan* plan);
  *       thread-block cluster per slice, scale 1 in its own launch, while
  *       batch x cluster size <= the SM count; 0: one launch per scale
  *   [7] parts per subband of the SURE threshold search (Algorithm 1 lines
- *       6-7): 1 = one CTA per subband sorts and searches (one launch);
+ *       6-7): 1 = one CTA per subband bounds SURE per bucket of magnitudes,
+ *       sorts only the candidate buckets and searches them (subbands with
+ *       too many candidates take the full sort in a second, one-wave kernel);
  *       2, 4 or 8 = subbands above 2048 coefficients split over up to that
  *       many CTAs (a sort and a search launch); 0 = 8 while the CTAs of the
  *       split (batch x the parts of all subbands) fit on the SMs at once,
@@ -313,6 +315,15 @@ vdamp_status vdamp_cnn_onsager(const float* r, const float* f, const double* tau
                                const double* sure_soft, int B, const double* sums,
                                const int* images, int n_img, int total_tiles, float* r_tilde,
                                float* w_hat, int* use_out, double* alpha_out, void* stream);
+
+/* Diagnostics of the one-CTA-per-subband threshold search (tuning entry 7 =
+ * 1, chosen automatically for many slices): it bounds SURE per bucket of
+ * magnitudes and sorts only the buckets that can hold the minimiser; a
+ * subband whose candidates do not fit its tables (heavy ties, degenerate
+ * data) is solved by the full sort and search instead.  Waits for `stream`
+ * and writes to *count how many subbands took that path since the plan was
+ * created (Sec. 3's minimiser either way). */
+vdamp_status vdamp_sure_fallback_count(vdamp_plan* plan, int* count, void* stream);
 
 /* Minimum SURE value of each subband at the last threshold search (solve
  * or iterate) of this plan: double [batch][B], copied to `out` (device or

@@ -75,6 +75,7 @@ _SIGS = {
     "vdamp_cnn_default_wait_limit": (ctypes.c_uint, []),
     "vdamp_cnn_status": (_I, [_P, _P]),
     "vdamp_fma_peak": (_I, [_I, _I, _D, _D, _P]),
+    "vdamp_sure_fallback_count": (_I, [_P, ctypes.POINTER(_I), _P]),
 }
 
 VDAMP_TUNING_LEN = 8
@@ -279,6 +280,14 @@ def vdamp_fma_peak(precision, iters, stream=None):
     check(load().vdamp_fma_peak(precision, iters, ctypes.byref(tf), ctypes.byref(ms),
                                 _stream(stream)), "vdamp_fma_peak")
     return tf.value, ms.value
+
+
+def vdamp_sure_fallback_count(plan, stream=None) -> int:
+    """Subbands the pruned one-CTA threshold search left to the full sort (running total)."""
+    n = _I(0)
+    check(load().vdamp_sure_fallback_count(plan, ctypes.byref(n), _stream(stream)),
+          "vdamp_sure_fallback_count")
+    return n.value
 
 
 def vdamp_cnn_set_wait_limit(polls):

@@ -222,6 +222,7 @@ struct vdamp_plan {
     double4_32a* partrec = nullptr;
     double4_32a* bestrec = nullptr;
     unsigned* counter = nullptr;
+    int* fallback = nullptr;           // [3 + max_batch B] subbands left to the full SURE sort
     float4* coef = nullptr;
     float* sigma_d = nullptr;
     int* status = nullptr;
@@ -258,7 +259,7 @@ static void plan_free(vdamp_plan* p) {
     void* bufs[] = {p->ey,       p->ex,      p->tw_y,    p->tw_x,    p->u,      p->kbuf,
                     p->ll0,      p->ll1,     p->rA,      p->rB,      p->tau_part, p->sorted,
                     p->partrec,  p->bestrec, p->counter, p->coef,    p->sigma_d, p->status,
-                    p->sure_val,
+                    p->sure_val, p->fallback,
                     p->st_y,     p->st_mask, p->st_p,    p->st_x,    p->st_r0,  p->st_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -427,6 +428,7 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(dalloc(&p->bestrec, MB * p->B * SURE_MAX_PARTS, &acc));
     A(dalloc(&p->counter, MB * p->B, &acc));
     A(dalloc(&p->sure_val, MB * p->B, &acc));
+    A(dalloc(&p->fallback, 3 + MB * p->B, &acc));
     A(dalloc(&p->coef, MB * p->B, &acc));
     A(dalloc(&p->sigma_d, MB, &acc));
     A(dalloc(&p->status, (size_t)2, &acc));
@@ -457,6 +459,7 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(cudaMemcpy(p->tw_x, twx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice));
     A(cudaMemset(p->status, 0, 2 * sizeof(int)));
     A(cudaMemset(p->counter, 0, MB * p->B * sizeof(unsigned)));  // each search returns it to 0
+    A(cudaMemset(p->fallback, 0, 3 * sizeof(int)));               // each fallback launch empties it
     A(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     // shared-memory attributes large enough for every tile choice the tuner may make
     p->smem_col = vdamp::col_pass_smem(ny, cb, nt);
@@ -782,6 +785,7 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     a.bestrec = p->bestrec;
     a.counter = p->counter;
     a.sure_out = p->sure_val;
+    a.fallback = p->fallback;
     // Split big subbands over several CTAs only while the split grid fits in one wave
     // (each part rereads its whole subband: past one wave one CTA per subband is
     // faster), unless the tuning fixes the number of parts.
@@ -794,9 +798,9 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     if ((int)(p->N / 4) > SURE_SMALL_BAND && a.max_parts < SURE_MIN_PARTS_BIG)
         a.max_parts = SURE_MAX_PARTS;
     c.pre();
-    // one kernel (sort and search in one CTA) when every subband is one part, else two
-    c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), c.st), VDAMP_KERNEL_SURE,
-          a.max_parts == 1 ? 1 : 2);
+    // the pruned search and its fallback when every subband is one part, else sort and search
+    c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), std::max(p->num_sms, 1), c.st),
+          VDAMP_KERNEL_SURE, 2);
 }
 
 void enq_line8(Ctx& c, const float2* r, float2* out) {
@@ -937,6 +941,7 @@ void enq_fused(Ctx& c, const SolveArgs& s) {
     u.bestrec = p->bestrec;
     u.counter = p->counter;
     u.sure_out = p->sure_val;
+    u.fallback = p->fallback;
     u.max_parts = SURE_MAX_PARTS;
     f.l8.src = make_src(p, vdamp::SRC_LINE8, nullptr);
     f.l8.N = N;
@@ -1754,6 +1759,13 @@ extern "C" vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count,
         groups[i].plan->last_launches = launches[i] + hit->launches[i];
         groups[i].plan->last_k0 = 0;
     }
+    return VDAMP_OK;
+}
+
+extern "C" vdamp_status vdamp_sure_fallback_count(vdamp_plan* p, int* count, void* stream) {
+    if (!p || !count) return fail(VDAMP_EINVAL, "vdamp_sure_fallback_count: NULL");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaMemcpy(count, p->fallback + 2, sizeof(int), cudaMemcpyDeviceToHost));
     return VDAMP_OK;
 }
 

@@ -195,6 +195,7 @@ struct SureArgs {
     double4_32a* bestrec; // [batch][B][SURE_MAX_PARTS] (SURE, theta, H, m) of a part's best
     unsigned* counter;    // [batch][B] search parts done (returns to 0 after each search)
     double* sure_out;     // [batch][B] minimum SURE of the last search
+    int* fallback;        // [3 + batch B]: subbands the pruned search leaves to the full sort
 };
 
 struct Line8Args {
@@ -235,7 +236,10 @@ cudaError_t launch_col_pass(const ColArgs& a, int batch, cudaStream_t st);
 size_t col_pass_smem(int ny, int cb, int ntypes);
 cudaError_t launch_dwt_level(const DwtArgs& a, int batch, cudaStream_t st);
 cudaError_t launch_idwt_level(const IdwtArgs& a, int batch, cudaStream_t st);
-cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, cudaStream_t st);
+// fallback_ctas: grid of the fallback kernel that follows the pruned search
+// (max_parts == 1); one wave of CTAs.
+cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, int fallback_ctas,
+                        cudaStream_t st);
 size_t sure_smem(int max_band);
 cudaError_t launch_line8(const Line8Args& a, int batch, cudaStream_t st);
 cudaError_t configure_col_pass(size_t smem_bytes);

@@ -420,6 +420,52 @@ def test_resume_reports_iterations_from_k0():
     plan.close()
 
 
+@pytest.mark.parametrize("mag", [1.2, 0.0])
+def test_one_cta_threshold_search_on_a_degenerate_subband(mag):
+    """The one-CTA-per-subband threshold search (tuning entry 7 = 1) on a subband whose
+    1024 magnitudes are all equal to mag sqrt(tau) (mag 1.2: one bucket far above the
+    table's limit and holding the minimiser theta = max a, so the subband must take the
+    full sort, and the running count shows it did), or zero (mag 0: magnitudes at the FP32
+    rounding level, far below the noise: the flat top, pruned search); every other subband
+    from the oracle's state.  r~ is chosen and y = m F Psi^H r~, so that z ~ 0 and r_k = r~
+    up to FP32 rounding.  Teacher-forced against the oracle, on two calls in a row (the
+    fallback list must empty itself)."""
+    wl = synth.PLAIN_64_HAAR3
+    pr = synth.make_problem(wl)
+    ops = O.make_operators(pr.mask, pr.density, pr.wavelet, pr.levels)
+    y0 = np.where(pr.mask == 1, pr.y.astype(np.complex128), 0.0)
+    rec0 = O.iterate(np.zeros(wl.ny * wl.nx, np.complex128), y0, ops, float(pr.sigma) ** 2)
+    rt = O.next_r_tilde(rec0, ops).astype(np.complex64)
+    sb = ops.sbs[-1]   # D1, 32 x 32
+    tau_d1 = float(O.tau_estimate(np.zeros((wl.ny, wl.nx)), ops, float(pr.sigma) ** 2)[sb.index])
+    ph = np.exp(2j * np.pi * np.random.default_rng(3).random(sb.size))
+    rt[sb.offset:sb.offset + sb.size] = (mag * math.sqrt(tau_d1) * ph).astype(np.complex64)
+    y = np.where(pr.mask == 1, ops.phi(ops.psi_h(rt.astype(np.complex128))), 0.0)
+    y32 = y.astype(np.complex64)
+    rec = O.iterate(rt.astype(np.complex128), y32.astype(np.complex128), ops,
+                    float(pr.sigma) ** 2)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    plan.set_tuning(vb.vdamp_plan_get_tuning(plan.handle)[:7] + [1])
+    N, B = wl.ny * wl.nx, plan.B
+    r = torch.empty((1, N), dtype=torch.complex64, device="cuda")
+    rn = torch.empty_like(r)
+    tau = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    thr, alpha = torch.empty_like(tau), torch.empty_like(tau)
+    before = vb.vdamp_sure_fallback_count(plan.handle)
+    for call in range(2):
+        vb.vdamp_iterate(plan.handle, 1, dev(rt[None]), dev(y32[None]), dev(pr.mask[None]),
+                         dev(pr.density[None]), [pr.sigma], r, tau, thr, alpha, rn)
+        torch.cuda.synchronize()
+        assert vb.vdamp_device_status(plan.handle)[0] == vb.VDAMP_OK
+        assert rel(r.cpu().numpy()[0], rec.r) < 1e-5, call
+        assert tau_ok(tau.cpu().numpy()[0], rec.tau), call
+        ok, band = theta_ok(rec.r, ops.sbs, rec.tau, thr.cpu().numpy()[0], rec.theta)
+        assert ok, (call, band)
+    after = vb.vdamp_sure_fallback_count(plan.handle)
+    assert after - before == (2 if mag > 0 else 0), (before, after)
+    plan.close()
+
+
 def test_invalid_solve_arguments_launch_nothing():
     wl = synth.PLAIN_64_HAAR3
     pr = synth.make_problem(wl)
