@@ -4,8 +4,6 @@
 // part per subband (many slices), the pruned exact search of one CTA per
 // subband and a one-wave kernel for the subbands it leaves to the full sort.
 // The arithmetic is in sure_dev.cuh and sure_prune_dev.cuh.
-#include <algorithm>
-
 #include "sure_prune_dev.cuh"
 
 namespace vdamp {
@@ -23,12 +21,25 @@ __global__ void __launch_bounds__(SURE_THREADS) sure_search_kernel(const __grid_
     sure_search_part(a, a.k, blockIdx.x, a.B - 1 - (int)blockIdx.y, blockIdx.z, sm_keys);
 }
 
-// One CTA per subband (max_parts == 1, many slices): the pruned exact search
-// (sure_prune_dev.cuh); subbands it cannot take go to the fallback list.
-__global__ void __launch_bounds__(PRUNE_THREADS) sure_prune_kernel(const __grid_constant__ SureArgs a) {
+// Many slices (max_parts == 1): the pruned exact search (sure_prune_dev.cuh),
+// one large subband or four small ones per CTA; subbands it cannot take go
+// to the fallback list.  Grid: (prune_ctas, batch).
+__global__ void __launch_bounds__(PRUNE_THREADS, 1) sure_prune_kernel(const __grid_constant__ SureArgs a) {
     extern __shared__ unsigned sm_words[];
+    __shared__ PruneShared sh[PRUNE_GROUPS];
     cudaGridDependencySynchronize();
-    sure_prune_subband(a, a.B - 1 - (int)blockIdx.y, blockIdx.z, sm_words);
+    const int slice = blockIdx.y, item = blockIdx.x;
+    const int ns = prune_n_small(a.off, a.B), nbig = a.B - ns;
+    if (item < nbig) {   // a large subband, the finest first
+        sure_prune_subband<PRUNE_THREADS>(a, a.B - 1 - item, slice, sm_words, sh[0], threadIdx.x, 0);
+        return;
+    }
+    const int g = threadIdx.x / PRUNE_GROUP;
+    const int b = (item - nbig) * PRUNE_GROUPS + g;
+    if (b < ns)
+        sure_prune_subband<PRUNE_GROUP>(
+            a, b, slice, sm_words + g * prune_words<PRUNE_GROUP>(16 << PruneLimits<PRUNE_GROUP>::max_lpo),
+            sh[g], threadIdx.x % PRUNE_GROUP, 1 + g);
 }
 
 // The subbands on the fallback list, one after another per CTA (a fixed grid,
@@ -65,8 +76,8 @@ size_t sure_smem(int max_band) { return sure_split_smem_bytes(max_band); }
 cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, int fallback_ctas,
                         cudaStream_t st) {
     if (a.max_parts == 1) {
-        cudaError_t e = launch_pdl(sure_prune_kernel, dim3(1, a.B, batch), dim3(PRUNE_THREADS),
-                                   prune_smem_bytes(max_band), st, a);
+        cudaError_t e = launch_pdl(sure_prune_kernel, dim3(prune_ctas(a.off, a.B), batch),
+                                   dim3(PRUNE_THREADS), prune_smem_bytes(max_band), st, a);
         if (e != cudaSuccess) return e;
         return launch_pdl(sure_fallback_kernel, dim3(fallback_ctas), dim3(SURE_THREADS),
                           sure_smem_bytes(max_band), st, a);
@@ -89,8 +100,9 @@ cudaError_t configure_sure(size_t smem_bytes) {
     e = cudaFuncSetAttribute(sure_fallback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes);
     if (e != cudaSuccess) return e;
+    // the most the pruned search ever takes (4096 buckets)
     e = cudaFuncSetAttribute(sure_prune_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)std::min(smem_bytes, (size_t)(227 * 1024)));
+                             (int)prune_smem_bytes(SURE_SMALL_BAND));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sure_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes);

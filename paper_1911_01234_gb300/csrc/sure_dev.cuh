@@ -618,6 +618,16 @@ static __device__ void sure_sort_part(const SureArgs& a, const float2* rk, int p
     sure_sort_part_f<false>(a, rk, part, b, slice, keys);
 }
 
+// n / d in FP64 from an FP32 reciprocal and Newton steps (the FP64 divider is
+// slow here): d and n / d within the FP32 range, d != 0.
+__device__ __forceinline__ double pdiv(double n, double d) {
+    double r = (double)__frcp_rn((float)d);
+    r = r * (2.0 - d * r);
+    r = r * (2.0 - d * r);
+    const double q = n * r;
+    return q + r * (n - d * q);
+}
+
 // Writes the results of subband b at iteration k (one thread): tau, theta and
 // alpha of the chosen interval (bmi keys below theta, the sum bh of 1/a above
 // it, SURE value bv; bmi = nb for theta >= max a, bmi < 0 when nothing was
@@ -639,7 +649,7 @@ __device__ __forceinline__ void sure_finish(const SureArgs& a, int k, int b, int
     double theta = 0.0, alpha = 0.0;
     if (bmi >= 0) {
         theta = btheta;
-        alpha = (bmi == nb) ? 0.0 : ((double)(nb - bmi) - 0.5 * theta * bh) / (double)nb;
+        alpha = (bmi == nb) ? 0.0 : pdiv((double)(nb - bmi) - 0.5 * theta * bh, (double)nb);
     }
     a.tau_out[orow] = tau;
     a.thr_out[orow] = theta;
@@ -647,7 +657,7 @@ __device__ __forceinline__ void sure_finish(const SureArgs& a, int k, int b, int
     if (a.sure_out) a.sure_out[(size_t)slice * a.B + b] = bmi >= 0 ? bv : 0.0;
     // line 8 as r~ = r (1 - c1 / |r|) above theta and -c2 r below, c1 = theta / (1 - alpha),
     // c2 = alpha / (1 - alpha): no FP32 difference of nearly equal terms when alpha -> 1
-    const double inv = 1.0 / (1.0 - alpha);
+    const double inv = pdiv(1.0, 1.0 - alpha);
     a.coef[slice * a.B + b] =
         make_float4((float)theta, (float)(theta * inv), (float)(alpha * inv), 0.f);
     if (bmi < 0 || !isfinite(alpha) || !isfinite(theta) || !isfinite(inv)) record_numeric(a.status, k);

@@ -1,6 +1,6 @@
 // Exact SURE threshold of one subband without sorting it (Sec. 3, the
 // unnumbered equation after Algorithm 1; alpha of line 7): the batched form
-// of the threshold step, one CTA of PRUNE_THREADS threads per subband.
+// of the threshold step.
 //
 // SURE(theta) = sum_{a <= theta} (a^2 - tau) + sum_{a > theta} (theta^2 + tau - tau theta / a)
 // over the magnitudes a of the subband.  On each interval between consecutive
@@ -13,8 +13,7 @@
 //   2. per bucket j the count n_j and the sums of a^2 and of 1/a, as integer
 //      sums of 16-bit quantised offsets inside the bucket's value range (order-
 //      independent, hence deterministic; bucket 0 summed per thread in a fixed
-//      order instead), prefix sums over buckets (FP32 within a thread's run of
-//      buckets, FP64 across threads);
+//      order instead), prefix sums over buckets;
 //   3. for theta in bucket j's range [lo_j, hi_j) every magnitude of the bucket
 //      contributes at least lo_j^2 - tau (below theta: a^2 - tau; above:
 //      theta^2 + tau (1 - theta / a) >= theta^2), the others exactly a convex
@@ -25,49 +24,72 @@
 //   4. only buckets with LB_j <= UB + 1e-5 (sum a^2 + N_b tau) can hold the
 //      minimiser (the margin covers the FP32 rounding of the bounds): an
 //      empty one is a single quadratic piece, evaluated at once; the keys of
-//      the others (a few hundred of N_b) are gathered in a second pass over
-//      r_k, ranked within their bucket, and every interval piece inside these
-//      buckets is evaluated as in the full search.
+//      the others (a few hundred of N_b) are gathered from the magnitudes each
+//      thread holds in registers (r_k is read once), ranked within their
+//      bucket, and every interval piece inside these buckets is evaluated as
+//      in the full search.
 // A piece whose vertex lies beyond the bucket's upper edge is skipped: its
 // minimum over the interval lies in a higher bucket, where it is either
 // evaluated or bounded above UB.  Candidates are compared in FP32 (ties to
 // the smaller theta, then the smaller m), the winner recomputed in FP64.
 //
-// A subband whose candidates exceed the table (PRUNE_TABLE non-empty
-// buckets, PRUNE_CAP keys, PRUNE_BUCKET_MAX keys in one bucket; heavy ties
-// or degenerate data) is appended to a device list, and sure_fallback_kernel
-// solves it with the one-CTA full sort and search.
+// Precision and cost: FP64 runs at a small fraction of the FP32 rate on this
+// GPU, so no per-thread step uses it.  A prefix sum is carried as an FP64
+// base per warp (formed by one warp's FP64 shuffle scan over the warp totals)
+// plus an FP32 offset inside the warp; the FP32 comparisons use the base
+// rounded once to FP32, and only the winning candidate forms base + offset in
+// FP64.
+//
+// A CTA of PRUNE_THREADS threads takes one large subband, or four small ones
+// (up to PRUNE_SMALL_BAND magnitudes), one per group of PRUNE_GROUP threads
+// with a named barrier of its own: the fixed cost of the search's phases is
+// shared by four coarse subbands.  A subband whose candidates exceed its
+// tables (PruneLimits: non-empty candidate buckets, candidate magnitudes,
+// magnitudes of one candidate bucket; heavy ties or degenerate data) is
+// appended to a device list, and sure_fallback_kernel solves it with the
+// one-CTA full sort and search.
 #pragma once
 
 #include "sure_dev.cuh"
 
 namespace vdamp {
 
-#define PRUNE_THREADS 512
-#define PRUNE_MAX_LPO 8          // at most 4096 buckets (256 per octave)
-#define PRUNE_TABLE 128          // non-empty candidate buckets of one subband
-#define PRUNE_CAP 1024           // candidate magnitudes of one subband
-#define PRUNE_BUCKET_MAX 256     // magnitudes of one candidate bucket
+#define PRUNE_THREADS 1024       // threads of a CTA: one large subband, or four groups
+#define PRUNE_WARPS (PRUNE_THREADS / 32)
+#define PRUNE_GROUP 256          // threads of a group that takes one small subband
+#define PRUNE_GROUPS (PRUNE_THREADS / PRUNE_GROUP)
+#define PRUNE_SMALL_BAND (8 * PRUNE_GROUP)   // subbands up to 2048 magnitudes go to a group
 
-// log2 of the buckets per octave: about two buckets per magnitude, 16 .. 256.
-__host__ __device__ inline int prune_lpo(int nb) {
+// Limits per subband, for a whole CTA (NT = PRUNE_THREADS) and for a group:
+// log2 buckets per octave, candidate magnitudes, non-empty candidate buckets,
+// magnitudes of one candidate bucket.
+template <int NT> struct PruneLimits {
+    static constexpr int max_lpo = NT == PRUNE_THREADS ? 8 : 7;   // 4096 / 2048 buckets
+    static constexpr int cap = NT == PRUNE_THREADS ? 4096 : 1024;
+    static constexpr int table = NT == PRUNE_THREADS ? 512 : 128;
+    static constexpr int bucket_max = NT == PRUNE_THREADS ? 1024 : 256;
+};
+
+// log2 of the buckets per octave: about two buckets per magnitude, 16 .. 2^max_lpo.
+__host__ __device__ inline int prune_lpo(int nb, int max_lpo) {
     int l = 4;
-    while (l < PRUNE_MAX_LPO && (16 << l) < 2 * nb) ++l;
+    while (l < max_lpo && (16 << l) < 2 * nb) ++l;
     return l;
 }
 
-// Dynamic shared memory: three per-bucket words (count, sum of quantised a^2
-// offsets, sum of quantised 1/a offsets; later the packed local prefixes),
-// the candidate-bucket bits, and two candidate key buffers.
-inline size_t prune_smem_bytes(int max_band) {
-    const size_t nbk = (size_t)16 << prune_lpo(max_band);
-    return 3 * nbk * sizeof(unsigned) + (nbk / 32) * sizeof(unsigned) +
-           2 * (size_t)PRUNE_CAP * sizeof(float);
-}
+// A sum carried as an FP64 base and an FP32 offset (base + off in FP64 only
+// where the exact value is needed; basef = base rounded to FP32).
+struct Split {
+    double base;
+    float basef, off;
+    __device__ __forceinline__ float approx() const { return basef + off; }
+    __device__ __forceinline__ double exact() const { return base + (double)off; }
+    __device__ __forceinline__ Split plus(float x) const { return Split{base, basef, off + x}; }
+};
 
 struct PruneEntry {   // one non-empty candidate bucket
-    double c_lt;      // sum of a^2 over the magnitudes below the bucket
-    double h_gt;      // sum of 1/a over the magnitudes above the bucket
+    Split c_lt;       // sum of a^2 over the magnitudes below the bucket
+    Split h_gt;       // sum of 1/a over the magnitudes above the bucket
     float lo, hi;     // the bucket's value range [lo, hi)
     int m_lt;         // magnitudes below the bucket (exact zeros included)
     int n;            // magnitudes in the bucket
@@ -75,11 +97,38 @@ struct PruneEntry {   // one non-empty candidate bucket
     int fill;         // gather counter
 };
 
+// Dynamic shared memory of one subband's search (a CTA's, or a group's share):
+// three per-bucket words (count, sum of quantised a^2 offsets, sum of
+// quantised 1/a offsets; later the packed local prefixes), the candidate-
+// bucket bits, two candidate key buffers and the table of candidate buckets.
+template <int NT>
+__host__ __device__ inline size_t prune_words(int nbk) {
+    using Lim = PruneLimits<NT>;
+    return 3 * (size_t)nbk + nbk / 32 + 2 * (size_t)Lim::cap +
+           Lim::table * (sizeof(PruneEntry) / sizeof(unsigned));
+}
+// Dynamic shared memory of the pruned kernel: the larger of one CTA-wide
+// search and four group searches.
+inline size_t prune_smem_bytes(int max_band) {
+    const size_t big = prune_words<PRUNE_THREADS>(16 << PruneLimits<PRUNE_THREADS>::max_lpo);
+    const size_t small = PRUNE_GROUPS * prune_words<PRUNE_GROUP>(16 << PruneLimits<PRUNE_GROUP>::max_lpo);
+    (void)max_band;
+    return (big > small ? big : small) * sizeof(unsigned);
+}
+
+// Barrier of the threads taking one subband: the whole CTA (barrier 0), or a
+// group's named barrier 1 .. PRUNE_GROUPS.
+template <int NT>
+__device__ __forceinline__ void psync(int bar) {
+    if (NT == PRUNE_THREADS) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" :: "r"(bar), "r"(NT) : "memory");
+}
+
 // The best candidate a thread has seen, with what the FP64 recomputation needs.
 struct PruneBest {
     float v, t;       // FP32 SURE value and theta
     int m;            // magnitudes at or below theta (nb: theta = max a, the flat top)
-    double c, h;      // FP64 sum of a^2 below and of 1/a above theta
+    Split c, h;       // sum of a^2 below and of 1/a above theta
     float lo, hi;     // the piece: theta in [lo, hi) (lo = hi = theta on the flat top)
 };
 
@@ -87,8 +136,8 @@ __device__ __forceinline__ bool prune_better(float v, float t, int m, const Prun
     return v < b.v || (v == b.v && (t < b.t || (t == b.t && m < b.m)));
 }
 
-__device__ __forceinline__ void prune_take(PruneBest& b, float v, float t, int m, double c,
-                                           double h, float lo, float hi) {
+__device__ __forceinline__ void prune_take(PruneBest& b, float v, float t, int m, const Split& c,
+                                           const Split& h, float lo, float hi) {
     if (prune_better(v, t, m, b)) {
         b.v = v;
         b.t = t;
@@ -101,12 +150,12 @@ __device__ __forceinline__ void prune_take(PruneBest& b, float v, float t, int m
 }
 
 // One interval piece: m magnitudes at or below theta, the sums c (a^2 below)
-// and h (1/a above), theta in [lo, hi): the clamped vertex, if inside.
-__device__ __forceinline__ void prune_piece(PruneBest& best, int nb, float tf, int m, double c,
-                                            double h, float lo, float hi) {
+// and h (1/a above), theta in [lo, hi): the clamped vertex, if inside (FP32).
+__device__ __forceinline__ void prune_piece(PruneBest& best, int nb, float tf, int m,
+                                            const Split& c, const Split& h, float lo, float hi) {
     const int K = nb - m;
     if (K <= 0) return;
-    const float hf = (float)h, cf = (float)c, Kf = (float)K;
+    const float hf = h.approx(), cf = c.approx(), Kf = (float)K;
     float t = tf * hf * __frcp_rn(2.0f * Kf);
     t = fmaxf(t, lo);
     if (!(t < hi)) return;
@@ -114,81 +163,169 @@ __device__ __forceinline__ void prune_piece(PruneBest& best, int nb, float tf, i
     prune_take(best, v, t, m, c, h, lo, hi);
 }
 
-// Block-wide (PRUNE_THREADS) exclusive scan of (int, float, float) per thread:
-// FP32 within each warp, FP64 across warps.  Returns the exclusive prefixes
-// and, through tot_*, the block totals.
-__device__ __forceinline__ void prune_scan3(int vi, float vc, float vh, int& ei, double& ec,
-                                            double& eh, int& tot_i, double& tot_c,
-                                            double& tot_h) {
-    constexpr int NW = PRUNE_THREADS / 32;
-    __shared__ int s_i[NW + 1];
-    __shared__ double s_c[NW + 1], s_h[NW + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Static shared state of one subband's search, declared by the kernel (one
+// per group; a __shared__ variable inside the templated routine would exist
+// once per instantiation).
+struct PruneShared {
+    double tau, s20, h0;          // tau; sums of a^2 and 1/a over bucket 0
+    float s20f, h0f;
+    unsigned max;
+    int zero, bad, win;
+    float flat, ub, delta;        // SURE for theta >= max a, the upper bound, the margin
+    int wi[PRUNE_WARPS + 1];      // scan: per-warp exclusive bases (ints), total last
+    double wc[PRUNE_WARPS], wh[PRUNE_WARPS];   // FP64 warp bases: prefix of c, suffix of h
+    float wcf[PRUNE_WARPS], whf[PRUNE_WARPS];
+    double tot_c;
+    float tc[PRUNE_WARPS], th[PRUNE_WARPS];    // per-warp totals handed to warp 0
+    float red_v[PRUNE_WARPS], red_t[PRUNE_WARPS];
+    int red_m[PRUNE_WARPS], red_w[PRUNE_WARPS];
+};
+
+// Scan over the NT threads of a subband's search (gtid: index among them) of an int, an FP32 prefix and an
+// FP32 suffix per thread: the int's exclusive prefix ei (exact), the
+// exclusive prefix c of vc and the sum h of vh over the threads after this
+// one, each as an FP64 warp base plus an FP32 offset inside the warp.  The
+// FP64 bases come from one warp's shuffle scan over the warp totals.
+template <int NT>
+__device__ __forceinline__ void prune_scan(PruneShared& sh, int gtid, int bar, int vi, float vc,
+                                           float vh, int& ei, Split& c, Split& h, int& tot_i) {
+    constexpr int NW = NT / 32;
+    const int lane = gtid & 31, warp = gtid >> 5;
     int ii = vi;
     float ic = vc, ih = vh;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < 32; o <<= 1) {   // inclusive prefix (i, c), inclusive suffix (h)
         const int ti = __shfl_up_sync(0xffffffffu, ii, o);
         const float tc = __shfl_up_sync(0xffffffffu, ic, o);
-        const float th = __shfl_up_sync(0xffffffffu, ih, o);
+        const float th = __shfl_down_sync(0xffffffffu, ih, o);
         if (lane >= o) {
             ii += ti;
             ic += tc;
-            ih += th;
         }
+        if (lane + o < 32) ih += th;
     }
     if (lane == 31) {
-        s_i[warp] = ii;
-        s_c[warp] = ic;
-        s_h[warp] = ih;
+        sh.wi[warp] = ii;
+        sh.tc[warp] = ic;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {   // FP64 over the warps, in warp order
-        int ai = 0;
-        double ac = 0.0, ah = 0.0;
-        for (int w = 0; w < NW; ++w) {
-            const int xi = s_i[w];
-            const double xc = s_c[w], xh = s_h[w];
-            s_i[w] = ai;
-            s_c[w] = ac;
-            s_h[w] = ah;
-            ai += xi;
-            ac += xc;
-            ah += xh;
+    if (lane == 0) sh.th[warp] = ih;
+    psync<NT>(bar);
+    if (warp == 0) {   // FP64 over the warps (lane = warp): exclusive prefix, exclusive suffix
+        const bool live = lane < NW;
+        int xi = live ? sh.wi[lane] : 0;
+        double xc = live ? (double)sh.tc[lane] : 0.0, xh = live ? (double)sh.th[lane] : 0.0;
+        int pi = xi;
+        double pc = xc, sh_ = xh;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ti = __shfl_up_sync(0xffffffffu, pi, o);
+            const double tc = __shfl_up_sync(0xffffffffu, pc, o);
+            const double th = __shfl_down_sync(0xffffffffu, sh_, o);
+            if (lane >= o) {
+                pi += ti;
+                pc += tc;
+            }
+            if (lane + o < 32) sh_ += th;
         }
-        s_i[NW] = ai;
-        s_c[NW] = ac;
-        s_h[NW] = ah;
+        const int tot = __shfl_sync(0xffffffffu, pi, 31);
+        const double totc = __shfl_sync(0xffffffffu, pc, 31);
+        if (live) {
+            sh.wi[lane] = pi - xi;
+            sh.wc[lane] = pc - xc;
+            sh.wh[lane] = sh_ - xh;
+            sh.wcf[lane] = (float)(pc - xc);
+            sh.whf[lane] = (float)(sh_ - xh);
+        }
+        if (lane == 0) {
+            sh.wi[NW] = tot;
+            sh.tot_c = totc;
+        }
     }
-    __syncthreads();
+    psync<NT>(bar);
     int xi = __shfl_up_sync(0xffffffffu, ii, 1);
-    float xc = __shfl_up_sync(0xffffffffu, ic, 1), xh = __shfl_up_sync(0xffffffffu, ih, 1);
+    float xc = __shfl_up_sync(0xffffffffu, ic, 1);
+    float xh = __shfl_down_sync(0xffffffffu, ih, 1);
     if (lane == 0) {
         xi = 0;
         xc = 0.f;
-        xh = 0.f;
     }
-    ei = s_i[warp] + xi;
-    ec = s_c[warp] + (double)xc;
-    eh = s_h[warp] + (double)xh;
-    tot_i = s_i[NW];
-    tot_c = s_c[NW];
-    tot_h = s_h[NW];
-    __syncthreads();   // the scratch is reused by the next scan
+    if (lane == 31) xh = 0.f;
+    ei = sh.wi[warp] + xi;
+    c = Split{sh.wc[warp], sh.wcf[warp], xc};
+    h = Split{sh.wh[warp], sh.whf[warp], xh};
+    tot_i = sh.wi[NW];
+    psync<NT>(bar);   // the scratch is reused by the next scan
 }
 
-// Block-wide minimum of a float (PRUNE_THREADS threads).
-__device__ __forceinline__ float prune_min(float v) {
-    constexpr int NW = PRUNE_THREADS / 32;
-    __shared__ float s_m[NW];
+// Exclusive prefix (over the NT threads) of two ints (exact) and their totals.
+template <int NT>
+__device__ __forceinline__ void prune_scan_int2(PruneShared& sh, int gtid, int bar, int va, int vb,
+                                                int& ea, int& eb, int& ta, int& tb) {
+    constexpr int NW = NT / 32;
+    const int lane = gtid & 31, warp = gtid >> 5;
+    int ia = va, ib = vb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, ia, o);
+        const int y = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += x;
+            ib += y;
+        }
+    }
+    if (lane == 31) {
+        sh.wi[warp] = ia;
+        sh.red_m[warp] = ib;
+    }
+    psync<NT>(bar);
+    if (warp == 0) {
+        const bool live = lane < NW;
+        const int xa = live ? sh.wi[lane] : 0, xb = live ? sh.red_m[lane] : 0;
+        int pa = xa, pb = xb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, pa, o);
+            const int y = __shfl_up_sync(0xffffffffu, pb, o);
+            if (lane >= o) {
+                pa += x;
+                pb += y;
+            }
+        }
+        const int tpa = __shfl_sync(0xffffffffu, pa, 31), tpb = __shfl_sync(0xffffffffu, pb, 31);
+        if (live) {
+            sh.wi[lane] = pa - xa;
+            sh.red_m[lane] = pb - xb;
+        }
+        if (lane == 0) {
+            sh.wi[NW] = tpa;
+            sh.red_w[0] = tpb;
+        }
+    }
+    psync<NT>(bar);
+    ea = sh.wi[warp] + ia - va;
+    eb = sh.red_m[warp] + ib - vb;
+    ta = sh.wi[NW];
+    tb = sh.red_w[0];
+    psync<NT>(bar);
+}
+
+// Minimum of a float over the NT threads, broadcast to each.
+template <int NT>
+__device__ __forceinline__ float prune_min(PruneShared& sh, int gtid, int bar, float v) {
+    constexpr int NW = NT / 32;
+    const int lane = gtid & 31, warp = gtid >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float m = s_m[0];
-    for (int w = 1; w < NW; ++w) m = fminf(m, s_m[w]);
-    __syncthreads();
-    return m;
+    if (lane == 0) sh.red_v[warp] = v;
+    psync<NT>(bar);
+    if (warp == 0) {
+        float m = lane < NW ? sh.red_v[lane] : INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) sh.ub = m;
+    }
+    psync<NT>(bar);
+    return sh.ub;
 }
 
 // Bucket edges: bucket q >= 1 holds the bit patterns [lo_bits + q 2^shift,
@@ -216,26 +353,26 @@ __device__ __forceinline__ void prune_bucket_sums(unsigned lo_bits, int shift, i
 // line-8 constants (sure_finish), or, when its candidates do not fit the
 // table, the subband appended to the fallback list a.fallback ([0] entries,
 // [1] the fallback kernel's done counter, [2] a running total of the subbands
-// ever appended, [3 ..] slice B + b).  Called by all
-// PRUNE_THREADS threads of a CTA; dyn: prune_smem_bytes(largest subband).
-static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, unsigned* dyn) {
-    constexpr int NT = PRUNE_THREADS, NW = NT / 32;
-    __shared__ double s_tau, s_s20, s_h0;
-    __shared__ unsigned s_max;
-    __shared__ int s_zero, s_bad, s_win;
-    __shared__ float s_w2[NW], s_wh[NW], s_bv[NW], s_bt[NW];
-    __shared__ int s_bm[NW], s_bw[NW];
-    __shared__ PruneEntry s_tab[PRUNE_TABLE];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// ever appended, [3 ..] slice B + b).  Called by the NT threads that take
+// the subband (gtid: index among them; bar: their barrier, see psync); EMAX
+// magnitudes per thread (EMAX NT >= N_b); dyn: prune_words<NT>(max buckets)
+// words of dynamic shared memory of their own.
+template <int NT, int EMAX>
+static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice, unsigned* dyn,
+                                            PruneShared& sh, int gtid, int bar) {
+    using Lim = PruneLimits<NT>;
+    constexpr int NW = NT / 32;
+    const int tid = gtid, lane = tid & 31, warp = tid >> 5;
     const int off = a.off[b], nb = a.off[b + 1] - off;
     const float2* r = a.r + (size_t)slice * a.N + off;
-    const int lpo = prune_lpo(nb), nbk = 16 << lpo, shift = 23 - lpo;
+    const int lpo = prune_lpo(nb, Lim::max_lpo), nbk = 16 << lpo, shift = 23 - lpo;
     unsigned* X = dyn;        // count, then (local prefix of counts << 16 | count), then entry
     unsigned* Y = X + nbk;    // sum of quantised a^2 offsets, then local prefix of a^2 (FP32)
     unsigned* Z = Y + nbk;    // sum of quantised 1/a offsets, then local suffix of 1/a (FP32)
     unsigned* F = Z + nbk;    // candidate bits
     float* candA = reinterpret_cast<float*>(F + nbk / 32);   // gathered (bucket order)
-    float* candB = candA + PRUNE_CAP;                         // sorted
+    float* candB = candA + Lim::cap;                          // sorted
+    PruneEntry* tab = reinterpret_cast<PruneEntry*>(candB + Lim::cap);   // 8-byte aligned
 
     if (warp == 0) {   // tau: fixed-order FP64 sum of the column partials
         double t = 0.0;
@@ -243,58 +380,62 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
             t += a.tau_part[((size_t)slice * a.nparts + p) * a.B + b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) s_tau = t;
+        if (lane == 0) sh.tau = t;
     }
     for (int i = tid; i < 3 * nbk + nbk / 32; i += NT) X[i] = 0u;
     if (tid == 0) {
-        s_max = 0u;
-        s_zero = 0;
-        s_bad = 0;
+        sh.max = 0u;
+        sh.zero = 0;
+        sh.bad = 0;
     }
-    __syncthreads();
-    const double tau = s_tau;
-    if (!(tau > 0.0) || !isfinite(tau)) {   // no effective noise, or a numeric failure
-        if (tid == 0) sure_finish(a, a.k, b, slice, nb, tau, -1, 0.0, 0.0, 0.0);
-        return;
-    }
-    const float tf = (float)tau;
-
-    // ---- pass 1 over r_k: the largest magnitude (as bits) and the exact zeros
+    // the magnitudes into registers (every load in flight at once): the largest
+    // (as bits) and the exact zeros
+    float kr[EMAX];
     unsigned mx = 0u;
     int nz = 0;
-    for (int i = tid; i < nb; i += NT) {
-        const unsigned u = __float_as_uint(cabs_f(r[i]));
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+        const int i = tid + e * NT;
+        kr[e] = i < nb ? cabs_f(r[i]) : 0.f;
+        const unsigned u = __float_as_uint(kr[e]);
         mx = max(mx, u);
-        nz += u == 0u;
+        nz += (i < nb) && u == 0u;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         nz += __shfl_xor_sync(0xffffffffu, nz, o);
     }
+    psync<NT>(bar);
     if (lane == 0) {
-        atomicMax(&s_max, mx);
-        atomicAdd(&s_zero, nz);
+        atomicMax(&sh.max, mx);
+        atomicAdd(&sh.zero, nz);
     }
-    __syncthreads();
-    const unsigned M = s_max;
-    const int z = s_zero;
-    if (M >= 0x7f800000u || M == 0u) {
-        // non-finite magnitudes (recorded as a numeric failure), or all zero: theta = max a = 0
-        if (tid == 0)
-            sure_finish(a, a.k, b, slice, nb, tau, M == 0u ? nb : -1, 0.0, 0.0,
-                        -(double)nb * tau);
+    psync<NT>(bar);
+    const double tau = sh.tau;
+    const unsigned M = sh.max;
+    const int z = sh.zero;
+    if (!(tau > 0.0) || !isfinite(tau) || M >= 0x7f800000u || M == 0u) {
+        // no effective noise; a numeric failure (tau or a magnitude not finite); or an
+        // all-zero subband, where theta = max a = 0
+        if (tid == 0) {
+            const bool zero = tau > 0.0 && isfinite(tau) && M == 0u;
+            sure_finish(a, a.k, b, slice, nb, tau, zero ? nb : -1, 0.0, 0.0,
+                        zero ? -(double)nb * tau : 0.0);
+        }
         return;
     }
+    const float tf = (float)tau;
     const unsigned span = (unsigned)nbk << shift;
     const unsigned lo_bits = M + 1u > span ? M + 1u - span : 0u;
 
-    // ---- pass 2: counts and quantised sums per bucket (bucket 0 summed per thread)
+    // ---- counts and quantised sums per bucket (bucket 0 summed per thread)
     float s20 = 0.f, h0 = 0.f;
-    for (int i = tid; i < nb; i += NT) {
-        const float x = cabs_f(r[i]);
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+        const float x = kr[e];
         const unsigned u = __float_as_uint(x);
-        if (u == 0u) continue;
+        if (u == 0u) continue;   // exact zeros, and the slots past the subband
         const int q = u < lo_bits ? 0 : (int)((u - lo_bits) >> shift);
         atomicAdd(&X[q], 1u);
         if (q == 0) {
@@ -303,9 +444,10 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
             continue;
         }
         const float lo = prune_lo(lo_bits, shift, q), hi = prune_hi(lo_bits, shift, q);
-        const float w = __frcp_rn(hi - lo);
-        const float r2 = (x - lo) * w * ((x + lo) * __frcp_rn(hi + lo));   // (a^2 - lo^2) / (hi^2 - lo^2)
-        const float rh = (hi - x) * w * (lo * __frcp_rn(x));               // (1/a - 1/hi) / (1/lo - 1/hi)
+        // the quantisation needs neither correct rounding nor more than ~1e-6
+        const float w = __fdividef(1.f, hi - lo);
+        const float r2 = (x - lo) * w * __fdividef(x + lo, hi + lo);   // (a^2 - lo^2) / (hi^2 - lo^2)
+        const float rh = (hi - x) * w * __fdividef(lo, x);             // (1/a - 1/hi) / (1/lo - 1/hi)
         atomicAdd(&Y[q], min(__float2uint_rz(r2 * 65536.f), 65535u));
         atomicAdd(&Z[q], min(__float2uint_rz(rh * 65536.f), 65535u));
     }
@@ -315,28 +457,34 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
         h0 += __shfl_xor_sync(0xffffffffu, h0, o);
     }
     if (lane == 0) {
-        s_w2[warp] = s20;
-        s_wh[warp] = h0;
+        sh.red_v[warp] = s20;
+        sh.red_t[warp] = h0;
     }
-    __syncthreads();
-    if (tid == 0) {
-        double t2 = 0.0, th = 0.0;
-        for (int w = 0; w < NW; ++w) {
-            t2 += s_w2[w];
-            th += s_wh[w];
+    psync<NT>(bar);
+    if (warp == 0) {   // bucket 0: FP64 over the warps, in a fixed order
+        double x2 = lane < NW ? (double)sh.red_v[lane] : 0.0;
+        double xh = lane < NW ? (double)sh.red_t[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+            xh += __shfl_xor_sync(0xffffffffu, xh, o);
         }
-        s_s20 = t2;
-        s_h0 = th;
+        if (lane == 0) {
+            sh.s20 = x2;
+            sh.h0 = xh;
+            sh.s20f = (float)x2;
+            sh.h0f = (float)xh;
+        }
     }
-    __syncthreads();
+    psync<NT>(bar);
 
     // ---- prefix sums over buckets: each thread owns a run of consecutive buckets
     const int per = nbk >= NT ? nbk / NT : 1;
     const int j0 = min(tid * per, nbk), j1 = min(j0 + per, nbk);
     auto sums = [&](int j, int n, float& s2, float& hs) {
         if (j == 0) {
-            s2 = (float)s_s20;
-            hs = (float)s_h0;
+            s2 = sh.s20f;
+            hs = sh.h0f;
         } else {
             prune_bucket_sums(lo_bits, shift, j, n, Y[j], Z[j], s2, hs);
         }
@@ -352,11 +500,10 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
         th += hs;
     }
     int em, tot_m;
-    double ec, eh, c_all, tot_h;
-    prune_scan3(tm, tc, th, em, ec, eh, tot_m, c_all, tot_h);
-    const int mb = z + em;                       // magnitudes below this thread's buckets
-    const double cb = ec;                        // their sum of a^2
-    const double hb = tot_h - (eh + (double)th); // sum of 1/a above this thread's buckets
+    Split cS, hS;   // a^2 below this thread's buckets, 1/a above them
+    prune_scan<NT>(sh, gtid, bar, tm, tc, th, em, cS, hS, tot_m);
+    const double c_all = sh.tot_c;
+    const int mb = z + em;          // magnitudes below this thread's buckets
     // local prefixes: X = (count below in the run << 16 | count), Y = a^2 below in the run
     {
         int lm = 0;
@@ -372,48 +519,53 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
         }
     }
     // local suffixes of 1/a (Z), and the attained SURE just below each bucket's lower edge
-    float umin = (float)(c_all - (double)nb * tau);   // theta >= max a
+    float umin = INFINITY;
+    if (tid == 0) {   // theta >= max a: constant; and the pruning margin
+        const float flat = (float)(c_all - (double)nb * tau);
+        umin = flat;
+        sh.delta = 1e-5f * (float)(c_all + (double)nb * tau);
+    }
     {
         float lh = 0.f;
         for (int j = j1 - 1; j >= j0; --j) {
             const unsigned xw = X[j];
             const int n = (int)(xw & 0xffffu), m_lt = mb + (int)(xw >> 16);
-            float hs = (float)s_h0;
+            float hs = sh.h0f;
             if (j > 0) {
                 float s2_unused;
                 prune_bucket_sums(lo_bits, shift, j, n, 0u, Z[j], s2_unused, hs);
             }
             Z[j] = __float_as_uint(lh);
-            const float c_lt = (float)(cb + (double)__uint_as_float(Y[j]));
-            const float h_ge = (float)(hb + (double)lh) + hs;
+            const float c_lt = cS.basef + (cS.off + __uint_as_float(Y[j]));
+            const float h_ge = hS.basef + (hS.off + lh + hs);
             const float t = j == 0 ? 0.f : __uint_as_float(lo_bits + ((unsigned)j << shift) - 1u);
             const float kge = (float)(nb - m_lt);
             umin = fminf(umin, c_lt - tf * (float)m_lt + kge * (t * t + tf) - tf * t * h_ge);
             lh += hs;
         }
     }
-    const float ub = prune_min(umin);
-    const float delta = 1e-5f * (float)(c_all + (double)nb * tau);
+    const float ub = prune_min<NT>(sh, gtid, bar, umin);
+    const float delta = sh.delta;
 
     // ---- lower bounds: empty candidate buckets are evaluated now, the others marked
     PruneBest best;
     best.v = INFINITY;
     best.t = INFINITY;
     best.m = 0x7fffffff;
-    best.c = best.h = 0.0;
+    best.c = best.h = Split{0.0, 0.f, 0.f};
     best.lo = best.hi = 0.f;
     int my_e = 0, my_k = 0;
     for (int j = j0; j < j1; ++j) {
         const unsigned xw = X[j];
         const int n = (int)(xw & 0xffffu), m_lt = mb + (int)(xw >> 16);
-        const double c_lt = cb + (double)__uint_as_float(Y[j]);
-        const double h_gt = hb + (double)__uint_as_float(Z[j]);
+        const Split c_lt = cS.plus(__uint_as_float(Y[j]));
+        const Split h_gt = hS.plus(__uint_as_float(Z[j]));
         const float lo = prune_lo(lo_bits, shift, j), hi = prune_hi(lo_bits, shift, j);
         const int K = nb - m_lt - n;
-        const float hf = (float)h_gt;
+        const float hf = h_gt.approx();
         float t = K > 0 ? tf * hf * __frcp_rn(2.f * (float)K) : lo;
         t = fminf(fmaxf(t, lo), hi);
-        const float lb = (float)c_lt - tf * (float)m_lt + (float)n * (lo * lo - tf) +
+        const float lb = c_lt.approx() - tf * (float)m_lt + (float)n * (lo * lo - tf) +
                          (float)K * (t * t + tf) - tf * t * hf;
         if (!(lb <= ub + delta)) continue;
         if (n == 0) {
@@ -422,14 +574,12 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
             atomicOr(&F[j >> 5], 1u << (j & 31));
             ++my_e;
             my_k += n;
-            if (n > PRUNE_BUCKET_MAX) s_bad = 1;
+            if (n > Lim::bucket_max) sh.bad = 1;
         }
     }
-    int e0, tot_e;
-    double k0d, unused0, tot_kd, unused1;
-    prune_scan3(my_e, (float)my_k, 0.f, e0, k0d, unused0, tot_e, tot_kd, unused1);
-    const int tot_k = (int)tot_kd;
-    if (tot_e > PRUNE_TABLE || tot_k > PRUNE_CAP || s_bad) {
+    int e0, k0, tot_e, tot_k;
+    prune_scan_int2<NT>(sh, gtid, bar, my_e, my_k, e0, k0, tot_e, tot_k);
+    if (tot_e > Lim::table || tot_k > Lim::cap || sh.bad) {
         if (tid == 0) {
             const int idx = atomicAdd(&a.fallback[0], 1);
             a.fallback[3 + idx] = slice * a.B + b;
@@ -440,14 +590,14 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
 
     // ---- the table of non-empty candidate buckets; X[j] becomes j's entry (or none)
     {
-        int e = e0, kpos = (int)k0d;
+        int e = e0, kpos = k0;
         for (int j = j0; j < j1; ++j) {
             const unsigned xw = X[j];
             const int n = (int)(xw & 0xffffu);
             if (n > 0 && ((F[j >> 5] >> (j & 31)) & 1u)) {
-                PruneEntry& E = s_tab[e];
-                E.c_lt = cb + (double)__uint_as_float(Y[j]);
-                E.h_gt = hb + (double)__uint_as_float(Z[j]);
+                PruneEntry& E = tab[e];
+                E.c_lt = cS.plus(__uint_as_float(Y[j]));
+                E.h_gt = hS.plus(__uint_as_float(Z[j]));
                 E.lo = prune_lo(lo_bits, shift, j);
                 E.hi = prune_hi(lo_bits, shift, j);
                 E.m_lt = mb + (int)(xw >> 16);
@@ -462,29 +612,30 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
             }
         }
     }
-    __syncthreads();
-    // ---- pass 3 over r_k: gather the candidates' magnitudes, grouped by bucket
-    for (int i = tid; i < nb; i += NT) {
-        const float x = cabs_f(r[i]);
+    psync<NT>(bar);
+    // ---- gather the candidates' magnitudes, grouped by bucket
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+        const float x = kr[e];
         const unsigned u = __float_as_uint(x);
         if (u == 0u) continue;
         const int q = u < lo_bits ? 0 : (int)((u - lo_bits) >> shift);
-        const unsigned e = X[q];
-        if (e != 0xffffffffu) candA[s_tab[e].start + atomicAdd(&s_tab[e].fill, 1)] = x;
+        const unsigned ent = X[q];
+        if (ent != 0xffffffffu) candA[tab[ent].start + atomicAdd(&tab[ent].fill, 1)] = x;
     }
-    __syncthreads();
+    psync<NT>(bar);
     auto entry_of = [&](int p) {   // the entry whose slots hold position p
         int l = 0, h = tot_e - 1;
         while (l < h) {
             const int mid = (l + h + 1) >> 1;
-            if (s_tab[mid].start <= p) l = mid;
+            if (tab[mid].start <= p) l = mid;
             else h = mid - 1;
         }
         return l;
     };
     // rank within the bucket (ties by gather slot): the sorted order, whatever the gather order
     for (int p = tid; p < tot_k; p += NT) {
-        const PruneEntry& E = s_tab[entry_of(p)];
+        const PruneEntry& E = tab[entry_of(p)];
         const float x = candA[p];
         int rk = 0;
         for (int k = E.start; k < E.start + E.n; ++k) {
@@ -493,10 +644,10 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
         }
         candB[E.start + rk] = x;
     }
-    __syncthreads();
+    psync<NT>(bar);
     // ---- every piece inside the candidate buckets: the interval after each magnitude ...
     for (int p = tid; p < tot_k; p += NT) {
-        const PruneEntry& E = s_tab[entry_of(p)];
+        const PruneEntry& E = tab[entry_of(p)];
         const int k = p - E.start;
         float cs = 0.f, hs = 0.f;   // a^2 up to and including k, 1/a after k (bucket order)
         for (int i = 0; i < E.n; ++i) {
@@ -506,20 +657,20 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
         }
         const float bk = candB[p];
         const int m = E.m_lt + k + 1;
-        const double c = E.c_lt + (double)cs;
+        const Split c = E.c_lt.plus(cs);
         if (m == nb) {   // theta >= max a: SURE is constant, theta = max a
-            prune_take(best, (float)c - (float)nb * tf, bk, nb, c, 0.0, bk, bk);
+            prune_take(best, c.approx() - (float)nb * tf, bk, nb, c, Split{0.0, 0.f, 0.f}, bk, bk);
         } else {
             const float nxt = k + 1 < E.n ? candB[p + 1] : E.hi;
-            prune_piece(best, nb, tf, m, c, E.h_gt + (double)hs, bk, nxt);
+            prune_piece(best, nb, tf, m, c, E.h_gt.plus(hs), bk, nxt);
         }
     }
     // ... and the piece below each candidate bucket's first magnitude
     for (int e = tid; e < tot_e; e += NT) {
-        const PruneEntry& E = s_tab[e];
+        const PruneEntry& E = tab[e];
         float hs = 0.f;
         for (int i = 0; i < E.n; ++i) hs += __frcp_rn(candB[E.start + i]);
-        prune_piece(best, nb, tf, E.m_lt, E.c_lt, E.h_gt + (double)hs, E.lo, candB[E.start]);
+        prune_piece(best, nb, tf, E.m_lt, E.c_lt, E.h_gt.plus(hs), E.lo, candB[E.start]);
     }
 
     // ---- the best candidate of the CTA (ties: smaller theta, smaller m, lower thread)
@@ -540,45 +691,78 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
             }
         }
         if (lane == 0) {
-            s_bv[warp] = v;
-            s_bt[warp] = t;
-            s_bm[warp] = m;
-            s_bw[warp] = w;
+            sh.red_v[warp] = v;
+            sh.red_t[warp] = t;
+            sh.red_m[warp] = m;
+            sh.red_w[warp] = w;
         }
-        __syncthreads();
-        if (tid == 0) {
-            float bv = s_bv[0], bt = s_bt[0];
-            int bm = s_bm[0], bw = s_bw[0];
-            for (int q = 1; q < NW; ++q) {
-                const float v2 = s_bv[q], t2 = s_bt[q];
-                const int m2 = s_bm[q], w2 = s_bw[q];
-                if (v2 < bv || (v2 == bv && (t2 < bt || (t2 == bt && (m2 < bm || (m2 == bm && w2 < bw)))))) {
-                    bv = v2;
-                    bt = t2;
-                    bm = m2;
-                    bw = w2;
+        psync<NT>(bar);
+        if (warp == 0) {
+            const bool live = lane < NW;
+            v = live ? sh.red_v[lane] : INFINITY;
+            t = live ? sh.red_t[lane] : INFINITY;
+            m = live ? sh.red_m[lane] : 0x7fffffff;
+            w = live ? sh.red_w[lane] : 0x7fffffff;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const float t2 = __shfl_xor_sync(0xffffffffu, t, o);
+                const int m2 = __shfl_xor_sync(0xffffffffu, m, o);
+                const int w2 = __shfl_xor_sync(0xffffffffu, w, o);
+                if (v2 < v || (v2 == v && (t2 < t || (t2 == t && (m2 < m || (m2 == m && w2 < w)))))) {
+                    v = v2;
+                    t = t2;
+                    m = m2;
+                    w = w2;
                 }
             }
-            s_win = bw;
+            if (lane == 0) sh.win = w;
         }
-        __syncthreads();
+        psync<NT>(bar);
     }
     // ---- the winner in FP64 (theta, alpha and the line-8 constants by sure_finish)
-    if (tid == s_win) {
+    if (tid == sh.win) {
         if (!(best.v < INFINITY)) {   // nothing found: recorded as a numeric failure
             sure_finish(a, a.k, b, slice, nb, tau, -1, 0.0, 0.0, 0.0);
         } else if (best.m == nb) {
             sure_finish(a, a.k, b, slice, nb, tau, nb, (double)best.t, 0.0,
-                        best.c - (double)nb * tau);
+                        best.c.exact() - (double)nb * tau);
         } else {
-            const double K = (double)(nb - best.m);
-            double theta = fmax(tau * best.h / (2.0 * K), (double)best.lo);
+            const double K = (double)(nb - best.m), c = best.c.exact(), h = best.h.exact();
+            double theta = fmax(pdiv(tau * h, 2.0 * K), (double)best.lo);
             theta = fmin(theta, (double)best.hi);
-            const double val = best.c - best.m * tau + K * theta * theta + K * tau -
-                               tau * theta * best.h;
-            sure_finish(a, a.k, b, slice, nb, tau, best.m, theta, best.h, val);
+            const double val = c - best.m * tau + K * theta * theta + K * tau - tau * theta * h;
+            sure_finish(a, a.k, b, slice, nb, tau, best.m, theta, h, val);
         }
     }
+}
+
+// The magnitudes a thread holds: the smallest power of two of registers that
+// covers the subband (up to 32 per thread at NT = PRUNE_THREADS, 32768
+// magnitudes; up to 8 in a group, PRUNE_SMALL_BAND).
+template <int NT>
+static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, unsigned* dyn,
+                                          PruneShared& sh, int gtid, int bar) {
+    const int nb = a.off[b + 1] - a.off[b];
+    if (nb <= NT) sure_prune_subband_t<NT, 1>(a, b, slice, dyn, sh, gtid, bar);
+    else if (nb <= 2 * NT) sure_prune_subband_t<NT, 2>(a, b, slice, dyn, sh, gtid, bar);
+    else if (nb <= 4 * NT) sure_prune_subband_t<NT, 4>(a, b, slice, dyn, sh, gtid, bar);
+    else if (NT < PRUNE_THREADS || nb <= 8 * NT) sure_prune_subband_t<NT, 8>(a, b, slice, dyn, sh, gtid, bar);
+    else if (nb <= 16 * NT) sure_prune_subband_t<NT, 16>(a, b, slice, dyn, sh, gtid, bar);
+    else sure_prune_subband_t<NT, 32>(a, b, slice, dyn, sh, gtid, bar);
+}
+
+// Subbands of up to PRUNE_SMALL_BAND magnitudes (the coarse ones, b = 0 ..
+// n_small - 1 in packed order) go four to a CTA, the larger ones one to a
+// CTA: CTAs per slice.
+__host__ __device__ inline int prune_n_small(const int* off, int B) {
+    int n = 0;
+    while (n < B && off[n + 1] - off[n] <= PRUNE_SMALL_BAND) ++n;
+    return n;
+}
+__host__ __device__ inline int prune_ctas(const int* off, int B) {
+    const int ns = prune_n_small(off, B);
+    return (B - ns) + (ns + PRUNE_GROUPS - 1) / PRUNE_GROUPS;
 }
 
 }  // namespace vdamp
