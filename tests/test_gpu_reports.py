@@ -199,6 +199,10 @@ def test_precision_report():
     assert err["n (rel L2, vs BF16-storage oracle)"] < 2e-2
     assert err["f (rel L2, vs FP64)"] < 1e-2
 
+    rep["256x256 db4 s=4, 30 iterations, teacher forced"]["final NMSE, free running"] = (
+        "relaxed bound: within max(4 std, 0.02 dB) of 8 FP64 runs perturbed at 1e-6 per "
+        "iteration, not 0.01 dB of one run (the iteration amplifies FP32-level differences "
+        "about 1.5x per iteration; test_solve_free_running); 0.01 dB holds at 64x64")
     md = ["| result | largest error vs the FP64 oracle |", "|---|---|"]
     for sec, vals in rep.items():
         md.append(f"| **{sec}** | |")
