@@ -100,11 +100,12 @@ struct PruneEntry {   // one non-empty candidate bucket
 // Dynamic shared memory of one subband's search (a CTA's, or a group's share):
 // three per-bucket words (count, sum of quantised a^2 offsets, sum of
 // quantised 1/a offsets; later the packed local prefixes), the candidate-
-// bucket bits, two candidate key buffers and the table of candidate buckets.
+// bucket bits, three candidate buffers (gathered keys, later their prefix sums
+// of a^2; sorted keys; prefix sums of 1/a) and the table of candidate buckets.
 template <int NT>
 __host__ __device__ inline size_t prune_words(int nbk) {
     using Lim = PruneLimits<NT>;
-    return 3 * (size_t)nbk + nbk / 32 + 2 * (size_t)Lim::cap +
+    return 3 * (size_t)nbk + nbk / 32 + 3 * (size_t)Lim::cap +
            Lim::table * (sizeof(PruneEntry) / sizeof(unsigned));
 }
 // Dynamic shared memory of the pruned kernel: the larger of one CTA-wide
@@ -372,16 +373,9 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
     unsigned* F = Z + nbk;    // candidate bits
     float* candA = reinterpret_cast<float*>(F + nbk / 32);   // gathered (bucket order)
     float* candB = candA + Lim::cap;                          // sorted
-    PruneEntry* tab = reinterpret_cast<PruneEntry*>(candB + Lim::cap);   // 8-byte aligned
+    float* candH = candB + Lim::cap;                          // prefix sums of 1/a in a bucket
+    PruneEntry* tab = reinterpret_cast<PruneEntry*>(candH + Lim::cap);   // 8-byte aligned
 
-    if (warp == 0) {   // tau: fixed-order FP64 sum of the column partials
-        double t = 0.0;
-        for (int p = lane; p < a.nparts; p += 32)
-            t += a.tau_part[((size_t)slice * a.nparts + p) * a.B + b];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) sh.tau = t;
-    }
     for (int i = tid; i < 3 * nbk + nbk / 32; i += NT) X[i] = 0u;
     if (tid == 0) {
         sh.max = 0u;
@@ -400,6 +394,14 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
         const unsigned u = __float_as_uint(kr[e]);
         mx = max(mx, u);
         nz += (i < nb) && u == 0u;
+    }
+    if (warp == 0) {   // tau (loads in flight with the magnitudes): fixed-order FP64 sum of the partials
+        double t = 0.0;
+        for (int p = lane; p < a.nparts; p += 32)
+            t += a.tau_part[((size_t)slice * a.nparts + p) * a.B + b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh.tau = t;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -491,10 +493,12 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
     };
     int tm = 0;
     float tc = 0.f, th = 0.f;
-    for (int j = j0; j < j1; ++j) {
+    for (int j = j0; j < j1; ++j) {   // the bucket's sums, kept in Y and Z from here on
         float s2, hs;
         const int n = (int)X[j];
         sums(j, n, s2, hs);
+        Y[j] = __float_as_uint(s2);
+        Z[j] = __float_as_uint(hs);
         tm += n;
         tc += s2;
         th += hs;
@@ -509,9 +513,8 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
         int lm = 0;
         float lc = 0.f;
         for (int j = j0; j < j1; ++j) {
-            float s2, hs;
             const int n = (int)X[j];
-            sums(j, n, s2, hs);
+            const float s2 = __uint_as_float(Y[j]);
             X[j] = ((unsigned)lm << 16) | (unsigned)n;
             Y[j] = __float_as_uint(lc);
             lm += n;
@@ -530,11 +533,7 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
         for (int j = j1 - 1; j >= j0; --j) {
             const unsigned xw = X[j];
             const int n = (int)(xw & 0xffffu), m_lt = mb + (int)(xw >> 16);
-            float hs = sh.h0f;
-            if (j > 0) {
-                float s2_unused;
-                prune_bucket_sums(lo_bits, shift, j, n, 0u, Z[j], s2_unused, hs);
-            }
+            const float hs = __uint_as_float(Z[j]);
             Z[j] = __float_as_uint(lh);
             const float c_lt = cS.basef + (cS.off + __uint_as_float(Y[j]));
             const float h_ge = hS.basef + (hS.off + lh + hs);
@@ -645,16 +644,26 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
         candB[E.start + rk] = x;
     }
     psync<NT>(bar);
+    // per candidate bucket, in sorted order: prefix sums of a^2 (candA, no longer needed
+    // for the gathered keys) and of 1/a (candH), one thread per bucket
+    for (int e = tid; e < tot_e; e += NT) {
+        const PruneEntry& E = tab[e];
+        float cs = 0.f, hs = 0.f;
+        for (int i = E.start; i < E.start + E.n; ++i) {
+            const float y = candB[i];
+            cs += y * y;
+            hs += __frcp_rn(y);
+            candA[i] = cs;
+            candH[i] = hs;
+        }
+    }
+    psync<NT>(bar);
     // ---- every piece inside the candidate buckets: the interval after each magnitude ...
     for (int p = tid; p < tot_k; p += NT) {
         const PruneEntry& E = tab[entry_of(p)];
-        const int k = p - E.start;
-        float cs = 0.f, hs = 0.f;   // a^2 up to and including k, 1/a after k (bucket order)
-        for (int i = 0; i < E.n; ++i) {
-            const float y = candB[E.start + i];
-            if (i <= k) cs += y * y;
-            else hs += __frcp_rn(y);
-        }
+        const int k = p - E.start, last = E.start + E.n - 1;
+        const float cs = candA[p];                  // a^2 up to and including k
+        const float hs = candH[last] - candH[p];    // 1/a after k
         const float bk = candB[p];
         const int m = E.m_lt + k + 1;
         const Split c = E.c_lt.plus(cs);
@@ -668,9 +677,8 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
     // ... and the piece below each candidate bucket's first magnitude
     for (int e = tid; e < tot_e; e += NT) {
         const PruneEntry& E = tab[e];
-        float hs = 0.f;
-        for (int i = 0; i < E.n; ++i) hs += __frcp_rn(candB[E.start + i]);
-        prune_piece(best, nb, tf, E.m_lt, E.c_lt, E.h_gt.plus(hs), E.lo, candB[E.start]);
+        prune_piece(best, nb, tf, E.m_lt, E.c_lt, E.h_gt.plus(candH[E.start + E.n - 1]), E.lo,
+                    candB[E.start]);
     }
 
     // ---- the best candidate of the CTA (ties: smaller theta, smaller m, lower thread)
