@@ -223,6 +223,8 @@ struct vdamp_plan {
     double4_32a* bestrec = nullptr;
     unsigned* counter = nullptr;
     int* fallback = nullptr;           // [3 + max_batch B] subbands left to the full SURE sort
+    vdamp::KEntry* klist = nullptr;    // [max_batch][nx][ny] sampled entries of a solve, per column
+    int* kcnt = nullptr;               // [max_batch][nx] their counts
     float4* coef = nullptr;
     float* sigma_d = nullptr;
     int* status = nullptr;
@@ -259,7 +261,7 @@ static void plan_free(vdamp_plan* p) {
     void* bufs[] = {p->ey,       p->ex,      p->tw_y,    p->tw_x,    p->u,      p->kbuf,
                     p->ll0,      p->ll1,     p->rA,      p->rB,      p->tau_part, p->sorted,
                     p->partrec,  p->bestrec, p->counter, p->coef,    p->sigma_d, p->status,
-                    p->sure_val, p->fallback,
+                    p->sure_val, p->fallback, p->klist, p->kcnt,
                     p->st_y,     p->st_mask, p->st_p,    p->st_x,    p->st_r0,  p->st_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -429,6 +431,8 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(dalloc(&p->counter, MB * p->B, &acc));
     A(dalloc(&p->sure_val, MB * p->B, &acc));
     A(dalloc(&p->fallback, 3 + MB * p->B, &acc));
+    A(dalloc(&p->klist, MB * N, &acc));
+    A(dalloc(&p->kcnt, MB * (size_t)nx, &acc));
     A(dalloc(&p->coef, MB * p->B, &acc));
     A(dalloc(&p->sigma_d, MB, &acc));
     A(dalloc(&p->status, (size_t)2, &acc));
@@ -548,6 +552,9 @@ struct Ctx {
     cudaError_t err = cudaSuccess;
     bool timed = false;
     int ev_start = -1;
+    // the compacted k-space inputs of this solve (NULL: the column passes read y, mask, p)
+    const vdamp::KEntry* klist = nullptr;
+    const int* kcnt = nullptr;
     cudaEvent_t ev(int i) {
         while ((int)p->ev_pool.size() <= i) {
             cudaEvent_t e;
@@ -731,16 +738,32 @@ vdamp::ColArgs col_args(const vdamp_plan* p, int mode, const float2* in, float2*
 
 float inv_sqrt_n(const vdamp_plan* p) { return (float)(1.0 / std::sqrt((double)p->N)); }
 
+// The sampled entries of y, 1/p (and the mask) compacted per column, once per solve;
+// later column passes on this Ctx read the list instead of the dense inputs.
+void enq_kspace_list(Ctx& c, const float2* y, const uint8_t* mask, const float* density) {
+    vdamp_plan* p = c.p;
+    vdamp::ColArgs a = col_args(p, vdamp::COL_ITER, p->kbuf, p->kbuf, y, mask, density);
+    a.klist = p->klist;
+    a.kcnt = p->kcnt;
+    c.pre();
+    c.chk(vdamp::launch_kspace_list(a, c.batch, c.st), VDAMP_KERNEL_OTHER);
+    c.klist = p->klist;
+    c.kcnt = p->kcnt;
+}
+
 // k-space part of one iteration: from the image u (or zero) to u' = F^H P^-1 z
 void enq_kspace_iter(Ctx& c, bool u_zero, const float2* y, const uint8_t* mask,
                      const float* density) {
     vdamp_plan* p = c.p;
-    if (!u_zero)
+    if (!u_zero) {   // r~ = 0 (cold start): U = 0, the column pass needs no row transform
         c.pre();
         c.chk(vdamp::launch_fft_rows(p->u, p->kbuf, p->ny, p->nx, c.batch, p->axx, 0, 1.0f,
                                      p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+    }
     vdamp::ColArgs a = col_args(p, vdamp::COL_ITER, p->kbuf, p->kbuf, y, mask, density);
     a.u_zero = u_zero ? 1 : 0;
+    a.klist = c.klist;
+    a.kcnt = c.kcnt;
     c.pre();
     c.chk(vdamp::launch_col_pass(a, c.batch, c.st), VDAMP_KERNEL_COL_PASS);
     c.pre();
@@ -756,6 +779,8 @@ void enq_final(Ctx& c, const SrcSpec& src, const float2* y, const uint8_t* mask,
     c.chk(vdamp::launch_fft_rows(p->u, p->kbuf, p->ny, p->nx, c.batch, p->axx, 0, 1.0f, p->rpc,
                                  c.st), VDAMP_KERNEL_FFT_ROWS);
     vdamp::ColArgs a = col_args(p, vdamp::COL_FINAL, p->kbuf, p->kbuf, y, mask, nullptr);
+    a.klist = c.klist;
+    a.kcnt = c.kcnt;
     c.pre();
     c.chk(vdamp::launch_col_pass(a, c.batch, c.st), VDAMP_KERNEL_COL_PASS);
     c.pre();
@@ -841,6 +866,7 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
         c.err = cudaMemsetAsync(p->status, 0, sizeof(int), c.st);
     if (s.reset_status && c.err == cudaSuccess)
         c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
+    enq_kspace_list(c, s.y, s.mask, s.density);   // the column passes of this solve read only these
     float2* prev = p->rA;  // r_{k-1}
     float2* cur = p->rB;   // r_k
     for (int k = 0; k < s.iters; ++k) {

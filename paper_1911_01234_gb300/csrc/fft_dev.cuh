@@ -452,40 +452,69 @@ __device__ __forceinline__ void col_pass_block_t(const ColArgs& a, int mode, int
     float q[2 * VDAMP_MAX_LEVELS];  // this thread's column: sum over its rows of S_y,t(ky) v
 #pragma unroll
     for (int t = 0; t < 2 * VDAMP_MAX_LEVELS; ++t) q[t] = 0.f;
-    // chunks of 4 elements per thread: the mask, y and p loads of a chunk go out together
-    for (int base = tid; base < cnt; base += 4 * nthr) {
-        bool mv[4];
-        float2 yv[4];
-        float pv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * nthr;
-            if (idx < cnt) {
-                const size_t g = gidx(idx);
-                mv[u] = a.mask[g] != 0;
-                yv[u] = a.y[g];
-                pv[u] = mode == COL_ITER ? a.density[g] : 1.f;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * nthr;
-            if (idx >= cnt) continue;
-            const int i = idx / CB;
-            const float2 uu = U ? cscale(U[idx], a.scale_fwd) : make_float2(0.f, 0.f);
-            const bool m = mv[u];
+    if (a.klist) {
+        // compacted inputs: the unsampled entries are 0 (lines 3-4) or U (the return
+        // line), then each thread takes the listed entries of its own column
+        for (int idx = tid; idx < cnt; idx += nthr)
+            X[idx] = (mode == COL_FINAL) ? cscale(U[idx], a.scale_fwd) : make_float2(0.f, 0.f);
+        __syncthreads();
+        const int c = tid & (CB - 1), lanes = nthr / CB;
+        const size_t lb = ((size_t)slice * nparts + cblk) * CB + c;
+        const KEntry* el = a.klist + lb * ny;
+        const int ne = a.kcnt[lb];
+        for (int e = tid / CB; e < ne; e += lanes) {
+            const KEntry k = el[e];
+            const int idx = k.row * CB + c;
             if (mode == COL_FINAL) {
-                X[idx] = m ? yv[u] : uu;
+                X[idx] = k.y;
                 continue;
             }
-            const float2 z = m ? csub(yv[u], uu) : make_float2(0.f, 0.f);
-            const float w = m ? __frcp_rn(pv[u]) : 0.f;  // P^-1 on Omega (1/p rounded once), 0 elsewhere
+            const float2 uu = U ? cscale(U[idx], a.scale_fwd) : make_float2(0.f, 0.f);
+            const float2 z = csub(k.y, uu);
+            const float w = k.w;   // P^-1 (1/p rounded once)
             const float z2 = z.x * z.x + z.y * z.y;
             const float v = w * ((w - 1.0f) * z2 + sig2);
 #pragma unroll
             for (int t = 0; t < 2 * VDAMP_MAX_LEVELS; ++t)
-                if (t < nt) q[t] += eys[t * ny + i] * v;
+                if (t < nt) q[t] += eys[t * ny + k.row] * v;
             X[idx] = cscale(z, w);
+        }
+    } else {   // dense inputs
+        // chunks of 4 elements per thread: the mask, y and p loads of a chunk go out together
+        for (int base = tid; base < cnt; base += 4 * nthr) {
+            bool mv[4];
+            float2 yv[4];
+            float pv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * nthr;
+                if (idx < cnt) {
+                    const size_t g = gidx(idx);
+                    mv[u] = a.mask[g] != 0;
+                    yv[u] = a.y[g];
+                    pv[u] = mode == COL_ITER ? a.density[g] : 1.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * nthr;
+                if (idx >= cnt) continue;
+                const int i = idx / CB;
+                const float2 uu = U ? cscale(U[idx], a.scale_fwd) : make_float2(0.f, 0.f);
+                const bool m = mv[u];
+                if (mode == COL_FINAL) {
+                    X[idx] = m ? yv[u] : uu;
+                    continue;
+                }
+                const float2 z = m ? csub(yv[u], uu) : make_float2(0.f, 0.f);
+                const float w = m ? __frcp_rn(pv[u]) : 0.f;  // P^-1 on Omega (1/p rounded once), 0 elsewhere
+                const float z2 = z.x * z.x + z.y * z.y;
+                const float v = w * ((w - 1.0f) * z2 + sig2);
+#pragma unroll
+                for (int t = 0; t < 2 * VDAMP_MAX_LEVELS; ++t)
+                    if (t < nt) q[t] += eys[t * ny + i] * v;
+                X[idx] = cscale(z, w);
+            }
         }
     }
 

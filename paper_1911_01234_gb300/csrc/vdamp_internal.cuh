@@ -122,6 +122,14 @@ enum ColMode {
     COL_FINAL = 3   // U = F u; out = F^H-column (m y + (1-m) U)
 };
 
+// One sampled frequency of a column (the compacted k-space inputs of a solve):
+// its row, P^-1 = 1/p rounded once, and the measurement y.
+struct __align__(16) KEntry {
+    int row;
+    float w;
+    float2 y;
+};
+
 struct ColArgs {
     const float2* in;    // row-transformed data [batch][ny][nx] (ignored if u_zero)
     float2* out;         // [batch][ny][nx]
@@ -143,6 +151,10 @@ struct ColArgs {
     int ty[VDAMP_MAX_BANDS];
     int tx[VDAMP_MAX_BANDS];
     double* tau_part;    // [batch][nx / cb][B]
+    // the sampled entries, compacted once per solve (NULL: read y, mask, density densely):
+    // klist[slice][cblk][c][ny] (column c of block cblk, rows ascending), kcnt[slice][cblk][c]
+    const KEntry* klist;
+    const int* kcnt;
 };
 
 struct DwtArgs {   // one analysis level: image (H x W) -> four (H/2 x W/2) bands
@@ -233,6 +245,9 @@ cudaError_t launch_fft_rows(const float2* in, float2* out, int ny, int nx, int b
                             const FftAxis& ax, int inverse, float scale, int rows_per_cta,
                             cudaStream_t st);
 cudaError_t launch_col_pass(const ColArgs& a, int batch, cudaStream_t st);
+// Compacts the sampled entries of every column block (a.mask, a.density, a.y) into
+// a.klist / a.kcnt for the column passes of one solve.
+cudaError_t launch_kspace_list(const ColArgs& a, int batch, cudaStream_t st);
 size_t col_pass_smem(int ny, int cb, int ntypes);
 cudaError_t launch_dwt_level(const DwtArgs& a, int batch, cudaStream_t st);
 cudaError_t launch_idwt_level(const IdwtArgs& a, int batch, cudaStream_t st);
