@@ -22,24 +22,34 @@ __global__ void __launch_bounds__(SURE_THREADS) sure_search_kernel(const __grid_
 }
 
 // Many slices (max_parts == 1): the pruned exact search (sure_prune_dev.cuh),
-// one large subband or four small ones per CTA; subbands it cannot take go
-// to the fallback list.  Grid: (prune_ctas, batch).
+// one large subband, two medium or four small ones per CTA; subbands it cannot
+// take go to the fallback list.  Grid: (prune_ctas, batch), the finest first.
 __global__ void __launch_bounds__(PRUNE_THREADS, 1) sure_prune_kernel(const __grid_constant__ SureArgs a) {
     extern __shared__ unsigned sm_words[];
     __shared__ PruneShared sh[PRUNE_GROUPS];
     cudaGridDependencySynchronize();
     const int slice = blockIdx.y, item = blockIdx.x;
-    const int ns = prune_n_small(a.off, a.B), nbig = a.B - ns;
-    if (item < nbig) {   // a large subband, the finest first
+    const int ns = prune_n_small(a.off, a.B), nm = prune_n_med(a.off, a.B, ns);
+    const int nbig = a.B - ns - nm;
+    constexpr int per_med = PRUNE_THREADS / PRUNE_MED;
+    const int cmed = (nm + per_med - 1) / per_med;
+    if (item < nbig) {   // a large subband
         sure_prune_subband<PRUNE_THREADS>(a, a.B - 1 - item, slice, sm_words, sh[0], threadIdx.x, 0);
         return;
     }
-    const int g = threadIdx.x / PRUNE_GROUP;
-    const int b = (item - nbig) * PRUNE_GROUPS + g;
+    if (item < nbig + cmed) {   // two medium subbands
+        const int g = threadIdx.x / PRUNE_MED;
+        const int b = ns + (item - nbig) * per_med + g;
+        if (b < ns + nm)
+            sure_prune_subband<PRUNE_MED>(a, b, slice, sm_words + g * prune_words<PRUNE_MED>(), sh[g],
+                                          threadIdx.x % PRUNE_MED, 1 + g);
+        return;
+    }
+    const int g = threadIdx.x / PRUNE_GROUP;   // four small subbands
+    const int b = (item - nbig - cmed) * PRUNE_GROUPS + g;
     if (b < ns)
-        sure_prune_subband<PRUNE_GROUP>(
-            a, b, slice, sm_words + g * prune_words<PRUNE_GROUP>(16 << PruneLimits<PRUNE_GROUP>::max_lpo),
-            sh[g], threadIdx.x % PRUNE_GROUP, 1 + g);
+        sure_prune_subband<PRUNE_GROUP>(a, b, slice, sm_words + g * prune_words<PRUNE_GROUP>(), sh[g],
+                                        threadIdx.x % PRUNE_GROUP, 1 + g);
 }
 
 // The subbands on the fallback list, one after another per CTA (a fixed grid,
@@ -77,7 +87,7 @@ cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, int fallback
                         cudaStream_t st) {
     if (a.max_parts == 1) {
         cudaError_t e = launch_pdl(sure_prune_kernel, dim3(prune_ctas(a.off, a.B), batch),
-                                   dim3(PRUNE_THREADS), prune_smem_bytes(max_band), st, a);
+                                   dim3(PRUNE_THREADS), prune_smem_bytes(), st, a);
         if (e != cudaSuccess) return e;
         return launch_pdl(sure_fallback_kernel, dim3(fallback_ctas), dim3(SURE_THREADS),
                           sure_smem_bytes(max_band), st, a);
@@ -100,9 +110,9 @@ cudaError_t configure_sure(size_t smem_bytes) {
     e = cudaFuncSetAttribute(sure_fallback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes);
     if (e != cudaSuccess) return e;
-    // the most the pruned search ever takes (4096 buckets)
+    // the pruned search always takes its largest layout (one CTA-wide subband)
     e = cudaFuncSetAttribute(sure_prune_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)prune_smem_bytes(SURE_SMALL_BAND));
+                             (int)prune_smem_bytes());
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sure_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes);

@@ -24,10 +24,10 @@
 //   4. only buckets with LB_j <= UB + 1e-5 (sum a^2 + N_b tau) can hold the
 //      minimiser (the margin covers the FP32 rounding of the bounds): an
 //      empty one is a single quadratic piece, evaluated at once; the keys of
-//      the others (a few hundred of N_b) are gathered from the magnitudes each
-//      thread holds in registers (r_k is read once), ranked within their
-//      bucket, and every interval piece inside these buckets is evaluated as
-//      in the full search.
+//      the others (a few hundred of N_b) are gathered from the magnitudes,
+//      which stay in shared memory from the first step (r_k is read once),
+//      ranked within their bucket, and every interval piece inside these
+//      buckets is evaluated as in the full search.
 // A piece whose vertex lies beyond the bucket's upper edge is skipped: its
 // minimum over the interval lies in a higher bucket, where it is either
 // evaluated or bounded above UB.  Candidates are compared in FP32 (ties to
@@ -40,10 +40,11 @@
 // rounded once to FP32, and only the winning candidate forms base + offset in
 // FP64.
 //
-// A CTA of PRUNE_THREADS threads takes one large subband, or four small ones
-// (up to PRUNE_SMALL_BAND magnitudes), one per group of PRUNE_GROUP threads
-// with a named barrier of its own: the fixed cost of the search's phases is
-// shared by four coarse subbands.  A subband whose candidates exceed its
+// A CTA of PRUNE_THREADS threads takes one large subband, two medium ones (up
+// to PRUNE_MED_BAND magnitudes, a group of PRUNE_MED threads each) or four
+// small ones (up to PRUNE_SMALL_BAND magnitudes, PRUNE_GROUP threads each);
+// a group has a named barrier of its own, so the groups' barrier-separated
+// phases overlap and the fixed cost of a phase is shared.  A subband whose candidates exceed its
 // tables (PruneLimits: non-empty candidate buckets, candidate magnitudes,
 // magnitudes of one candidate bucket; heavy ties or degenerate data) is
 // appended to a device list, and sure_fallback_kernel solves it with the
@@ -59,15 +60,21 @@ namespace vdamp {
 #define PRUNE_GROUP 256          // threads of a group that takes one small subband
 #define PRUNE_GROUPS (PRUNE_THREADS / PRUNE_GROUP)
 #define PRUNE_SMALL_BAND (8 * PRUNE_GROUP)   // subbands up to 2048 magnitudes go to a group
+#define PRUNE_MED 512            // threads of a group that takes one medium subband
+#define PRUNE_MED_BAND (16 * PRUNE_MED)      // subbands up to 8192 magnitudes: two per CTA
+#define PRUNE_BIG_BAND 32768     // the largest subband of the pruned search
 
-// Limits per subband, for a whole CTA (NT = PRUNE_THREADS) and for a group:
-// log2 buckets per octave, candidate magnitudes, non-empty candidate buckets,
-// magnitudes of one candidate bucket.
+// Limits per subband, for a whole CTA (NT = PRUNE_THREADS), a medium group and a
+// small group: magnitudes held, log2 buckets per octave, candidate magnitudes,
+// non-empty candidate buckets, magnitudes of one candidate bucket.
 template <int NT> struct PruneLimits {
-    static constexpr int max_lpo = NT == PRUNE_THREADS ? 8 : 7;   // 4096 / 2048 buckets
-    static constexpr int cap = NT == PRUNE_THREADS ? 4096 : 1024;
-    static constexpr int table = NT == PRUNE_THREADS ? 512 : 128;
-    static constexpr int bucket_max = NT == PRUNE_THREADS ? 1024 : 256;
+    static constexpr bool big = NT == PRUNE_THREADS, med = NT == PRUNE_MED;
+    static constexpr int max_band = big ? PRUNE_BIG_BAND : (med ? PRUNE_MED_BAND : PRUNE_SMALL_BAND);
+    static constexpr int max_lpo = big ? 8 : 7;   // 4096 / 2048 buckets
+    static constexpr int cap = big || med ? 2048 : 1024;
+    static constexpr int table = big || med ? 256 : 128;
+    static constexpr int bucket_max = big ? 1024 : (med ? 512 : 256);
+    static constexpr int loads = NT >= PRUNE_MED ? 16 : 8;   // r_k loads in flight per thread
 };
 
 // log2 of the buckets per octave: about two buckets per magnitude, 16 .. 2^max_lpo.
@@ -98,27 +105,30 @@ struct PruneEntry {   // one non-empty candidate bucket
 };
 
 // Dynamic shared memory of one subband's search (a CTA's, or a group's share):
-// three per-bucket words (count, sum of quantised a^2 offsets, sum of
-// quantised 1/a offsets; later the packed local prefixes), the candidate-
-// bucket bits, three candidate buffers (gathered keys, later their prefix sums
-// of a^2; sorted keys; prefix sums of 1/a) and the table of candidate buckets.
+// the magnitudes, three per-bucket words (count, sum of quantised a^2
+// offsets, sum of quantised 1/a offsets; later the packed local prefixes),
+// the candidate-bucket bits, three candidate buffers (gathered keys, later
+// their prefix sums of a^2; sorted keys; prefix sums of 1/a) and the table of
+// candidate buckets.
 template <int NT>
-__host__ __device__ inline size_t prune_words(int nbk) {
+__host__ __device__ inline size_t prune_words() {
     using Lim = PruneLimits<NT>;
-    return 3 * (size_t)nbk + nbk / 32 + 3 * (size_t)Lim::cap +
+    constexpr size_t nbk = (size_t)16 << Lim::max_lpo;
+    return (size_t)Lim::max_band + 3 * nbk + nbk / 32 + 3 * (size_t)Lim::cap +
            Lim::table * (sizeof(PruneEntry) / sizeof(unsigned));
 }
-// Dynamic shared memory of the pruned kernel: the larger of one CTA-wide
-// search and four group searches.
-inline size_t prune_smem_bytes(int max_band) {
-    const size_t big = prune_words<PRUNE_THREADS>(16 << PruneLimits<PRUNE_THREADS>::max_lpo);
-    const size_t small = PRUNE_GROUPS * prune_words<PRUNE_GROUP>(16 << PruneLimits<PRUNE_GROUP>::max_lpo);
-    (void)max_band;
-    return (big > small ? big : small) * sizeof(unsigned);
+// Dynamic shared memory of the pruned kernel: the largest of one CTA-wide
+// search, two medium and four small group searches.
+inline size_t prune_smem_bytes() {
+    const size_t big = prune_words<PRUNE_THREADS>();
+    const size_t med = (PRUNE_THREADS / PRUNE_MED) * prune_words<PRUNE_MED>();
+    const size_t small = PRUNE_GROUPS * prune_words<PRUNE_GROUP>();
+    const size_t m = big > med ? big : med;
+    return (m > small ? m : small) * sizeof(unsigned);
 }
 
 // Barrier of the threads taking one subband: the whole CTA (barrier 0), or a
-// group's named barrier 1 .. PRUNE_GROUPS.
+// group's named barrier (1 + its index in the CTA).
 template <int NT>
 __device__ __forceinline__ void psync(int bar) {
     if (NT == PRUNE_THREADS) __syncthreads();
@@ -355,19 +365,28 @@ __device__ __forceinline__ void prune_bucket_sums(unsigned lo_bits, int shift, i
 // table, the subband appended to the fallback list a.fallback ([0] entries,
 // [1] the fallback kernel's done counter, [2] a running total of the subbands
 // ever appended, [3 ..] slice B + b).  Called by the NT threads that take
-// the subband (gtid: index among them; bar: their barrier, see psync); EMAX
-// magnitudes per thread (EMAX NT >= N_b); dyn: prune_words<NT>(max buckets)
-// words of dynamic shared memory of their own.
-template <int NT, int EMAX>
-static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice, unsigned* dyn,
-                                            PruneShared& sh, int gtid, int bar) {
+// the subband (gtid: index among them; bar: their barrier, see psync); N_b at
+// most PruneLimits<NT>::max_band; dyn: prune_words<NT>() words of dynamic
+// shared memory of their own.
+template <int NT>
+static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, unsigned* dyn,
+                                          PruneShared& sh, int gtid, int bar) {
     using Lim = PruneLimits<NT>;
     constexpr int NW = NT / 32;
     const int tid = gtid, lane = tid & 31, warp = tid >> 5;
     const int off = a.off[b], nb = a.off[b + 1] - off;
     const float2* r = a.r + (size_t)slice * a.N + off;
     const int lpo = prune_lpo(nb, Lim::max_lpo), nbk = 16 << lpo, shift = 23 - lpo;
-    unsigned* X = dyn;        // count, then (local prefix of counts << 16 | count), then entry
+    float* mag = reinterpret_cast<float*>(dyn);   // the magnitudes, in packed order
+    if (nb > Lim::max_band) {   // not a subband for this group size: the full sort takes it
+        if (tid == 0) {
+            const int idx = atomicAdd(&a.fallback[0], 1);
+            a.fallback[3 + idx] = slice * a.B + b;
+            atomicAdd(&a.fallback[2], 1);
+        }
+        return;
+    }
+    unsigned* X = dyn + Lim::max_band;   // count, then (local prefix of counts << 16 | count), then entry
     unsigned* Y = X + nbk;    // sum of quantised a^2 offsets, then local prefix of a^2 (FP32)
     unsigned* Z = Y + nbk;    // sum of quantised 1/a offsets, then local suffix of 1/a (FP32)
     unsigned* F = Z + nbk;    // candidate bits
@@ -382,18 +401,28 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
         sh.zero = 0;
         sh.bad = 0;
     }
-    // the magnitudes into registers (every load in flight at once): the largest
-    // (as bits) and the exact zeros
-    float kr[EMAX];
+    // the magnitudes into shared memory (Lim::loads loads in flight per thread):
+    // the largest (as bits) and the exact zeros
     unsigned mx = 0u;
     int nz = 0;
+    for (int i0 = tid; i0 < nb; i0 += Lim::loads * NT) {
+        float2 v[Lim::loads];
 #pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-        const int i = tid + e * NT;
-        kr[e] = i < nb ? cabs_f(r[i]) : 0.f;
-        const unsigned u = __float_as_uint(kr[e]);
-        mx = max(mx, u);
-        nz += (i < nb) && u == 0u;
+        for (int u = 0; u < Lim::loads; ++u) {
+            const int i = i0 + u * NT;
+            v[u] = i < nb ? r[i] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < Lim::loads; ++u) {
+            const int i = i0 + u * NT;
+            if (i < nb) {
+                const float x = cabs_f(v[u]);
+                mag[i] = x;
+                const unsigned bits = __float_as_uint(x);
+                mx = max(mx, bits);
+                nz += bits == 0u;
+            }
+        }
     }
     if (warp == 0) {   // tau (loads in flight with the magnitudes): fixed-order FP64 sum of the partials
         double t = 0.0;
@@ -433,11 +462,10 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
 
     // ---- counts and quantised sums per bucket (bucket 0 summed per thread)
     float s20 = 0.f, h0 = 0.f;
-#pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-        const float x = kr[e];
+    for (int i = tid; i < nb; i += NT) {
+        const float x = mag[i];
         const unsigned u = __float_as_uint(x);
-        if (u == 0u) continue;   // exact zeros, and the slots past the subband
+        if (u == 0u) continue;   // exact zeros
         const int q = u < lo_bits ? 0 : (int)((u - lo_bits) >> shift);
         atomicAdd(&X[q], 1u);
         if (q == 0) {
@@ -613,9 +641,8 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
     }
     psync<NT>(bar);
     // ---- gather the candidates' magnitudes, grouped by bucket
-#pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-        const float x = kr[e];
+    for (int i = tid; i < nb; i += NT) {
+        const float x = mag[i];
         const unsigned u = __float_as_uint(x);
         if (u == 0u) continue;
         const int q = u < lo_bits ? 0 : (int)((u - lo_bits) >> shift);
@@ -745,32 +772,24 @@ static __device__ void sure_prune_subband_t(const SureArgs& a, int b, int slice,
     }
 }
 
-// The magnitudes a thread holds: the smallest power of two of registers that
-// covers the subband (up to 32 per thread at NT = PRUNE_THREADS, 32768
-// magnitudes; up to 8 in a group, PRUNE_SMALL_BAND).
-template <int NT>
-static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, unsigned* dyn,
-                                          PruneShared& sh, int gtid, int bar) {
-    const int nb = a.off[b + 1] - a.off[b];
-    if (nb <= NT) sure_prune_subband_t<NT, 1>(a, b, slice, dyn, sh, gtid, bar);
-    else if (nb <= 2 * NT) sure_prune_subband_t<NT, 2>(a, b, slice, dyn, sh, gtid, bar);
-    else if (nb <= 4 * NT) sure_prune_subband_t<NT, 4>(a, b, slice, dyn, sh, gtid, bar);
-    else if (NT < PRUNE_THREADS || nb <= 8 * NT) sure_prune_subband_t<NT, 8>(a, b, slice, dyn, sh, gtid, bar);
-    else if (nb <= 16 * NT) sure_prune_subband_t<NT, 16>(a, b, slice, dyn, sh, gtid, bar);
-    else sure_prune_subband_t<NT, 32>(a, b, slice, dyn, sh, gtid, bar);
-}
-
 // Subbands of up to PRUNE_SMALL_BAND magnitudes (the coarse ones, b = 0 ..
-// n_small - 1 in packed order) go four to a CTA, the larger ones one to a
-// CTA: CTAs per slice.
+// n_small - 1 in packed order) go four to a CTA, the next ones up to
+// PRUNE_MED_BAND (b = n_small .. n_small + n_med - 1) two to a CTA, the
+// larger ones one to a CTA: CTAs per slice.
 __host__ __device__ inline int prune_n_small(const int* off, int B) {
     int n = 0;
     while (n < B && off[n + 1] - off[n] <= PRUNE_SMALL_BAND) ++n;
     return n;
 }
+__host__ __device__ inline int prune_n_med(const int* off, int B, int n_small) {
+    int n = n_small;
+    while (n < B && off[n + 1] - off[n] <= PRUNE_MED_BAND) ++n;
+    return n - n_small;
+}
 __host__ __device__ inline int prune_ctas(const int* off, int B) {
-    const int ns = prune_n_small(off, B);
-    return (B - ns) + (ns + PRUNE_GROUPS - 1) / PRUNE_GROUPS;
+    const int ns = prune_n_small(off, B), nm = prune_n_med(off, B, ns);
+    constexpr int per_med = PRUNE_THREADS / PRUNE_MED;
+    return (B - ns - nm) + (nm + per_med - 1) / per_med + (ns + PRUNE_GROUPS - 1) / PRUNE_GROUPS;
 }
 
 }  // namespace vdamp
