@@ -52,11 +52,14 @@ __device__ __forceinline__ void dwt_tile_t(const DwtArgs& a, const float2* in_ba
     const float2* in = in_base + (size_t)slice * a.in_stride;
     const int tid = threadIdx.x;
 
+    // a window row or column is wrapped once (a cheap test where the image is at
+    // least a window wide)
+    auto wr = [](int v, int n) { return n >= IT ? (v >= n ? v - n : v) : wrap(v, n); };
     batched_for<8, float2>(
         tid, IT * IT, blockDim.x,
         [&](int idx) {
             const int r = idx / IT, c = idx - r * IT;
-            return in[(size_t)wrap(2 * m0 + r, H) * W + wrap(2 * n0 + c, W)];
+            return in[(size_t)wr(2 * m0 + r, H) * W + wr(2 * n0 + c, W)];
         },
         [&](int idx, float2 v) { X[idx] = v; });
     __syncthreads();
@@ -140,26 +143,35 @@ __device__ __forceinline__ void idwt_tile_t(const IdwtArgs& a, float2* out, cons
     const bool ll_dense = !a.first;
     const int mode = src.mode;
 
-    batched_for<8, float2>(
-        tid, 4 * CTT, nthr,
-        [&](int idx) {
-            const int q = idx / CTT;
-            const int rem = idx - q * CTT;
-            const int r = rem / CT, c = rem - r * CT;
-            const int pos = wrap(ms + r, h) * w + wrap(ns + c, w);
-            if (q == 0 && ll_dense) return lls[pos];
-            if (mode == SRC_ZERO) return make_float2(0.f, 0.f);
-            const int o = q == 0 ? o0 : (q == 1 ? o1 : (q == 2 ? o2 : o3));
-            return rs[o + pos];
-        },
-        [&](int idx, float2 v) {
-            const int q = idx / CTT;
-            if (!(q == 0 && ll_dense)) {
-                const float4 k = q == 0 ? k0 : (q == 1 ? k1 : (q == 2 ? k2 : k3));
-                v = src_apply(mode, v, k);
+    // the four bands' CT x CT windows: each thread takes window positions e and
+    // e + nthr of every band, so eight loads go out together; a window row is
+    // wrapped once (a cheap test where the band is at least a window wide)
+    auto wr = [](int v, int n) { return n >= CT ? (v < 0 ? v + n : (v >= n ? v - n : v)) : wrap(v, n); };
+    const float2* base[4] = {ll_dense ? lls : rs + o0, rs + o1, rs + o2, rs + o3};
+    const float4 kq[4] = {k0, k1, k2, k3};
+    for (int e0 = tid; e0 < CTT; e0 += 2 * nthr) {
+        float2 v[2][4];
+        int pos[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int e = e0 + j * nthr;
+            const int r = e / CT, c = e - r * CT;
+            pos[j] = wr(ms + r, h) * w + wr(ns + c, w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool live = e < CTT && (mode != SRC_ZERO || (q == 0 && ll_dense));
+                v[j][q] = live ? base[q][pos[j]] : make_float2(0.f, 0.f);
             }
-            C[idx] = v;
-        });
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int e = e0 + j * nthr;
+            if (e >= CTT) continue;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                C[q * CTT + e] = (q == 0 && ll_dense) ? v[j][q] : src_apply(mode, v[j][q], kq[q]);
+        }
+    }
     __syncthreads();
     const float2* LL = C;
     const float2* HB = C + CTT;

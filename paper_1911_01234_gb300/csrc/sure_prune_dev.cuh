@@ -401,6 +401,14 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
         sh.zero = 0;
         sh.bad = 0;
     }
+    // tau: a fixed-order FP64 sum of the column blocks' partials; warp 0's first two
+    // partials per lane go out before the magnitudes
+    const double* tp = a.tau_part + (size_t)slice * a.nparts * a.B + b;
+    double t0 = 0.0, t1 = 0.0;
+    if (warp == 0) {
+        if (lane < a.nparts) t0 = tp[(size_t)lane * a.B];
+        if (lane + 32 < a.nparts) t1 = tp[(size_t)(lane + 32) * a.B];
+    }
     // the magnitudes into shared memory (Lim::loads loads in flight per thread):
     // the largest (as bits) and the exact zeros
     unsigned mx = 0u;
@@ -424,10 +432,10 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
             }
         }
     }
-    if (warp == 0) {   // tau (loads in flight with the magnitudes): fixed-order FP64 sum of the partials
-        double t = 0.0;
-        for (int p = lane; p < a.nparts; p += 32)
-            t += a.tau_part[((size_t)slice * a.nparts + p) * a.B + b];
+    if (warp == 0) {
+        double t = t0;
+        t += t1;
+        for (int p = lane + 64; p < a.nparts; p += 32) t += tp[(size_t)p * a.B];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) sh.tau = t;
@@ -647,7 +655,10 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
         if (u == 0u) continue;
         const int q = u < lo_bits ? 0 : (int)((u - lo_bits) >> shift);
         const unsigned ent = X[q];
-        if (ent != 0xffffffffu) candA[tab[ent].start + atomicAdd(&tab[ent].fill, 1)] = x;
+        if (ent < (unsigned)tot_e) {   // (an entry beyond the table is never written)
+            const int slot = tab[ent].start + atomicAdd(&tab[ent].fill, 1);
+            if (slot < tot_k) candA[slot] = x;
+        }
     }
     psync<NT>(bar);
     auto entry_of = [&](int p) {   // the entry whose slots hold position p

@@ -92,13 +92,18 @@ struct SrcSpec {
 
 // The coefficient a source forms from the stored value v of subband b, whose
 // denoiser parameters are c = coef[slice][b].
+// |r| > theta is tested on the squares and 1/|r| is one reciprocal square
+// root (a few ulp): both maps are continuous at |r| = theta, so a rounding-level
+// difference in the test moves the result only by rounding.
 __device__ __forceinline__ float2 src_apply(int mode, float2 v, float4 c) {
     if (mode == SRC_ZERO) return make_float2(0.f, 0.f);
     if (mode == SRC_EXPLICIT) return v;
-    float a = cabs_f(v);
-    if (mode == SRC_SOFT) return cscale_rn(v, a > c.x ? 1.f - c.x / a : 0.f);
+    const float a2 = __fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y));
+    const bool above = a2 > c.x * c.x;   // theta >= 0
+    const float inv = rsqrtf(a2);        // used only above theta, where a2 > 0
+    if (mode == SRC_SOFT) return cscale_rn(v, above ? 1.f - c.x * inv : 0.f);
     // (soft(r) - alpha r) / (1 - alpha) = r (1 - c1 / |r|) above theta, -c2 r below
-    return cscale_rn(v, a > c.x ? 1.f - c.y / a : -c.z);
+    return cscale_rn(v, above ? 1.f - c.y * inv : -c.z);
 }
 
 __device__ __forceinline__ float4 src_coef(const SrcSpec& s, int slice, int b) {

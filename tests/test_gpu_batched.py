@@ -344,3 +344,27 @@ def test_solve_batched_descriptors_equal_solve():
     with pytest.raises(vb.VdampError):
         vb.vdamp_solve_batched(plan.handle, [descs[1], bad])
     plan.close()
+
+
+def test_pruned_search_on_many_slices_equals_single_slices():
+    """The batched threshold search (one CTA per large subband, two medium or
+    four small ones per CTA, many waves of CTAs) must give each subband the
+    result it gets when its slice is solved alone: per slice every output equals
+    that of a one-slice solve, bit for bit, and no error is recorded."""
+    wl = synth.BATCH_320_DB4_5
+    n = 48   # 48 slices x 8 CTAs: several waves
+    prs = [synth.make_problem(wl, i) for i in range(n)]
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels, max_batch=n)
+    t = plan.tuning()
+    t["sure_parts"] = 1
+    plan.set_tuning(t)
+    y, m, p = _stack(prs, "y"), _stack(prs, "mask"), _stack(prs, "density")
+    sig = [q.sigma for q in prs]
+    out = plan.solve(y, m, p, sig, 4)
+    st, _ = vb.vdamp_device_status(plan.handle)
+    assert st == vb.VDAMP_OK
+    for i in (0, 17, n - 1):
+        one = plan.solve(y[i:i + 1], m[i:i + 1], p[i:i + 1], [sig[i]], 4)
+        for key in ("x_hat", "tau", "thr", "alpha"):
+            assert torch.equal(one[key][0], out[key][i]), (i, key)
+    plan.close()
