@@ -714,6 +714,7 @@ vdamp::ColArgs col_args(const vdamp_plan* p, int mode, const float2* in, float2*
     a.ny = p->ny;
     a.nx = p->nx;
     a.cb = p->cb;
+    a.plan_batch = p->max_batch;
     a.ax = p->axy;
     a.mode = mode;
     a.u_zero = 0;
@@ -758,7 +759,7 @@ void enq_kspace_iter(Ctx& c, bool u_zero, const float2* y, const uint8_t* mask,
     if (!u_zero) {   // r~ = 0 (cold start): U = 0, the column pass needs no row transform
         c.pre();
         c.chk(vdamp::launch_fft_rows(p->u, p->kbuf, p->ny, p->nx, c.batch, p->axx, 0, 1.0f,
-                                     p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+                                     p->rpc, p->max_batch, c.st), VDAMP_KERNEL_FFT_ROWS);
     }
     vdamp::ColArgs a = col_args(p, vdamp::COL_ITER, p->kbuf, p->kbuf, y, mask, density);
     a.u_zero = u_zero ? 1 : 0;
@@ -768,7 +769,7 @@ void enq_kspace_iter(Ctx& c, bool u_zero, const float2* y, const uint8_t* mask,
     c.chk(vdamp::launch_col_pass(a, c.batch, c.st), VDAMP_KERNEL_COL_PASS);
     c.pre();
     c.chk(vdamp::launch_fft_rows(p->kbuf, p->u, p->ny, p->nx, c.batch, p->axx, 1, inv_sqrt_n(p),
-                                 p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+                                 p->rpc, p->max_batch, c.st), VDAMP_KERNEL_FFT_ROWS);
 }
 
 // return line: x = u + F^H M^T (y - M F u) with u = Psi^H (src)
@@ -776,7 +777,7 @@ void enq_final(Ctx& c, const SrcSpec& src, const float2* y, const uint8_t* mask,
     vdamp_plan* p = c.p;
     enq_psi_h(c, src, p->u);
     c.pre();
-    c.chk(vdamp::launch_fft_rows(p->u, p->kbuf, p->ny, p->nx, c.batch, p->axx, 0, 1.0f, p->rpc,
+    c.chk(vdamp::launch_fft_rows(p->u, p->kbuf, p->ny, p->nx, c.batch, p->axx, 0, 1.0f, p->rpc, p->max_batch,
                                  c.st), VDAMP_KERNEL_FFT_ROWS);
     vdamp::ColArgs a = col_args(p, vdamp::COL_FINAL, p->kbuf, p->kbuf, y, mask, nullptr);
     a.klist = c.klist;
@@ -785,7 +786,7 @@ void enq_final(Ctx& c, const SrcSpec& src, const float2* y, const uint8_t* mask,
     c.chk(vdamp::launch_col_pass(a, c.batch, c.st), VDAMP_KERNEL_COL_PASS);
     c.pre();
     c.chk(vdamp::launch_fft_rows(p->kbuf, x, p->ny, p->nx, c.batch, p->axx, 1, inv_sqrt_n(p),
-                                 p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+                                 p->rpc, p->max_batch, c.st), VDAMP_KERNEL_FFT_ROWS);
 }
 
 void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* thr,
@@ -1392,7 +1393,7 @@ extern "C" vdamp_status vdamp_fft2(vdamp_plan* p, int batch, const float* in, fl
     c.timed = p->timing != 0;
     c.pre();
     c.chk(vdamp::launch_fft_rows((const float2*)in, (float2*)out, p->ny, p->nx, batch, p->axx,
-                                 inverse ? 1 : 0, 1.0f, p->rpc, c.st), VDAMP_KERNEL_FFT_ROWS);
+                                 inverse ? 1 : 0, 1.0f, p->rpc, p->max_batch, c.st), VDAMP_KERNEL_FFT_ROWS);
     vdamp::ColArgs a = col_args(p, inverse ? vdamp::COL_INV : vdamp::COL_FWD, (float2*)out,
                                 (float2*)out, nullptr, nullptr, nullptr);
     a.scale_inv = inv_sqrt_n(p);

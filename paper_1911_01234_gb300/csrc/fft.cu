@@ -16,10 +16,16 @@ __global__ void fft_rows_kernel(const float2* in, float2* out, int ny, int nx,
 
 cudaError_t launch_fft_rows(const float2* in, float2* out, int ny, int nx, int batch,
                             const FftAxis& ax, int inverse, float scale, int rpc,
-                            cudaStream_t st) {
+                            int plan_batch, cudaStream_t st) {
     dim3 grid((ny + rpc - 1) / rpc, batch);
-    int threads = rpc * nx / 4;
-    threads = threads < 64 ? 64 : (threads > 512 ? 512 : threads);
+    // a plan whose largest batch fills the GPU: one thread per butterfly of the
+    // axis plan's largest radix, so that its stages keep every lane busy (a
+    // smaller radix loops over the butterflies); a plan for few slices (latency-
+    // bound): more threads.  Decided by the plan, not by the call's batch, so
+    // that a slice gives the same bits in any batch.
+    const bool full = (long long)grid.x * plan_batch >= device_sms();
+    int threads = rpc * nx / (full ? max_radix(ax) : 4);
+    threads = threads < 32 ? 32 : (threads > 512 ? 512 : threads);
     threads = (threads + 31) / 32 * 32;
     size_t smem = 2 * (size_t)rpc * nx * sizeof(float2);
     if (inverse)

@@ -15,7 +15,9 @@ __global__ void __launch_bounds__(512, 2) col_pass_kernel(const __grid_constant_
 
 cudaError_t launch_col_pass(const ColArgs& a, int batch, cudaStream_t st) {
     dim3 grid(a.nx / a.cb, batch);
-    int threads = a.ny * a.cb / 4;
+    // threads per butterfly as in launch_fft_rows
+    const bool full = (long long)grid.x * (a.plan_batch > 0 ? a.plan_batch : batch) >= device_sms();
+    int threads = a.ny * a.cb / (full ? max_radix(a.ax) : 4);
     threads = threads < 64 ? 64 : (threads > 512 ? 512 : threads);
     threads = (threads + 31) / 32 * 32;
     // every thread keeps one column: blockDim must be a multiple of cb

@@ -288,10 +288,12 @@ __device__ __forceinline__ bool axis_has_plan(const FftAxis& ax) {
 }
 
 // fft_stage with the length N, the radix R and the sub-transform length NS
-// known at compile time (same butterflies, same order of operations).
-template <int R, bool INV, bool ROWS, int CB, int N, int NS>
+// known at compile time (same butterflies, same order of operations); SCALE:
+// the outputs are multiplied by `scale` as they are stored.
+template <int R, bool INV, bool ROWS, int CB, int N, int NS, bool SCALE = false>
 __device__ __forceinline__ void fft_stage_ct(const float2* __restrict__ src, float2* __restrict__ dst,
-                                             const float2* __restrict__ tw, int ntrans) {
+                                             const float2* __restrict__ tw, int ntrans,
+                                             float scale = 1.f) {
     constexpr int NB = N / R;
     constexpr int STEP = N / (NS * R);
     constexpr int ES = ROWS ? 1 : CB;
@@ -321,7 +323,60 @@ __device__ __forceinline__ void fft_stage_ct(const float2* __restrict__ src, flo
         Dft<R, INV>::run(v);
         const int d = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[tbase + (d + r * NS) * ES] = v[r];
+        for (int r = 0; r < R; ++r) dst[tbase + (d + r * NS) * ES] = SCALE ? cscale(v[r], scale) : v[r];
+    }
+}
+
+// Whole rows with the compiled plan (N, VAR) from stage S on: stage 0 reads the
+// rows from `src` (global memory), the stages between alternate between the
+// shared buffers s0 and s1, and the last stage stores the scaled result to
+// `gout` (global memory): two shared-memory passes fewer than loading,
+// transforming and storing, with the same arithmetic.
+template <int N, int VAR, int S, bool INV>
+__device__ __forceinline__ void fft_rows_io(const float2* src, float2* gout, float2* s0, float2* s1,
+                                            const float2* tw, int ntrans, float scale) {
+    constexpr RadixPlan P = radix_plan(N, VAR);
+    constexpr int R = P.r[S];
+    constexpr int NS = plan_prefix(P, S);
+    if constexpr (S + 1 == P.ns) {
+        fft_stage_ct<R, INV, true, 1, N, NS, true>(src, gout, tw, ntrans, scale);
+    } else {
+        fft_stage_ct<R, INV, true, 1, N, NS>(src, s0, tw, ntrans);
+        __syncthreads();
+        fft_rows_io<N, VAR, S + 1, INV>(s0, gout, s1, s0, tw, ntrans, scale);
+    }
+}
+
+// One stage of a compiled plan over the CB columns of a column block, with its
+// own element strides on the source and the destination side (CB in shared
+// memory, the image width in global memory): the first stage of the forward
+// column transform reads the block from global memory, the last stage of the
+// inverse one stores it there (scaled).  Same butterflies as fft_stage_ct.
+template <int R, bool INV, int CB, int N, int NS, bool SCALE>
+__device__ __forceinline__ void fft_stage_cols_io(const float2* __restrict__ src, int ses,
+                                                  float2* __restrict__ dst, int des,
+                                                  const float2* __restrict__ tw, float scale) {
+    constexpr int NB = N / R;
+    constexpr int STEP = N / (NS * R);
+    for (int idx = threadIdx.x; idx < NB * CB; idx += blockDim.x) {
+        const int t = idx & (CB - 1), j = idx / CB;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[t + (size_t)(j + r * NB) * ses];
+        const int k = j % NS;
+        if (NS > 1 && k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(&tw[r * k * STEP]);
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        Dft<R, INV>::run(v);
+        const int d = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            dst[t + (size_t)(d + r * NS) * des] = SCALE ? cscale(v[r], scale) : v[r];
     }
 }
 
@@ -339,6 +394,36 @@ __device__ __forceinline__ float2* fft_stages_ct(float2* src, float2* dst, const
         fft_stage_ct<R, INV, ROWS, CB, N, NS>(src, dst, tw, ntrans);
         __syncthreads();
         return fft_stages_ct<N, VAR, S + 1, INV, ROWS, CB>(dst, src, tw, ntrans);
+    }
+}
+
+// The forward column transform of a column block with the compiled plan (N,
+// VAR): stage 0 from global memory (gsrc, row stride gstride) into s0, the
+// others in shared memory; returns the buffer holding the result.
+template <int N, int VAR, int CB>
+__device__ __forceinline__ float2* col_fwd_io(const float2* gsrc, int gstride, float2* s0, float2* s1,
+                                              const float2* tw) {
+    constexpr RadixPlan P = radix_plan(N, VAR);
+    fft_stage_cols_io<P.r[0], false, CB, N, 1, false>(gsrc, gstride, s0, CB, tw, 1.f);
+    __syncthreads();
+    return fft_stages_ct<N, VAR, 1, false, false, CB>(s0, s1, tw, CB);
+}
+
+// The inverse column transform from shared memory (src, with `other` the
+// second buffer) whose last stage stores the scaled result to global memory
+// (gdst, row stride gstride).
+template <int N, int VAR, int S, int CB>
+__device__ __forceinline__ void col_inv_io(float2* src, float2* other, float2* gdst, int gstride,
+                                           const float2* tw, float scale) {
+    constexpr RadixPlan P = radix_plan(N, VAR);
+    constexpr int R = P.r[S];
+    constexpr int NS = plan_prefix(P, S);
+    if constexpr (S + 1 == P.ns) {
+        fft_stage_cols_io<R, true, CB, N, NS, true>(src, CB, gdst, gstride, tw, scale);
+    } else {
+        fft_stage_ct<R, true, false, CB, N, NS>(src, other, tw, CB);
+        __syncthreads();
+        col_inv_io<N, VAR, S + 1, CB>(other, src, gdst, gstride, tw, scale);
     }
 }
 
@@ -362,6 +447,10 @@ static __device__ void fft_rows_block(const float2* in, float2* out, int ny, int
     float2* Bf = sm + rows * nx;
     const size_t base = (size_t)slice * ny * nx + (size_t)row0 * nx;
     const int cnt = rows * nx;
+    if constexpr (N > 0) {   // compiled plans have at least two stages
+        fft_rows_io<N, VAR, 0, INV>(in + base, out + base, A, Bf, ax.tw, rows, scale);
+        return;
+    }
     batched_for<8, float2>(threadIdx.x, cnt, blockDim.x, [&](int i) { return in[base + i]; },
                            [&](int i, float2 v) { A[i] = v; });
     __syncthreads();
@@ -422,8 +511,15 @@ __device__ __forceinline__ void col_pass_block_t(const ColArgs& a, int mode, int
 
     // ---- forward column transform (or U = 0)
     float2* U = nullptr;
-    if (mode != COL_INV && u_zero) {
-        U = nullptr;
+    bool fwd_done = false;
+    if constexpr (N > 0) {   // compiled plan: the first stage reads the block from global memory
+        if ((mode == COL_ITER || mode == COL_FINAL) && !u_zero) {
+            U = col_fwd_io<N, VAR, CB>(a.in + sbase, nx, A, Bf, a.ax.tw);
+            fwd_done = true;
+        }
+    }
+    if (fwd_done || (mode != COL_INV && u_zero)) {
+        // U is set (or zero)
     } else {
         batched_for<8, float2>(tid, cnt, nthr, [&](int idx) { return a.in[gidx(idx)]; },
                                [&](int idx, float2 v) { A[idx] = v; });
@@ -554,6 +650,10 @@ __device__ __forceinline__ void col_pass_block_t(const ColArgs& a, int mode, int
 
     // ---- inverse column transform (line 4: F^H of P^-1 z, or the return line)
     float2* other = (X == A) ? Bf : A;
+    if constexpr (N > 0) {   // compiled plan: the last stage stores to global memory
+        col_inv_io<N, VAR, 0, CB>(X, other, a.out + sbase, nx, a.ax.tw, a.scale_inv);
+        return;
+    }
     float2* res = axis_stages<N, VAR, true, false, CB>(X, other, a.ax, CB, 0);
     for (int idx = tid; idx < cnt; idx += nthr) a.out[gidx(idx)] = cscale(res[idx], a.scale_inv);
 }

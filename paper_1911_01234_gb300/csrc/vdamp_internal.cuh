@@ -34,8 +34,10 @@ __device__ __forceinline__ float2 cscale_rn(float2 a, float s) {
     return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s));
 }
 
-// |v| computed the same way everywhere, so that the SURE keys and the
-// threshold tests in the transforms classify a coefficient identically.
+// |v| as the SURE searches key it (correctly rounded square root).  The
+// transforms' threshold tests (src_apply) compare squares instead: the maps
+// they apply are continuous at |v| = theta, so the two may disagree on a
+// coefficient only where the outcome differs by rounding.
 __device__ __forceinline__ float cabs_f(float2 v) {
     return sqrtf(__fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)));
 }
@@ -74,6 +76,26 @@ struct FftAxis {
     int radix[VDAMP_MAX_STAGES];
     const float2* tw;  // device, tw[k] = exp(-2 pi i k / n)
 };
+
+// SMs of the current device (read once per process).
+inline int device_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            sms = n;
+        else
+            return 1;
+    }
+    return sms;
+}
+
+inline int max_radix(const FftAxis& ax) {
+    int r = 2;
+    for (int s = 0; s < ax.nstages; ++s) r = ax.radix[s] > r ? ax.radix[s] : r;
+    return r;
+}
 
 // How a transform forms the coefficient it reads from a packed array.
 enum SrcMode {
@@ -139,6 +161,7 @@ struct ColArgs {
     const float2* in;    // row-transformed data [batch][ny][nx] (ignored if u_zero)
     float2* out;         // [batch][ny][nx]
     int ny, nx, cb;      // cb = columns per CTA
+    int plan_batch;      // the plan's largest batch (sets the launch's threads; 0: the call's)
     FftAxis ax;          // along y
     int mode;
     int u_zero;          // 1: the image is zero, skip the forward transform
@@ -248,7 +271,7 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 // All return cudaGetLastError() after the launch.
 cudaError_t launch_fft_rows(const float2* in, float2* out, int ny, int nx, int batch,
                             const FftAxis& ax, int inverse, float scale, int rows_per_cta,
-                            cudaStream_t st);
+                            int plan_batch, cudaStream_t st);
 cudaError_t launch_col_pass(const ColArgs& a, int batch, cudaStream_t st);
 // Compacts the sampled entries of every column block (a.mask, a.density, a.y) into
 // a.klist / a.kcnt for the column passes of one solve.
