@@ -133,7 +133,10 @@ int vdamp_last_launch_count(const vdamp_plan* plan);
  *            1 = radix 4 only, 2 = radix 8 with the radices 3 and 5 first
  *   [6] 1: the scales s .. 2 of Psi (and of Psi^H) in one launch, one
  *       thread-block cluster per slice, scale 1 in its own launch, while
- *       batch x cluster size <= the SM count; 0: one launch per scale
+ *       batch x cluster size <= the SM count; 2: any batch, the coarse
+ *       scales (from the first whose synthesis output is at most 128 x 128)
+ *       in one launch, a cluster of up to 4 CTAs per slice, the finer
+ *       scales in their own launches; 0: one launch per scale
  *   [7] parts per subband of the SURE threshold search (Algorithm 1 lines
  *       6-7): 1 = one CTA per subband bounds SURE per bucket of magnitudes,
  *       sorts only the candidate buckets and searches them (subbands with

@@ -203,7 +203,8 @@ struct vdamp_plan {
     size_t smem_col = 0, smem_rows = 0, smem_dwt = 0;  // attributes raised for the tuner's choices
     int radix_var[2] = {0, 0};         // radix plan variant along y, x
     int wcluster = 0;                  // CTAs of the one-launch wavelet cluster (0: unavailable)
-    int use_wcluster = 0;              // tuning: all scales in one cluster launch (small batches)
+    int use_wcluster = 0;              // tuning: coarse scales in one cluster launch (1: small
+                                       // batches, scales s..2; 2: any batch, scales s..coarse_lo)
     int sure_parts = 0;                // tuning: SURE parts per subband (0: by batch size)
     int num_sms = 152;
     float* ey = nullptr;
@@ -595,12 +596,31 @@ SrcSpec make_src(const vdamp_plan* p, int mode, const float2* r) {
     return s;
 }
 
-// The cluster path for the coarse scales s .. 2 (scale 1 keeps its own wide
-// launch): while one cluster per slice leaves SMs free and there are >= 2 scales.
-bool wavelet_cluster(const Ctx& c) {
+// The first scale of the many-slice cluster path: the smallest j >= 2 whose
+// synthesis output is at most 128 x 128 (levels + 1: none).
+int coarse_lo(const vdamp_plan* p) {
+    for (int j = 2; j <= p->levels; ++j)
+        if ((p->ny >> (j - 1)) <= 128 && (p->nx >> (j - 1)) <= 128) return j;
+    return p->levels + 1;
+}
+
+// The cluster path for the coarse scales (the finer ones keep their own wide
+// launches): tuning 1, while one cluster of wcluster CTAs per slice leaves SMs
+// free: scales s .. 2; tuning 2, any batch: clusters of up to 4 CTAs per slice
+// for the scales s .. coarse_lo.  Returns the cluster size (0: per-scale
+// launches) and sets *lo.
+int wavelet_cluster(const Ctx& c, int* lo) {
     const vdamp_plan* p = c.p;
-    return p->wcluster > 0 && p->use_wcluster && p->levels >= 2 &&
-           c.batch * p->wcluster <= p->num_sms;
+    if (p->wcluster <= 0 || p->levels < 2) return 0;
+    if (p->use_wcluster == 1 && c.batch * p->wcluster <= p->num_sms) {
+        *lo = 2;
+        return p->wcluster;
+    }
+    if (p->use_wcluster == 2 && coarse_lo(p) <= p->levels) {
+        *lo = coarse_lo(p);
+        return std::min(4, p->wcluster);
+    }
+    return 0;
 }
 
 // x = Psi^H (src), levels s .. 1
@@ -608,12 +628,14 @@ void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
     vdamp_plan* p = c.p;
     const int s = p->levels;
     const float2* ll_in = nullptr;
-    const bool cl = wavelet_cluster(c);
+    int lo = 2;
+    const int C = wavelet_cluster(c, &lo);
+    const bool cl = C > 0;
     vdamp::WaveletArgs w;
     if (cl) {
         memset(&w, 0, sizeof(w));
         w.levels = s;
-        w.lo = 2;
+        w.lo = lo;
     }
     for (int j = s; j >= 1; --j) {
         vdamp::IdwtArgs a;
@@ -638,12 +660,12 @@ void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
         a.f = p->filt;
         a.to = p->idwt_to;
         ll_in = a.out;
-        if (cl && j >= 2) {
-            a.to = 32;   // one tile pass per CTA and scale up to 128x128 outputs
+        if (cl && j >= lo) {
+            a.to = 32;   // one tile pass per CTA and scale up to 128x128 outputs (16 CTAs)
             w.idwt[j - 1] = a;
-            if (j == 2) {   // the coarse scales in one cluster launch
+            if (j == lo) {   // the coarse scales in one cluster launch
                 c.pre();
-                c.chk(vdamp::launch_psi_h_cluster(w, c.batch, p->wcluster, p->smem_dwt, c.st),
+                c.chk(vdamp::launch_psi_h_cluster(w, c.batch, C, p->smem_dwt, c.st),
                       VDAMP_KERNEL_IDWT);
             }
             continue;
@@ -659,12 +681,14 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
     const int s = p->levels;
     const float2* in = img;
     size_t in_stride = p->N;
-    const bool cl = wavelet_cluster(c);
+    int lo = 2;
+    const int C = wavelet_cluster(c, &lo);
+    const bool cl = C > 0;
     vdamp::WaveletArgs w;
     if (cl) {
         memset(&w, 0, sizeof(w));
         w.levels = s;
-        w.lo = 2;
+        w.lo = lo;
     }
     for (int j = 1; j <= s; ++j) {
         vdamp::DwtArgs a;
@@ -691,7 +715,7 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
         a.to = p->dwt_to;
         in = a.ll_out;
         in_stride = p->N / 4;
-        if (cl && j >= 2) {
+        if (cl && j >= lo) {
             w.dwt[j - 1] = a;
             continue;
         }
@@ -700,7 +724,7 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
     }
     if (cl) {   // the coarse scales in one cluster launch
         c.pre();
-        c.chk(vdamp::launch_psi_cluster(w, c.batch, p->wcluster, p->smem_dwt, c.st),
+        c.chk(vdamp::launch_psi_cluster(w, c.batch, C, p->smem_dwt, c.st),
               VDAMP_KERNEL_DWT);
     }
 }
@@ -1450,7 +1474,8 @@ bool tuning_valid(const vdamp_plan* p, const int* t) {
     if (rpc < 1 || rpc > 8 || 2 * (size_t)rpc * p->nx * sizeof(float2) > p->smem_rows) return false;
     if (ito != 16 && ito != 32 && ito != 64) return false;
     if (dto != 16 && dto != 32) return false;
-    if (t[6] != 0 && t[6] != 1) return false;
+    if (t[6] != 0 && t[6] != 1 && t[6] != 2) return false;
+    if (t[6] == 2 && coarse_lo(p) > p->levels) return false;
     if (t[7] != 0 && t[7] != 1 && t[7] != 2 && t[7] != 4 && t[7] != SURE_MAX_PARTS) return false;
     if ((int)(p->N / 4) > SURE_SMALL_BAND && t[7] != 0 && t[7] < SURE_MIN_PARTS_BIG) return false;
     if (vdamp::idwt_tile_smem(ito, p->filt.L) > p->smem_dwt ||
@@ -1611,7 +1636,7 @@ extern "C" vdamp_status vdamp_plan_autotune(vdamp_plan* p, int batch, int trials
     // wavelet cluster, SURE parts)
     static const int choices[VDAMP_TUNING_LEN][4] = {{2, 4, 8, 16}, {1, 2, 4, 8}, {16, 32, 64, 0},
                                                      {16, 32, 0, 0}, {0, 1, 2, -1}, {0, 1, 2, -1},
-                                                     {0, 1, -1, -1}, {0, 1, 2, 4}};
+                                                     {0, 1, 2, -1}, {0, 1, 2, 4}};
     int best[VDAMP_TUNING_LEN];
     get_tuning(p, best);
     float best_ms = 0.f;

@@ -70,17 +70,17 @@ namespace vdamp {
 template <int NT> struct PruneLimits {
     static constexpr bool big = NT == PRUNE_THREADS, med = NT == PRUNE_MED;
     static constexpr int max_band = big ? PRUNE_BIG_BAND : (med ? PRUNE_MED_BAND : PRUNE_SMALL_BAND);
-    static constexpr int max_lpo = big ? 8 : 7;   // 4096 / 2048 buckets
+    static constexpr int max_lpo = big ? 8 : (med ? 7 : 6);   // 4096 / 2048 / 1024 buckets
     static constexpr int cap = big || med ? 2048 : 1024;
     static constexpr int table = big || med ? 256 : 128;
     static constexpr int bucket_max = big ? 1024 : (med ? 512 : 256);
     static constexpr int loads = NT >= PRUNE_MED ? 16 : 8;   // r_k loads in flight per thread
 };
 
-// log2 of the buckets per octave: about two buckets per magnitude, 16 .. 2^max_lpo.
+// log2 of the buckets per octave: about one bucket per magnitude, 16 .. 2^max_lpo.
 __host__ __device__ inline int prune_lpo(int nb, int max_lpo) {
     int l = 4;
-    while (l < max_lpo && (16 << l) < 2 * nb) ++l;
+    while (l < max_lpo && (16 << l) < nb) ++l;
     return l;
 }
 
