@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "VDAMP_OK", 1: "VDAMP_EINVAL", 2: "VDAMP_ENOMEM", 3: "VDAMP_E
                 4: "VDAMP_ENUMERIC", 5: "VDAMP_ETIMEOUT"}
 VDAMP_HAAR, VDAMP_DB4 = 1, 4
 WAVELETS = {"haar": VDAMP_HAAR, "db4": VDAMP_DB4}
-VDAMP_OPT_GRAPH, VDAMP_OPT_KERNEL_TIMING, VDAMP_OPT_FUSED = 1, 2, 3
+VDAMP_OPT_GRAPH, VDAMP_OPT_KERNEL_TIMING, VDAMP_OPT_FUSED, VDAMP_OPT_OVERLAP = 1, 2, 3, 4
 KERNEL_KINDS = ["idwt", "fft_rows", "col_pass", "dwt", "sure", "other", "fused"]
 
 

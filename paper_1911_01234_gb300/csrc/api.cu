@@ -1,9 +1,11 @@
 // C ABI of the VDAMP library: plans, table setup and the launch sequence of
 // Algorithm 1.  See include/vdamp.h for the contract of every entry point.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -241,6 +243,9 @@ struct vdamp_plan {
     int use_graph = 1;
     int timing = 0;
     int use_fused = 0;
+    int overlap = 1;       // the finest subbands' threshold search on a side stream (split path)
+    cudaStream_t side = nullptr;              // that side stream, and its fork / join events
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int fused_ok = 0;      // the device can hold the cluster
     int fused_C = 0, fused_cb = 0, fused_rpc = 0, fused_idwt_to = 0, fused_dwt_to = 0;
     size_t fused_smem = 0;
@@ -267,6 +272,9 @@ static void plan_free(vdamp_plan* p) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->side) cudaStreamDestroy(p->side);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     delete p;
 }
 
@@ -466,6 +474,9 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(cudaMemset(p->counter, 0, MB * p->B * sizeof(unsigned)));  // each search returns it to 0
     A(cudaMemset(p->fallback, 0, 3 * sizeof(int)));               // each fallback launch empties it
     A(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    A(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    A(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    A(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     // shared-memory attributes large enough for every tile choice the tuner may make
     p->smem_col = vdamp::col_pass_smem(ny, cb, nt);
     for (int c2 = 2; c2 <= 16; c2 *= 2) {
@@ -537,6 +548,13 @@ extern "C" vdamp_status vdamp_plan_set_option(vdamp_plan* p, int option, int val
     }
     if (option == VDAMP_OPT_FUSED) {
         p->use_fused = value ? 1 : 0;
+        return VDAMP_OK;
+    }
+    if (option == VDAMP_OPT_OVERLAP) {
+        p->overlap = value ? 1 : 0;
+        for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);  // they hold the old structure
+        p->graphs.clear();
+        purge_group_graphs(p);
         return VDAMP_OK;
     }
     return fail(VDAMP_EINVAL, "vdamp_plan_set_option: unknown option");
@@ -623,8 +641,10 @@ int wavelet_cluster(const Ctx& c, int* lo) {
     return 0;
 }
 
-// x = Psi^H (src), levels s .. 1
-void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
+// x = Psi^H (src), levels s .. 1; before_finest (if set) runs before scale 1 is
+// enqueued (scale 1 reads the finest subbands)
+void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img,
+               const std::function<void()>& before_finest = nullptr) {
     vdamp_plan* p = c.p;
     const int s = p->levels;
     const float2* ll_in = nullptr;
@@ -670,13 +690,16 @@ void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img) {
             }
             continue;
         }
+        if (j == 1 && before_finest) before_finest();
         c.pre();
         c.chk(vdamp::launch_idwt_level(a, c.batch, c.st), VDAMP_KERNEL_IDWT);
     }
 }
 
-// packed = Psi img + src (levels 1 .. s)
-void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
+// packed = Psi img + src (levels 1 .. s); after_finest (if set) runs once scale 1
+// (the finest subbands) is enqueued
+void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src,
+             const std::function<void()>& after_finest = nullptr) {
     vdamp_plan* p = c.p;
     const int s = p->levels;
     const float2* in = img;
@@ -721,6 +744,7 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src) {
         }
         c.pre();
         c.chk(vdamp::launch_dwt_level(a, c.batch, c.st), VDAMP_KERNEL_DWT);
+        if (j == 1 && after_finest) after_finest();
     }
     if (cl) {   // the coarse scales in one cluster launch
         c.pre();
@@ -813,8 +837,25 @@ void enq_final(Ctx& c, const SrcSpec& src, const float2* y, const uint8_t* mask,
                                  p->rpc, p->max_batch, c.st), VDAMP_KERNEL_FFT_ROWS);
 }
 
+// CTAs per subband of the threshold search (1: the pruned search)
+int sure_max_parts(const Ctx& c) {
+    const vdamp_plan* p = c.p;
+    // Split big subbands over several CTAs only while the split grid fits in one wave
+    // (each part rereads its whole subband: past one wave one CTA per subband is
+    // faster), unless the tuning fixes the number of parts.
+    int split = 0;
+    for (int b = 0; b < p->B; ++b)
+        split += vdamp::sure_parts(p->off[b + 1] - p->off[b], SURE_MAX_PARTS);
+    int mp = p->sure_parts ? p->sure_parts : ((c.batch * split > p->num_sms) ? 1 : SURE_MAX_PARTS);
+    // a finest subband above what one CTA holds is always split (SURE_MIN_PARTS_BIG or more)
+    if ((int)(p->N / 4) > SURE_SMALL_BAND && mp < SURE_MIN_PARTS_BIG) mp = SURE_MAX_PARTS;
+    return mp;
+}
+
+// Lines 5-7 for the subbands b_top, b_top - 1, ..., b_top - nb + 1 (default: all;
+// subsets only on the split path, max_parts > 1).
 void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* thr,
-              double* alpha) {
+              double* alpha, int b_top = -1, int nb = -1) {
     vdamp_plan* p = c.p;
     vdamp::SureArgs a;
     a.r = r;
@@ -836,17 +877,9 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     a.counter = p->counter;
     a.sure_out = p->sure_val;
     a.fallback = p->fallback;
-    // Split big subbands over several CTAs only while the split grid fits in one wave
-    // (each part rereads its whole subband: past one wave one CTA per subband is
-    // faster), unless the tuning fixes the number of parts.
-    int split = 0;
-    for (int b = 0; b < p->B; ++b)
-        split += vdamp::sure_parts(p->off[b + 1] - p->off[b], SURE_MAX_PARTS);
-    a.max_parts = p->sure_parts ? p->sure_parts
-                                : ((c.batch * split > p->num_sms) ? 1 : SURE_MAX_PARTS);
-    // a finest subband above what one CTA holds is always split (SURE_MIN_PARTS_BIG or more)
-    if ((int)(p->N / 4) > SURE_SMALL_BAND && a.max_parts < SURE_MIN_PARTS_BIG)
-        a.max_parts = SURE_MAX_PARTS;
+    a.max_parts = sure_max_parts(c);
+    a.b_top = b_top < 0 ? p->B - 1 : b_top;
+    a.nb_launch = nb < 0 ? p->B : nb;
     c.pre();
     // the pruned search and its fallback when every subband is one part, else sort and search
     c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), std::max(p->num_sms, 1), c.st),
@@ -892,6 +925,19 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
     if (s.reset_status && c.err == cudaSuccess)
         c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
     enq_kspace_list(c, s.y, s.mask, s.density);   // the column passes of this solve read only these
+    // On the split threshold path the finest subbands' search (lines 5-7 for the
+    // three subbands of scale 1, the costliest) runs on a side stream from the moment
+    // scale 1 of Psi has produced them, beside the coarser scales of Psi, their
+    // search and the coarser scales of the next Psi^H; the next scale 1 of Psi^H
+    // (which reads the finest subbands) waits for it.  Same kernels and arguments,
+    // so the same results.
+    const bool ov = p->overlap && !c.timed && p->levels >= 2 && p->B > 3 && sure_max_parts(c) > 1;
+    bool pending = false;   // a finest-subband search is in flight on the side stream
+    auto join = [&]() {
+        if (!pending) return;
+        if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(c.st, p->ev_join, 0);
+        pending = false;
+    };
     float2* prev = p->rA;  // r_{k-1}
     float2* cur = p->rB;   // r_k
     for (int k = 0; k < s.iters; ++k) {
@@ -903,17 +949,36 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
         } else {
             src = make_src(p, vdamp::SRC_LINE8, prev);
         }
-        if (!zero) enq_psi_h(c, src, p->u);            // Psi^H r~_k        (line 3)
+        if (!zero) enq_psi_h(c, src, p->u, join);       // Psi^H r~_k        (line 3)
+        join();
         enq_kspace_iter(c, zero, s.y, s.mask, s.density);  // z, tau parts, F^H P^-1 z (3-5)
-        enq_psi(c, p->u, cur, src);                     // r_k = r~_k + Psi u' (line 4)
-        enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha);  // tau, theta, alpha (5-7)
-        if (s.x_hat_iters)
+        if (ov) {
+            auto fork = [&]() {   // the finest subbands of r_k are written
+                if (c.err == cudaSuccess) c.err = cudaEventRecord(p->ev_fork, c.st);
+                if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+                Ctx side{p, c.batch, p->side};
+                enq_sure(side, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1, 3);
+                c.launches += side.launches;
+                if (c.err == cudaSuccess) c.err = side.err;
+                if (c.err == cudaSuccess) c.err = cudaEventRecord(p->ev_join, p->side);
+                pending = true;
+            };
+            enq_psi(c, p->u, cur, src, fork);            // r_k = r~_k + Psi u' (line 4)
+            enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 4, p->B - 3);  // coarse
+        } else {
+            enq_psi(c, p->u, cur, src);                  // r_k = r~_k + Psi u' (line 4)
+            enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha);  // tau, theta, alpha (5-7)
+        }
+        if (s.x_hat_iters) {
+            join();
             enq_final(c, make_src(p, vdamp::SRC_SOFT, cur), s.y, s.mask,
                       s.x_hat_iters + (size_t)k * c.batch * p->N);
+        }
         float2* t = prev;
         prev = cur;
         cur = t;
     }
+    join();
     enq_final(c, make_src(p, vdamp::SRC_SOFT, prev), s.y, s.mask, s.x_hat);  // return line
     if (s.r_tilde_out) enq_line8(c, prev, s.r_tilde_out);                      // line 8
 }

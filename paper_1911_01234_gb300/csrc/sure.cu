@@ -12,13 +12,13 @@ __global__ void __launch_bounds__(SURE_THREADS) sure_sort_kernel(const __grid_co
     extern __shared__ float sm_keys[];
     cudaGridDependencySynchronize();
     // the finest (largest) subbands first: the long CTAs start in the first wave
-    sure_sort_part(a, a.r, blockIdx.x, a.B - 1 - (int)blockIdx.y, blockIdx.z, sm_keys);
+    sure_sort_part(a, a.r, blockIdx.x, a.b_top - (int)blockIdx.y, blockIdx.z, sm_keys);
 }
 
 __global__ void __launch_bounds__(SURE_THREADS) sure_search_kernel(const __grid_constant__ SureArgs a) {
     extern __shared__ float sm_keys[];
     cudaGridDependencySynchronize();
-    sure_search_part(a, a.k, blockIdx.x, a.B - 1 - (int)blockIdx.y, blockIdx.z, sm_keys);
+    sure_search_part(a, a.k, blockIdx.x, a.b_top - (int)blockIdx.y, blockIdx.z, sm_keys);
 }
 
 // Many slices (max_parts == 1): the pruned exact search (sure_prune_dev.cuh),
@@ -92,10 +92,11 @@ cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, int fallback
         return launch_pdl(sure_fallback_kernel, dim3(fallback_ctas), dim3(SURE_THREADS),
                           sure_smem_bytes(max_band), st, a);
     }
-    cudaError_t e = launch_pdl(sure_sort_kernel, dim3(a.max_parts, a.B, batch),
+    // subbands b_top, b_top - 1, ..., b_top - nb_launch + 1 (the finest first)
+    cudaError_t e = launch_pdl(sure_sort_kernel, dim3(a.max_parts, a.nb_launch, batch),
                                dim3(SURE_THREADS), sure_split_smem_bytes(max_band), st, a);
     if (e != cudaSuccess) return e;
-    return launch_pdl(sure_search_kernel, dim3(a.max_parts, a.B, batch), dim3(SURE_THREADS),
+    return launch_pdl(sure_search_kernel, dim3(a.max_parts, a.nb_launch, batch), dim3(SURE_THREADS),
                       sure_split_search_smem_bytes(max_band), st, a);
 }
 

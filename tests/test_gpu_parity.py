@@ -318,6 +318,28 @@ def test_graph_and_direct_launches_agree():
     plan.close()
 
 
+@pytest.mark.parametrize("wl", [synth.PLAIN_64_HAAR3, synth.PLAIN_256_DB4_4], ids=lambda w: w.name[:16])
+def test_overlapped_threshold_search_is_bit_identical(wl):
+    """The finest subbands' threshold search on the plan's side stream (the split
+    path of a lone slice) gives the same bits as the one-stream order, in a
+    graph and in direct launches, with the per-iteration outputs too."""
+    pr = synth.make_problem(wl)
+    plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
+    y, m, p = _problem_on_device(pr)
+    outs = []
+    for overlap, graph in ((1, 1), (0, 1), (1, 0)):
+        vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_OVERLAP, overlap)
+        vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_GRAPH, graph)
+        outs.append(plan.solve(y, m, p, [pr.sigma], 8, want_iters=True))
+    torch.cuda.synchronize()
+    st, _ = vb.vdamp_device_status(plan.handle)
+    assert st == vb.VDAMP_OK
+    for o in outs[1:]:
+        for key in ("x_hat", "tau", "thr", "alpha", "x_hat_iters"):
+            assert torch.equal(outs[0][key], o[key]), key
+    plan.close()
+
+
 def test_batch_matches_single_slices():
     wl = synth.PLAIN_64_HAAR3
     probs = [synth.make_problem(wl, i) for i in range(3)]
