@@ -99,11 +99,12 @@ size_t vdamp_workspace_bytes(const vdamp_plan* plan);
  *     which a thread-block cluster iterates each slice (when the device can
  *     hold such a cluster); 0 runs one kernel per step of the iteration.
  *     Both give the same results up to the order of the tau partial sums.
- *   VDAMP_OPT_OVERLAP (default 1): when the threshold search splits subbands
- *     over several CTAs (few slices), search the three finest subbands on a
- *     second stream of the plan while the coarser scales of Psi, their search
- *     and the coarser scales of the next Psi^H run; 0 keeps one stream.  The
- *     same kernels with the same arguments: identical results. */
+ *   VDAMP_OPT_OVERLAP (default 1): in vdamp_solve (and the batched and
+ *     grouped solves), search the three finest subbands on a second stream of
+ *     the plan while the coarser scales of Psi, their search and the coarser
+ *     scales of the next Psi^H run (with the split search, and with the pruned
+ *     one when the finest subbands are its one-CTA subbands); 0 keeps one
+ *     stream.  The same kernels with the same arguments: identical results. */
 enum { VDAMP_OPT_GRAPH = 1, VDAMP_OPT_KERNEL_TIMING = 2, VDAMP_OPT_FUSED = 3, VDAMP_OPT_OVERLAP = 4 };
 vdamp_status vdamp_plan_set_option(vdamp_plan* plan, int option, int value);
 

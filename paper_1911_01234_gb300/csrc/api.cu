@@ -14,7 +14,7 @@
 #include "dwt_dev.cuh"
 #include "fft_dev.cuh"
 #include "fused.cuh"
-#include "sure_dev.cuh"
+#include "sure_prune_dev.cuh"   // (includes sure_dev.cuh)
 
 using vdamp::FftAxis;
 using vdamp::Filt;
@@ -226,6 +226,7 @@ struct vdamp_plan {
     double4_32a* bestrec = nullptr;
     unsigned* counter = nullptr;
     int* fallback = nullptr;           // [3 + max_batch B] subbands left to the full SURE sort
+    int* fallback2 = nullptr;          // the same for the search on the side stream
     vdamp::KEntry* klist = nullptr;    // [max_batch][nx][ny] sampled entries of a solve, per column
     int* kcnt = nullptr;               // [max_batch][nx] their counts
     float4* coef = nullptr;
@@ -267,7 +268,7 @@ static void plan_free(vdamp_plan* p) {
     void* bufs[] = {p->ey,       p->ex,      p->tw_y,    p->tw_x,    p->u,      p->kbuf,
                     p->ll0,      p->ll1,     p->rA,      p->rB,      p->tau_part, p->sorted,
                     p->partrec,  p->bestrec, p->counter, p->coef,    p->sigma_d, p->status,
-                    p->sure_val, p->fallback, p->klist, p->kcnt,
+                    p->sure_val, p->fallback, p->fallback2, p->klist, p->kcnt,
                     p->st_y,     p->st_mask, p->st_p,    p->st_x,    p->st_r0,  p->st_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -440,6 +441,7 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(dalloc(&p->counter, MB * p->B, &acc));
     A(dalloc(&p->sure_val, MB * p->B, &acc));
     A(dalloc(&p->fallback, 3 + MB * p->B, &acc));
+    A(dalloc(&p->fallback2, 3 + MB * p->B, &acc));
     A(dalloc(&p->klist, MB * N, &acc));
     A(dalloc(&p->kcnt, MB * (size_t)nx, &acc));
     A(dalloc(&p->coef, MB * p->B, &acc));
@@ -472,7 +474,8 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(cudaMemcpy(p->tw_x, twx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice));
     A(cudaMemset(p->status, 0, 2 * sizeof(int)));
     A(cudaMemset(p->counter, 0, MB * p->B * sizeof(unsigned)));  // each search returns it to 0
-    A(cudaMemset(p->fallback, 0, 3 * sizeof(int)));               // each fallback launch empties it
+    A(cudaMemset(p->fallback, 0, 3 * sizeof(int)));
+    A(cudaMemset(p->fallback2, 0, 3 * sizeof(int)));               // each fallback launch empties it
     A(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     A(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     A(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
@@ -852,10 +855,18 @@ int sure_max_parts(const Ctx& c) {
     return mp;
 }
 
-// Lines 5-7 for the subbands b_top, b_top - 1, ..., b_top - nb + 1 (default: all;
-// subsets only on the split path, max_parts > 1).
+// Large subbands of the pruned search (one CTA each; the finest ones).
+int prune_big(const vdamp_plan* p) {
+    const int ns = vdamp::prune_n_small(p->off, p->B);
+    return p->B - ns - vdamp::prune_n_med(p->off, p->B, ns);
+}
+
+// Lines 5-7 for the subbands b_top, b_top - 1, ..., b_top - nb + 1 (default: all).
+// On the pruned path a subset is either the large subbands (b_top = B - 1,
+// nb = prune_big) or all the others.  fallback: the pruned search's list (NULL:
+// the plan's first one).
 void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* thr,
-              double* alpha, int b_top = -1, int nb = -1) {
+              double* alpha, int b_top = -1, int nb = -1, int* fallback = nullptr) {
     vdamp_plan* p = c.p;
     vdamp::SureArgs a;
     a.r = r;
@@ -876,10 +887,22 @@ void enq_sure(Ctx& c, const float2* r, int iters, int k, double* tau, double* th
     a.bestrec = p->bestrec;
     a.counter = p->counter;
     a.sure_out = p->sure_val;
-    a.fallback = p->fallback;
+    a.fallback = fallback ? fallback : p->fallback;
     a.max_parts = sure_max_parts(c);
     a.b_top = b_top < 0 ? p->B - 1 : b_top;
     a.nb_launch = nb < 0 ? p->B : nb;
+    a.item0 = 0;
+    if (a.max_parts == 1) {   // the pruned search: a range of work items
+        const int ctas = vdamp::prune_ctas(p->off, p->B), big = prune_big(p);
+        if (nb < 0) {
+            a.nb_launch = ctas;
+        } else if (a.b_top == p->B - 1) {
+            a.nb_launch = big;
+        } else {
+            a.item0 = big;
+            a.nb_launch = ctas - big;
+        }
+    }
     c.pre();
     // the pruned search and its fallback when every subband is one part, else sort and search
     c.chk(vdamp::launch_sure(a, c.batch, (int)(p->N / 4), std::max(p->num_sms, 1), c.st),
@@ -925,13 +948,15 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
     if (s.reset_status && c.err == cudaSuccess)
         c.err = cudaMemsetAsync(p->status + 1, 0x7f, sizeof(int), c.st);
     enq_kspace_list(c, s.y, s.mask, s.density);   // the column passes of this solve read only these
-    // On the split threshold path the finest subbands' search (lines 5-7 for the
-    // three subbands of scale 1, the costliest) runs on a side stream from the moment
-    // scale 1 of Psi has produced them, beside the coarser scales of Psi, their
-    // search and the coarser scales of the next Psi^H; the next scale 1 of Psi^H
-    // (which reads the finest subbands) waits for it.  Same kernels and arguments,
-    // so the same results.
-    const bool ov = p->overlap && !c.timed && p->levels >= 2 && p->B > 3 && sure_max_parts(c) > 1;
+    // The finest subbands' threshold search (lines 5-7 for the three subbands of
+    // scale 1, the costliest; on the pruned path when they are its large subbands)
+    // runs on a side stream from the moment scale 1 of Psi has produced them, beside
+    // the coarser scales of Psi, their search and the coarser scales of the next
+    // Psi^H; the next scale 1 of Psi^H (which reads the finest subbands) waits for
+    // it.  Same kernels and arguments (the side's pruned search has a fallback list
+    // of its own), so the same results.
+    const bool ov = p->overlap && !c.timed && p->levels >= 2 && p->B > 3 &&
+                    (sure_max_parts(c) > 1 || prune_big(p) == 3);
     bool pending = false;   // a finest-subband search is in flight on the side stream
     auto join = [&]() {
         if (!pending) return;
@@ -957,7 +982,7 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
                 if (c.err == cudaSuccess) c.err = cudaEventRecord(p->ev_fork, c.st);
                 if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(p->side, p->ev_fork, 0);
                 Ctx side{p, c.batch, p->side};
-                enq_sure(side, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1, 3);
+                enq_sure(side, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1, 3, p->fallback2);
                 c.launches += side.launches;
                 if (c.err == cudaSuccess) c.err = side.err;
                 if (c.err == cudaSuccess) c.err = cudaEventRecord(p->ev_join, p->side);
@@ -1058,6 +1083,9 @@ void enq_fused(Ctx& c, const SolveArgs& s) {
     u.counter = p->counter;
     u.sure_out = p->sure_val;
     u.fallback = p->fallback;
+    u.b_top = p->B - 1;
+    u.nb_launch = p->B;
+    u.item0 = 0;
     u.max_parts = SURE_MAX_PARTS;
     f.l8.src = make_src(p, vdamp::SRC_LINE8, nullptr);
     f.l8.N = N;
@@ -1882,7 +1910,10 @@ extern "C" vdamp_status vdamp_solve_groups(const vdamp_group* groups, int count,
 extern "C" vdamp_status vdamp_sure_fallback_count(vdamp_plan* p, int* count, void* stream) {
     if (!p || !count) return fail(VDAMP_EINVAL, "vdamp_sure_fallback_count: NULL");
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    CUDA_TRY(cudaMemcpy(count, p->fallback + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    int n[2] = {0, 0};
+    CUDA_TRY(cudaMemcpy(&n[0], p->fallback + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&n[1], p->fallback2 + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    *count = n[0] + n[1];
     return VDAMP_OK;
 }
 

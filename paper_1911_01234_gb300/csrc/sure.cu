@@ -23,12 +23,13 @@ __global__ void __launch_bounds__(SURE_THREADS) sure_search_kernel(const __grid_
 
 // Many slices (max_parts == 1): the pruned exact search (sure_prune_dev.cuh),
 // one large subband, two medium or four small ones per CTA; subbands it cannot
-// take go to the fallback list.  Grid: (prune_ctas, batch), the finest first.
+// take go to the fallback list.  Grid: (work items of a slice, batch), the finest
+// first; a launch may take a range of the items (from item0).
 __global__ void __launch_bounds__(PRUNE_THREADS, 1) sure_prune_kernel(const __grid_constant__ SureArgs a) {
     extern __shared__ unsigned sm_words[];
     __shared__ PruneShared sh[PRUNE_GROUPS];
     cudaGridDependencySynchronize();
-    const int slice = blockIdx.y, item = blockIdx.x;
+    const int slice = blockIdx.y, item = blockIdx.x + a.item0;
     const int ns = prune_n_small(a.off, a.B), nm = prune_n_med(a.off, a.B, ns);
     const int nbig = a.B - ns - nm;
     constexpr int per_med = PRUNE_THREADS / PRUNE_MED;
@@ -86,7 +87,7 @@ size_t sure_smem(int max_band) { return sure_split_smem_bytes(max_band); }
 cudaError_t launch_sure(const SureArgs& a, int batch, int max_band, int fallback_ctas,
                         cudaStream_t st) {
     if (a.max_parts == 1) {
-        cudaError_t e = launch_pdl(sure_prune_kernel, dim3(prune_ctas(a.off, a.B), batch),
+        cudaError_t e = launch_pdl(sure_prune_kernel, dim3(a.nb_launch, batch),
                                    dim3(PRUNE_THREADS), prune_smem_bytes(), st, a);
         if (e != cudaSuccess) return e;
         return launch_pdl(sure_fallback_kernel, dim3(fallback_ctas), dim3(SURE_THREADS),

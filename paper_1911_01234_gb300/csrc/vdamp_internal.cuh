@@ -236,8 +236,9 @@ struct SureArgs {
     unsigned* counter;    // [batch][B] search parts done (returns to 0 after each search)
     double* sure_out;     // [batch][B] minimum SURE of the last search
     int* fallback;        // [3 + batch B]: subbands the pruned search leaves to the full sort
-    // the split search's subbands: b_top, b_top - 1, ..., b_top - nb_launch + 1
-    int b_top, nb_launch;
+    // the split search's subbands: b_top, b_top - 1, ..., b_top - nb_launch + 1; the
+    // pruned search's CTAs of a slice: items item0 .. item0 + nb_launch - 1
+    int b_top, nb_launch, item0;
 };
 
 struct Line8Args {

@@ -364,6 +364,12 @@ def test_pruned_search_on_many_slices_equals_single_slices():
     out = plan.solve(y, m, p, sig, 4)
     st, _ = vb.vdamp_device_status(plan.handle)
     assert st == vb.VDAMP_OK
+    # the large subbands' search on the side stream or in line: the same bits
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_OVERLAP, 0)
+    inline = plan.solve(y, m, p, sig, 4)
+    vb.vdamp_plan_set_option(plan.handle, vb.VDAMP_OPT_OVERLAP, 1)
+    for key in ("x_hat", "tau", "thr", "alpha"):
+        assert torch.equal(inline[key], out[key]), key
     for i in (0, 17, n - 1):
         one = plan.solve(y[i:i + 1], m[i:i + 1], p[i:i + 1], [sig[i]], 4)
         for key in ("x_hat", "tau", "thr", "alpha"):

@@ -323,6 +323,7 @@ def test_overlapped_threshold_search_is_bit_identical(wl):
     """The finest subbands' threshold search on the plan's side stream (the split
     path of a lone slice) gives the same bits as the one-stream order, in a
     graph and in direct launches, with the per-iteration outputs too."""
+    # (the pruned path of many slices: test_gpu_batched)
     pr = synth.make_problem(wl)
     plan = vb.Plan(wl.ny, wl.nx, wl.wavelet, wl.levels)
     y, m, p = _problem_on_device(pr)
