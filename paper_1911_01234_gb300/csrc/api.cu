@@ -247,6 +247,8 @@ struct vdamp_plan {
     int overlap = 1;       // the finest subbands' threshold search on a side stream (split path)
     cudaStream_t side = nullptr;              // that side stream, and its fork / join events
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side2 = nullptr;             // the same for the scale-2 subbands (split path)
+    cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
     int fused_ok = 0;      // the device can hold the cluster
     int fused_C = 0, fused_cb = 0, fused_rpc = 0, fused_idwt_to = 0, fused_dwt_to = 0;
     size_t fused_smem = 0;
@@ -276,6 +278,9 @@ static void plan_free(vdamp_plan* p) {
     if (p->side) cudaStreamDestroy(p->side);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->side2) cudaStreamDestroy(p->side2);
+    if (p->ev_fork2) cudaEventDestroy(p->ev_fork2);
+    if (p->ev_join2) cudaEventDestroy(p->ev_join2);
     delete p;
 }
 
@@ -480,6 +485,9 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     A(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     A(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    A(cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking));
+    A(cudaEventCreateWithFlags(&p->ev_fork2, cudaEventDisableTiming));
+    A(cudaEventCreateWithFlags(&p->ev_join2, cudaEventDisableTiming));
     // shared-memory attributes large enough for every tile choice the tuner may make
     p->smem_col = vdamp::col_pass_smem(ny, cb, nt);
     for (int c2 = 2; c2 <= 16; c2 *= 2) {
@@ -644,10 +652,10 @@ int wavelet_cluster(const Ctx& c, int* lo) {
     return 0;
 }
 
-// x = Psi^H (src), levels s .. 1; before_finest (if set) runs before scale 1 is
-// enqueued (scale 1 reads the finest subbands)
+// x = Psi^H (src), levels s .. 1; before_scale(j) (if set) runs before a scale j
+// launched on its own is enqueued (it reads the subbands of scale j)
 void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img,
-               const std::function<void()>& before_finest = nullptr) {
+               const std::function<void(int)>& before_scale = nullptr) {
     vdamp_plan* p = c.p;
     const int s = p->levels;
     const float2* ll_in = nullptr;
@@ -693,16 +701,16 @@ void enq_psi_h(Ctx& c, const SrcSpec& src, float2* img,
             }
             continue;
         }
-        if (j == 1 && before_finest) before_finest();
+        if (before_scale) before_scale(j);
         c.pre();
         c.chk(vdamp::launch_idwt_level(a, c.batch, c.st), VDAMP_KERNEL_IDWT);
     }
 }
 
-// packed = Psi img + src (levels 1 .. s); after_finest (if set) runs once scale 1
-// (the finest subbands) is enqueued
+// packed = Psi img + src (levels 1 .. s); after_scale(j) (if set) runs once a
+// scale j launched on its own (it writes the subbands of scale j) is enqueued
 void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src,
-             const std::function<void()>& after_finest = nullptr) {
+             const std::function<void(int)>& after_scale = nullptr) {
     vdamp_plan* p = c.p;
     const int s = p->levels;
     const float2* in = img;
@@ -747,7 +755,7 @@ void enq_psi(Ctx& c, const float2* img, float2* packed, const SrcSpec& src,
         }
         c.pre();
         c.chk(vdamp::launch_dwt_level(a, c.batch, c.st), VDAMP_KERNEL_DWT);
-        if (j == 1 && after_finest) after_finest();
+        if (after_scale) after_scale(j);
     }
     if (cl) {   // the coarse scales in one cluster launch
         c.pre();
@@ -957,11 +965,24 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
     // of its own), so the same results.
     const bool ov = p->overlap && !c.timed && p->levels >= 2 && p->B > 3 &&
                     (sure_max_parts(c) > 1 || prune_big(p) == 3);
-    bool pending = false;   // a finest-subband search is in flight on the side stream
+    // On the split path, with scale 2 of the transforms launched on its own, the
+    // scale-2 subbands' search runs on a second side stream in the same way (from
+    // scale 2 of Psi to scale 2 of the next Psi^H).
+    int clo = 2;
+    const int ccl = wavelet_cluster(c, &clo);
+    const bool ov2 = ov && sure_max_parts(c) > 1 && p->levels >= 3 && !(ccl > 0 && clo <= 2);
+    bool pending[3] = {false, false, false};   // a search of scale 1 / 2 in flight on a side stream
+    cudaStream_t side_st[3] = {nullptr, p->side, p->side2};
+    cudaEvent_t ev_fork[3] = {nullptr, p->ev_fork, p->ev_fork2};
+    cudaEvent_t ev_join[3] = {nullptr, p->ev_join, p->ev_join2};
+    auto join_scale = [&](int j) {
+        if (j < 1 || j > 2 || !pending[j]) return;
+        if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(c.st, ev_join[j], 0);
+        pending[j] = false;
+    };
     auto join = [&]() {
-        if (!pending) return;
-        if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(c.st, p->ev_join, 0);
-        pending = false;
+        join_scale(1);
+        join_scale(2);
     };
     float2* prev = p->rA;  // r_{k-1}
     float2* cur = p->rB;   // r_k
@@ -974,22 +995,25 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
         } else {
             src = make_src(p, vdamp::SRC_LINE8, prev);
         }
-        if (!zero) enq_psi_h(c, src, p->u, join);       // Psi^H r~_k        (line 3)
+        if (!zero) enq_psi_h(c, src, p->u, join_scale);  // Psi^H r~_k        (line 3)
         join();
         enq_kspace_iter(c, zero, s.y, s.mask, s.density);  // z, tau parts, F^H P^-1 z (3-5)
         if (ov) {
-            auto fork = [&]() {   // the finest subbands of r_k are written
-                if (c.err == cudaSuccess) c.err = cudaEventRecord(p->ev_fork, c.st);
-                if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(p->side, p->ev_fork, 0);
-                Ctx side{p, c.batch, p->side};
-                enq_sure(side, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1, 3, p->fallback2);
+            auto fork = [&](int j) {   // the subbands of scale j of r_k are written
+                if (j > 2 || (j == 2 && !ov2)) return;
+                if (c.err == cudaSuccess) c.err = cudaEventRecord(ev_fork[j], c.st);
+                if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(side_st[j], ev_fork[j], 0);
+                Ctx side{p, c.batch, side_st[j]};
+                enq_sure(side, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1 - 3 * (j - 1), 3,
+                         j == 1 ? p->fallback2 : nullptr);
                 c.launches += side.launches;
                 if (c.err == cudaSuccess) c.err = side.err;
-                if (c.err == cudaSuccess) c.err = cudaEventRecord(p->ev_join, p->side);
-                pending = true;
+                if (c.err == cudaSuccess) c.err = cudaEventRecord(ev_join[j], side_st[j]);
+                pending[j] = true;
             };
             enq_psi(c, p->u, cur, src, fork);            // r_k = r~_k + Psi u' (line 4)
-            enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 4, p->B - 3);  // coarse
+            const int done = ov2 ? 6 : 3;                // subbands searched on the side streams
+            enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1 - done, p->B - done);
         } else {
             enq_psi(c, p->u, cur, src);                  // r_k = r~_k + Psi u' (line 4)
             enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha);  // tau, theta, alpha (5-7)
