@@ -104,8 +104,9 @@ size_t vdamp_workspace_bytes(const vdamp_plan* plan);
  *     the plan while the coarser scales of Psi, their search and the coarser
  *     scales of the next Psi^H run (with the split search, and with the pruned
  *     one when the finest subbands are its one-CTA subbands); with the split
- *     search the three subbands of scale 2 likewise on a third stream; 0 keeps
- *     one stream.  The same kernels with the same arguments: identical results. */
+ *     search the subbands of every scale below the coarsest likewise, each
+ *     scale on a stream of its own; 0 keeps one stream.  The same kernels
+ *     with the same arguments: identical results. */
 enum { VDAMP_OPT_GRAPH = 1, VDAMP_OPT_KERNEL_TIMING = 2, VDAMP_OPT_FUSED = 3, VDAMP_OPT_OVERLAP = 4 };
 vdamp_status vdamp_plan_set_option(vdamp_plan* plan, int option, int value);
 

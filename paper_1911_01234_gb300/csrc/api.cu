@@ -245,10 +245,10 @@ struct vdamp_plan {
     int timing = 0;
     int use_fused = 0;
     int overlap = 1;       // the finest subbands' threshold search on a side stream (split path)
-    cudaStream_t side = nullptr;              // that side stream, and its fork / join events
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaStream_t side2 = nullptr;             // the same for the scale-2 subbands (split path)
-    cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+    // side stream j (j = 1 .. levels - 1) searches the subbands of scale j, with its
+    // fork and join events (scales >= 2: split path only)
+    cudaStream_t side[VDAMP_MAX_LEVELS] = {};
+    cudaEvent_t ev_fork[VDAMP_MAX_LEVELS] = {}, ev_join[VDAMP_MAX_LEVELS] = {};
     int fused_ok = 0;      // the device can hold the cluster
     int fused_C = 0, fused_cb = 0, fused_rpc = 0, fused_idwt_to = 0, fused_dwt_to = 0;
     size_t fused_smem = 0;
@@ -275,12 +275,11 @@ static void plan_free(vdamp_plan* p) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->cap) cudaStreamDestroy(p->cap);
-    if (p->side) cudaStreamDestroy(p->side);
-    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-    if (p->ev_join) cudaEventDestroy(p->ev_join);
-    if (p->side2) cudaStreamDestroy(p->side2);
-    if (p->ev_fork2) cudaEventDestroy(p->ev_fork2);
-    if (p->ev_join2) cudaEventDestroy(p->ev_join2);
+    for (int j = 0; j < VDAMP_MAX_LEVELS; ++j) {
+        if (p->side[j]) cudaStreamDestroy(p->side[j]);
+        if (p->ev_fork[j]) cudaEventDestroy(p->ev_fork[j]);
+        if (p->ev_join[j]) cudaEventDestroy(p->ev_join[j]);
+    }
     delete p;
 }
 
@@ -482,12 +481,11 @@ extern "C" vdamp_status vdamp_plan_create(vdamp_plan** out, int ny, int nx, int 
     A(cudaMemset(p->fallback, 0, 3 * sizeof(int)));
     A(cudaMemset(p->fallback2, 0, 3 * sizeof(int)));               // each fallback launch empties it
     A(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
-    A(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
-    A(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-    A(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
-    A(cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking));
-    A(cudaEventCreateWithFlags(&p->ev_fork2, cudaEventDisableTiming));
-    A(cudaEventCreateWithFlags(&p->ev_join2, cudaEventDisableTiming));
+    for (int j = 1; j < levels; ++j) {
+        A(cudaStreamCreateWithFlags(&p->side[j], cudaStreamNonBlocking));
+        A(cudaEventCreateWithFlags(&p->ev_fork[j], cudaEventDisableTiming));
+        A(cudaEventCreateWithFlags(&p->ev_join[j], cudaEventDisableTiming));
+    }
     // shared-memory attributes large enough for every tile choice the tuner may make
     p->smem_col = vdamp::col_pass_smem(ny, cb, nt);
     for (int c2 = 2; c2 <= 16; c2 *= 2) {
@@ -965,24 +963,27 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
     // of its own), so the same results.
     const bool ov = p->overlap && !c.timed && p->levels >= 2 && p->B > 3 &&
                     (sure_max_parts(c) > 1 || prune_big(p) == 3);
-    // On the split path, with scale 2 of the transforms launched on its own, the
-    // scale-2 subbands' search runs on a second side stream in the same way (from
-    // scale 2 of Psi to scale 2 of the next Psi^H).
-    int clo = 2;
+    // On the split path the subbands of every scale j < s launched on its own do the
+    // same on side stream j (from scale j of Psi to scale j of the next Psi^H); the
+    // coarsest scale and the approximation band stay in line.
+    int clo = p->levels + 1;
     const int ccl = wavelet_cluster(c, &clo);
-    const bool ov2 = ov && sure_max_parts(c) > 1 && p->levels >= 3 && !(ccl > 0 && clo <= 2);
-    bool pending[3] = {false, false, false};   // a search of scale 1 / 2 in flight on a side stream
-    cudaStream_t side_st[3] = {nullptr, p->side, p->side2};
-    cudaEvent_t ev_fork[3] = {nullptr, p->ev_fork, p->ev_fork2};
-    cudaEvent_t ev_join[3] = {nullptr, p->ev_join, p->ev_join2};
+    const bool split = sure_max_parts(c) > 1;
+    bool forks[VDAMP_MAX_LEVELS] = {};   // scale j's search goes to side stream j
+    int side_bands = 0;                  // subbands searched on side streams
+    for (int j = 1; ov && j < p->levels; ++j) {
+        if (j >= 2 && (!split || (ccl > 0 && j >= clo))) break;
+        forks[j] = true;
+        side_bands += 3;
+    }
+    bool pending[VDAMP_MAX_LEVELS] = {};   // scale j's search in flight on side stream j
     auto join_scale = [&](int j) {
-        if (j < 1 || j > 2 || !pending[j]) return;
-        if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(c.st, ev_join[j], 0);
+        if (j < 1 || j >= VDAMP_MAX_LEVELS || !pending[j]) return;
+        if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(c.st, p->ev_join[j], 0);
         pending[j] = false;
     };
     auto join = [&]() {
-        join_scale(1);
-        join_scale(2);
+        for (int j = 1; j < VDAMP_MAX_LEVELS; ++j) join_scale(j);
     };
     float2* prev = p->rA;  // r_{k-1}
     float2* cur = p->rB;   // r_k
@@ -1000,20 +1001,20 @@ void enq_solve(Ctx& c, const SolveArgs& s) {
         enq_kspace_iter(c, zero, s.y, s.mask, s.density);  // z, tau parts, F^H P^-1 z (3-5)
         if (ov) {
             auto fork = [&](int j) {   // the subbands of scale j of r_k are written
-                if (j > 2 || (j == 2 && !ov2)) return;
-                if (c.err == cudaSuccess) c.err = cudaEventRecord(ev_fork[j], c.st);
-                if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(side_st[j], ev_fork[j], 0);
-                Ctx side{p, c.batch, side_st[j]};
+                if (j < 1 || j >= VDAMP_MAX_LEVELS || !forks[j]) return;
+                if (c.err == cudaSuccess) c.err = cudaEventRecord(p->ev_fork[j], c.st);
+                if (c.err == cudaSuccess) c.err = cudaStreamWaitEvent(p->side[j], p->ev_fork[j], 0);
+                Ctx side{p, c.batch, p->side[j]};
                 enq_sure(side, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1 - 3 * (j - 1), 3,
                          j == 1 ? p->fallback2 : nullptr);
                 c.launches += side.launches;
                 if (c.err == cudaSuccess) c.err = side.err;
-                if (c.err == cudaSuccess) c.err = cudaEventRecord(ev_join[j], side_st[j]);
+                if (c.err == cudaSuccess) c.err = cudaEventRecord(p->ev_join[j], p->side[j]);
                 pending[j] = true;
             };
             enq_psi(c, p->u, cur, src, fork);            // r_k = r~_k + Psi u' (line 4)
-            const int done = ov2 ? 6 : 3;                // subbands searched on the side streams
-            enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1 - done, p->B - done);
+            enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha, p->B - 1 - side_bands,
+                     p->B - side_bands);                 // the other subbands in line
         } else {
             enq_psi(c, p->u, cur, src);                  // r_k = r~_k + Psi u' (line 4)
             enq_sure(c, cur, s.iters, k, s.tau, s.thr, s.alpha);  // tau, theta, alpha (5-7)
