@@ -682,17 +682,32 @@ static __device__ void sure_prune_subband(const SureArgs& a, int b, int slice, u
         candB[E.start + rk] = x;
     }
     psync<NT>(bar);
-    // per candidate bucket, in sorted order: prefix sums of a^2 (candA, no longer needed
-    // for the gathered keys) and of 1/a (candH), one thread per bucket
-    for (int e = tid; e < tot_e; e += NT) {
+    // per candidate bucket, in sorted order: inclusive prefix sums of a^2 (candA, no
+    // longer needed for the gathered keys) and of 1/a (candH), a warp per bucket
+    // (chunks of 32 by shuffle scans)
+    for (int e = warp; e < tot_e; e += NW) {
         const PruneEntry& E = tab[e];
-        float cs = 0.f, hs = 0.f;
-        for (int i = E.start; i < E.start + E.n; ++i) {
-            const float y = candB[i];
-            cs += y * y;
-            hs += __frcp_rn(y);
-            candA[i] = cs;
-            candH[i] = hs;
+        float cs = 0.f, hs = 0.f;   // the chunks before
+        for (int i0 = E.start; i0 < E.start + E.n; i0 += 32) {
+            const int i = i0 + lane;
+            const bool in = i < E.start + E.n;
+            const float y = in ? candB[i] : 1.f;
+            float c2 = in ? y * y : 0.f, h = in ? __frcp_rn(y) : 0.f;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float tc2 = __shfl_up_sync(0xffffffffu, c2, o);
+                const float th2 = __shfl_up_sync(0xffffffffu, h, o);
+                if (lane >= o) {
+                    c2 += tc2;
+                    h += th2;
+                }
+            }
+            if (in) {
+                candA[i] = cs + c2;
+                candH[i] = hs + h;
+            }
+            cs += __shfl_sync(0xffffffffu, c2, 31);
+            hs += __shfl_sync(0xffffffffu, h, 31);
         }
     }
     psync<NT>(bar);
