@@ -165,8 +165,9 @@ vdamp_status vdamp_plan_get_tuning(const vdamp_plan* plan, int* tuning);
 vdamp_status vdamp_plan_set_tuning(vdamp_plan* plan, const int* tuning);
 
 /*
- * Autotuner: times `trials` iterations (lines 3-8) of `batch` synthetic
- * slices, captured in one CUDA graph as a solve runs them, per candidate on
+ * Autotuner: times a solve of max(trials, 2) iterations (Algorithm 1 lines
+ * 3-8 and the return line) of `batch` synthetic slices, captured in one CUDA
+ * graph as vdamp_solve captures it (side streams included), per candidate on
  * `stream` and keeps, one parameter after another (coordinate descent over
  * the tuning above, starting from the current one), the fastest shape.  Blocks until done; allocates and frees
  * its own temporary device buffers (about 6 batch ny nx complex values).

@@ -1688,7 +1688,8 @@ extern "C" vdamp_status vdamp_plan_autotune(vdamp_plan* p, int batch, int trials
     A(cudaMalloc(&rn, n * sizeof(float2)));
     A(cudaMalloc(&m, n));
     A(cudaMalloc(&d, n * sizeof(float)));
-    A(cudaMalloc(&outs, 3 * nb * sizeof(double)));
+    const int iters = std::max(trials, 2);
+    A(cudaMalloc(&outs, 3 * nb * (size_t)iters * sizeof(double)));
     A(cudaEventCreate(&e0));
     A(cudaEventCreate(&e1));
     auto cleanup = [&]() {
@@ -1708,23 +1709,29 @@ extern "C" vdamp_status vdamp_plan_autotune(vdamp_plan* p, int batch, int trials
         cleanup();
         return st;
     }
-    // One timing trial: `trials` iterations (lines 3-8) captured in one CUDA graph, as a
-    // solve runs them (programmatic dependent launches, no host launch overhead); the
-    // faster of two timed launches after a warm-up launch.
+    // One timing trial: a solve of max(trials, 2) iterations from the synthetic r~,
+    // captured in one CUDA graph as vdamp_solve captures it (programmatic dependent
+    // launches, the threshold searches of the finer scales on their side streams), so
+    // that a shape is judged by what a solve costs with it; the faster of two timed
+    // launches after a warm-up launch.
     auto trial = [&](const int* t, float* ms) -> cudaError_t {
         apply_tuning(p, t);
         Ctx c{p, batch, p->cap};
-        const SrcSpec src = make_src(p, vdamp::SRC_EXPLICIT, rt);
-        auto once = [&]() {
-            enq_psi_h(c, src, p->u);
-            enq_kspace_iter(c, false, y, m, d);
-            enq_psi(c, p->u, r, src);
-            enq_sure(c, r, 1, 0, outs, outs + nb, outs + 2 * nb);
-            enq_line8(c, r, rn);
-        };
+        SolveArgs sa;
+        sa.y = y;
+        sa.mask = m;
+        sa.density = d;
+        sa.iters = iters;
+        sa.r_tilde0 = rt;
+        sa.x_hat = rn;
+        sa.tau = outs;
+        sa.thr = outs + nb * iters;
+        sa.alpha = outs + 2 * nb * iters;
+        sa.r_tilde_out = nullptr;
+        sa.x_hat_iters = nullptr;
         cudaError_t x = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
         if (x != cudaSuccess) return x;
-        for (int i = 0; i < trials; ++i) once();
+        enq_solve(c, sa);
         cudaGraph_t graph = nullptr;
         x = cudaStreamEndCapture(p->cap, &graph);
         if (c.err != cudaSuccess || x != cudaSuccess) {
